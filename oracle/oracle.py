@@ -1,0 +1,330 @@
+"""TripleID-Q CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, obviously-correct CPU statement of what the query hot path
+computes, used to check the CUDA library result by result.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+it.  It shares no code with the CUDA path: the loops live in ``oracle.c``
+(compiled here with gcc, loaded with ctypes) and the set algebra around them in
+numpy below.  Tuple sets are row-major (rows x k) int32 arrays with one
+variable id per column.
+
+Paper passages followed (TripleID-Q, IEEE TPDS 2018):
+* ``match``        -- Section 3, Algorithm 1 and its brute-force GPUSearch test;
+                      key value 0 is the free variable "?".
+* ``match_multi``  -- Section 4.1, keysArray / positionArray[i].query.
+* ``bind``         -- Section 4.2, result vectors R_qi (terms at the variable slots).
+* ``join``         -- Section 4.2 steps 1-3 and the relationship table (shared term
+                      at any of S/P/O on either side); inner join.
+* ``union``        -- Section 4.1; results keep only distinct values (Section 4.3).
+* ``filter``       -- Section 4.3 (filter during extraction), on integer IDs with the
+                      order-preserving literal encoding the same section proposes.
+* ``project``      -- Section 4.3, SELECT variables and DISTINCT.
+* ``execute``      -- Section 4.3 / Fig. "Integration of several operations": per
+                      subquery search+extract (filter fused), joins left to right,
+                      distinct results.
+
+Readings where the paper is silent: 0 (unbound, e.g. union padding) never joins
+and never passes a filter; every result is a set in canonical order (rows
+sorted lexicographically by column order, duplicates removed).
+"""
+from __future__ import annotations
+
+import contextlib
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+
+OPS = {"eq": 0, "ne": 1, "lt": 2, "le": 3, "gt": 4, "ge": 5, "range": 6}
+NESTED_LOOP_CAP = 2_000_000_000  # |L|*|R| above this switches to the sort-merge join
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library (plain gcc, no CUDA)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = f"{_SO}.{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = _load(build())
+    return _lib
+
+
+@contextlib.contextmanager
+def using_library(path: str):
+    """Run the oracle on another build of oracle.c (the pin tests use this to
+    show that planted mistakes are caught)."""
+    global _lib
+    saved = _lib
+    _lib = _load(path)
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def _load(path):
+    L = C.CDLL(path)
+    i32p, i64p = C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    L.or_match.restype = C.c_int64
+    L.or_match.argtypes = [i32p, i32p, i32p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, i32p]
+    L.or_match_multi.restype = None
+    L.or_match_multi.argtypes = [i32p, i32p, i32p, C.c_int64, i32p, C.c_int, i64p,
+                                 C.POINTER(i32p)]
+    L.or_bind.restype = C.c_int64
+    L.or_bind.argtypes = [i32p, i32p, i32p, i32p, C.c_int64, C.c_char_p, C.c_int,
+                          C.c_char_p, i32p]
+    L.or_canonical.restype = C.c_int64
+    L.or_canonical.argtypes = [i32p, C.c_int64, C.c_int]
+    ip = C.POINTER(C.c_int)
+    for f in (L.or_join_nested, L.or_join_sortmerge):
+        f.restype = C.c_int64
+        f.argtypes = [i32p, C.c_int64, C.c_int, i32p, C.c_int64, C.c_int,
+                      C.c_int, ip, ip, C.c_int, ip, i32p]
+    L.or_filter.restype = C.c_int64
+    L.or_filter.argtypes = [i32p, C.c_int64, C.c_int, C.c_int, C.c_int,
+                            C.c_int32, C.c_int32, i32p]
+    return L
+
+
+def _p32(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _ints(xs):
+    arr = (C.c_int * max(1, len(xs)))(*xs)
+    return arr
+
+
+def _col(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ---------------------------------------------------------------------------
+# tuple sets
+# ---------------------------------------------------------------------------
+
+@dataclass
+class TupleSet:
+    vars: tuple          # variable id per column
+    rows: np.ndarray     # (n, k) int32, row-major
+
+    @property
+    def n(self):
+        return int(self.rows.shape[0])
+
+    @property
+    def k(self):
+        return len(self.vars)
+
+
+def canonical(rows: np.ndarray) -> np.ndarray:
+    """Rows sorted lexicographically in column order, duplicates removed."""
+    rows = np.array(rows, dtype=np.int32, order="C", copy=True)
+    if rows.ndim != 2:
+        raise ValueError("rows must be 2-D")
+    n, k = rows.shape
+    if n == 0 or k == 0:
+        return rows
+    m = lib().or_canonical(_p32(rows), n, k)
+    if m < 0:
+        raise MemoryError("oracle canonical: out of memory")
+    return rows[:m].copy()
+
+
+def _set(vars_, rows):
+    return TupleSet(tuple(int(v) for v in vars_), canonical(rows))
+
+
+# ---------------------------------------------------------------------------
+# search
+# ---------------------------------------------------------------------------
+
+def match(s, p, o, key) -> np.ndarray:
+    """Ascending positions i with (S[i], P[i], O[i]) answering key (0 = "?")."""
+    s, p, o = _col(s), _col(p), _col(o)
+    ks, kp, ko = (int(x) for x in key)
+    if min(ks, kp, ko) < 0:
+        raise ValueError("negative ID in a key")
+    L = lib()
+    h = L.or_match(_p32(s), _p32(p), _p32(o), s.shape[0], ks, kp, ko, None)
+    out = np.empty(h, np.int32)
+    L.or_match(_p32(s), _p32(p), _p32(o), s.shape[0], ks, kp, ko, _p32(out))
+    return out
+
+
+def match_multi(s, p, o, keys) -> list:
+    """One pass over the store for m keys; one ascending position list per key."""
+    s, p, o = _col(s), _col(p), _col(o)
+    keys = np.ascontiguousarray(np.asarray(keys, dtype=np.int32).reshape(-1, 3))
+    m = keys.shape[0]
+    if m == 0:
+        return []
+    if keys.min() < 0:
+        raise ValueError("negative ID in a key")
+    L = lib()
+    counts = np.zeros(m, np.int64)
+    L.or_match_multi(_p32(s), _p32(p), _p32(o), s.shape[0], _p32(keys), m,
+                     counts.ctypes.data_as(C.POINTER(C.c_int64)), None)
+    outs = [np.empty(int(c), np.int32) for c in counts]
+    ptrs = (C.POINTER(C.c_int32) * m)(*[_p32(x) for x in outs])
+    L.or_match_multi(_p32(s), _p32(p), _p32(o), s.shape[0], _p32(keys), m,
+                     counts.ctypes.data_as(C.POINTER(C.c_int64)), ptrs)
+    return outs
+
+
+def pattern_vars(key, var) -> tuple:
+    """Output variables of a pattern: distinct ids at its "?" slots, in s,p,o order."""
+    out = []
+    for j in range(3):
+        v = int(var[j])
+        if v < 0:
+            continue
+        if int(key[j]) != 0:
+            raise ValueError("a bound slot cannot carry a variable")
+        if v not in out:
+            out.append(v)
+    if not out:
+        raise ValueError("pattern has no variable")
+    if len(out) > 8:
+        raise ValueError("too many variables")
+    return tuple(out)
+
+
+def bind(s, p, o, key, var, idx) -> TupleSet:
+    """Result vector of one subquery: values at the variable slots of each hit."""
+    s, p, o = _col(s), _col(p), _col(o)
+    idx = _col(idx)
+    vars_ = pattern_vars(key, var)
+    k = len(vars_)
+    out = np.empty((idx.shape[0], k), np.int32)
+    vb = bytes((int(v) & 0xFF) for v in var)
+    ob = bytes((int(v) & 0xFF) for v in vars_)
+    r = lib().or_bind(_p32(s), _p32(p), _p32(o), _p32(idx), idx.shape[0], vb, k, ob, _p32(out))
+    return _set(vars_, out[:r])
+
+
+# ---------------------------------------------------------------------------
+# operators on tuple sets
+# ---------------------------------------------------------------------------
+
+def join_schema(Lv, Rv):
+    shared = [v for v in Lv if v in Rv]
+    lkey = [Lv.index(v) for v in shared]
+    rkey = [Rv.index(v) for v in shared]
+    rrest = [j for j, v in enumerate(Rv) if v not in Lv]
+    out_vars = tuple(Lv) + tuple(Rv[j] for j in rrest)
+    return shared, lkey, rkey, rrest, out_vars
+
+
+def join(Ls: TupleSet, Rs: TupleSet, method: str = "auto") -> TupleSet:
+    """Inner join on all shared variables; output = L's columns then R's others."""
+    shared, lkey, rkey, rrest, out_vars = join_schema(Ls.vars, Rs.vars)
+    if len(out_vars) > 8:
+        raise ValueError("join output wider than 8 columns")
+    if method == "auto":
+        method = "nested" if Ls.n * Rs.n <= NESTED_LOOP_CAP else "sortmerge"
+    f = {"nested": lib().or_join_nested, "sortmerge": lib().or_join_sortmerge}[method]
+    Lr = np.ascontiguousarray(Ls.rows, np.int32)
+    Rr = np.ascontiguousarray(Rs.rows, np.int32)
+    args = (_p32(Lr), Ls.n, Ls.k, _p32(Rr), Rs.n, Rs.k, len(shared),
+            _ints(lkey), _ints(rkey), len(rrest), _ints(rrest))
+    m = f(*args, None)
+    if m < 0:
+        raise MemoryError("oracle join: out of memory")
+    out = np.empty((m, len(out_vars)), np.int32)
+    f(*args, _p32(out))
+    return _set(out_vars, out)
+
+
+def union_schema(sets):
+    out = []
+    for t in sets:
+        for v in t.vars:
+            if v not in out:
+                out.append(v)
+    return tuple(out)
+
+
+def union(sets) -> TupleSet:
+    """Set union; branches with other variables are padded with 0 (unbound)."""
+    sets = list(sets)
+    if not sets:
+        raise ValueError("union of nothing")
+    uv = union_schema(sets)
+    if len(uv) > 8:
+        raise ValueError("union schema wider than 8 columns")
+    parts = []
+    for t in sets:
+        a = np.zeros((t.n, len(uv)), np.int32)
+        for j, v in enumerate(t.vars):
+            a[:, uv.index(v)] = t.rows[:, j]
+        parts.append(a)
+    return _set(uv, np.concatenate(parts, axis=0))
+
+
+def filter(t: TupleSet, var: int, op: str, a: int, b: int = 0) -> TupleSet:
+    """Rows whose value of var passes the comparison (0 = unbound never passes)."""
+    if var not in t.vars:
+        raise ValueError("filter variable not in the set")
+    rows = np.ascontiguousarray(t.rows, np.int32)
+    out = np.empty_like(rows)
+    m = lib().or_filter(_p32(rows), t.n, t.k, t.vars.index(var), OPS[op], int(a), int(b),
+                        _p32(out))
+    return TupleSet(t.vars, out[:m].copy())
+
+
+def project(t: TupleSet, vars_) -> TupleSet:
+    """SELECT the given variables (in that order) with DISTINCT."""
+    cols = [t.vars.index(v) for v in vars_]
+    return _set(vars_, t.rows[:, cols])
+
+
+# ---------------------------------------------------------------------------
+# plans
+# ---------------------------------------------------------------------------
+
+def execute(s, p, o, plan) -> TupleSet:
+    """Evaluate a plan (list of node dicts; the last node is the root)."""
+    memo = {}
+
+    def ev(i):
+        if i in memo:
+            return memo[i]
+        nd = plan[i]
+        op = nd["op"]
+        if op == "match":
+            pat = nd["pattern"]
+            idx = match(s, p, o, pat.key())
+            r = bind(s, p, o, pat.key(), pat.var, idx)
+        elif op == "filter":
+            r = filter(ev(nd["input"]), nd["var"], nd["cmp"], nd["a"], nd.get("b", 0))
+        elif op == "join":
+            a, b = nd["inputs"]
+            r = join(ev(a), ev(b))
+        elif op == "union":
+            r = union([ev(j) for j in nd["inputs"]])
+        elif op == "project":
+            r = project(ev(nd["input"]), tuple(nd["vars"]))
+        else:
+            raise ValueError(f"unknown plan op {op}")
+        memo[i] = r
+        return r
+
+    return ev(len(plan) - 1)

@@ -1,0 +1,363 @@
+"""Seeded synthetic TripleID stores and query workloads.
+
+This module only draws inputs: dictionary-encoded int32 triple columns in
+structure-of-arrays layout and the triple patterns / plans asked of them.  It
+holds none of the query method's arithmetic (no pattern matching, joining or
+compaction); both the CPU oracle and the CUDA library consume what it makes.
+
+ID space (one shared namespace, so a subject ID and an object ID that are equal
+denote the same term -- the worked example of the entailment section joins
+object 56 with subject 56):
+
+* 0 is reserved for the free variable "?" (Section 3, the key encoding);
+* entity IDs lie in [1, 2^30 - 1];
+* an encoded integer literal of value v in [0, 2^30 - 1] has ID LIT_BASE + v,
+  LIT_BASE = 2^30, so ID order equals value order (the order-preserving ID
+  assignment suggested in Section 4.3).
+
+Workloads (the paper's BTC-2009 and SP2Bench files are not available; these
+stand in for them with the same kind of skew):
+
+* ``tiny``       -- 1M triples; S uniform over 1..100k, P = Zipf(1.2) rank over
+                    1..64, O = Zipf(1.1) rank over 1..200k; 16 queries, 4 each of
+                    (s,?,?), (?,p,?), (?,p,o), (s,p,?) keyed from stored triples.
+* ``university`` -- a university-shaped ontology (20 predicates with fixed
+                    frequencies, typed subject classes, 60% entity-valued and
+                    40% literal-valued objects); 200M triples at full size, any
+                    smaller size for parity runs; 64 single-pattern queries with
+                    target selectivity log-uniform on [1e-6, 0.3].
+
+Every store is a set: duplicate triples are removed and the store topped up to
+exactly ``n`` triples, then put in a seeded random order (the store is neither
+sorted nor indexed, as in the paper).
+"""
+from __future__ import annotations
+
+import hashlib
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+LIT_BASE = 1 << 30
+STORE_SEED = 1807
+QUERY_SEED = 1409
+GEN_VERSION = 5  # bump when any recipe below changes (invalidates the cache)
+
+# ----------------------------------------------------------------------------
+# data records
+# ----------------------------------------------------------------------------
+
+
+@dataclass
+class Store:
+    """Three int32 columns of equal length (SoA), plus the recipe that made them."""
+    s: np.ndarray
+    p: np.ndarray
+    o: np.ndarray
+    name: str
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.s.shape[0])
+
+    def triples(self) -> np.ndarray:
+        return np.stack([self.s, self.p, self.o], axis=1)
+
+
+@dataclass
+class Pattern:
+    """A triple pattern: 0 in s/p/o is "?"; var[j] labels the "?" in slot j (-1: anonymous)."""
+    s: int
+    p: int
+    o: int
+    var: tuple = (-1, -1, -1)
+
+    def key(self):
+        return (self.s, self.p, self.o)
+
+    def shape(self) -> str:
+        return "".join(c if v else "?" for c, v in zip("spo", self.key()))
+
+
+# ----------------------------------------------------------------------------
+# cache
+# ----------------------------------------------------------------------------
+
+
+def _cache_dir() -> str:
+    d = os.environ.get("TID_SYNTH_CACHE") or os.path.join(
+        os.environ.get("TMPDIR", "/tmp"), "tid_synth_cache")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def _cached(tag: str, builder):
+    h = hashlib.sha1(f"{tag}|v{GEN_VERSION}".encode()).hexdigest()[:16]
+    base = os.path.join(_cache_dir(), h)
+    names = ("s", "p", "o")
+    if all(os.path.exists(f"{base}.{c}.npy") for c in names):
+        return tuple(np.load(f"{base}.{c}.npy") for c in names)
+    cols = builder()
+    for c, a in zip(names, cols):
+        tmp = f"{base}.{c}.{os.getpid()}.tmp.npy"
+        np.save(tmp, a)
+        os.replace(tmp, f"{base}.{c}.npy")
+    return cols
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+
+
+def zipf_cdf(s: float, k: int) -> np.ndarray:
+    """CDF of a Zipf(s) law truncated to ranks 1..k (inverse-CDF sampling table)."""
+    w = np.arange(1, k + 1, dtype=np.float64) ** (-s)
+    c = np.cumsum(w)
+    return c / c[-1]
+
+
+def zipf_ranks(rng: np.random.Generator, n: int, cdf: np.ndarray) -> np.ndarray:
+    """n ranks in 1..len(cdf) drawn by inverse CDF."""
+    u = rng.random(n)
+    r = np.searchsorted(cdf, u, side="right") + 1
+    return np.minimum(r, len(cdf)).astype(np.int64)
+
+
+# packed (s, p, o) key used only to remove duplicate triples:
+#   s < 2^26, p < 2^7 (a small predicate value or index), o < 2^31
+_S_SHIFT, _P_SHIFT = 38, 31
+
+
+def _pack(s, pidx, o):
+    return (s.astype(np.uint64) << np.uint64(_S_SHIFT)) | \
+           (pidx.astype(np.uint64) << np.uint64(_P_SHIFT)) | o.astype(np.uint64)
+
+
+def _unpack(k):
+    s = (k >> np.uint64(_S_SHIFT)).astype(np.int32)
+    pidx = ((k >> np.uint64(_P_SHIFT)) & np.uint64(127)).astype(np.int32)
+    o = (k & np.uint64((1 << 31) - 1)).astype(np.int32)
+    return s, pidx, o
+
+
+def _sorted_distinct(k: np.ndarray) -> np.ndarray:
+    k = np.sort(k)
+    if k.shape[0] < 2:
+        return k
+    keep = np.empty(k.shape[0], dtype=bool)
+    keep[0] = True
+    np.not_equal(k[1:], k[:-1], out=keep[1:])
+    return k[keep]
+
+
+def _unique_topup(rng, n, draw):
+    """Draw packed keys until at least n distinct ones exist; keep a seeded n-subset
+    in a seeded random order."""
+    keys = _sorted_distinct(draw(int(n * 1.08) + 1024))
+    while keys.shape[0] < n:
+        extra = draw(int((n - keys.shape[0]) * 1.5) + 1024)
+        keys = _sorted_distinct(np.concatenate([keys, extra]))
+    perm = rng.permutation(keys.shape[0])[:n]
+    return keys[perm]
+
+
+# ----------------------------------------------------------------------------
+# tiny workload (1M triples)
+# ----------------------------------------------------------------------------
+
+TINY_SUBJECTS = 100_000
+TINY_PREDICATES = 64
+TINY_OBJECTS = 200_000
+
+
+def tiny_store(n: int = 1_000_000, seed: int = STORE_SEED) -> Store:
+    def build():
+        rng = np.random.default_rng(seed)
+        cp = zipf_cdf(1.2, TINY_PREDICATES)
+        co = zipf_cdf(1.1, TINY_OBJECTS)
+
+        def draw(m):
+            s = rng.integers(1, TINY_SUBJECTS + 1, size=m)
+            p = zipf_ranks(rng, m, cp)
+            o = zipf_ranks(rng, m, co)
+            return _pack(s, p, o)
+
+        keys = _unique_topup(rng, n, draw)
+        s, p, o = _unpack(keys)
+        return (np.ascontiguousarray(s), np.ascontiguousarray(p),
+                np.ascontiguousarray(o))
+
+    s, p, o = _cached(f"tiny|{n}|{seed}", build)
+    return Store(s, p, o, name=f"tiny-{n}", meta={"seed": seed})
+
+
+def tiny_queries(store: Store, seed: int = QUERY_SEED, per_shape: int = 4):
+    """4 each of (s,?,?), (?,p,?), (?,p,o), (s,p,?), keyed from uniformly drawn
+    stored triples (so none is empty)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for shape in ("s??", "?p?", "?po", "sp?"):
+        rows = rng.integers(0, store.n, size=per_shape)
+        for r in rows:
+            t = (int(store.s[r]), int(store.p[r]), int(store.o[r]))
+            key = tuple(t[j] if shape[j] != "?" else 0 for j in range(3))
+            var = tuple(-1 if key[j] else j for j in range(3))
+            out.append(Pattern(*key, var=var))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# university-shaped workload (200M at full size)
+# ----------------------------------------------------------------------------
+
+UNI_FULL = 200_000_000
+CLASS_FRACTIONS = np.array([.40, .20, .15, .10, .06, .04, .03, .02])
+SUBCLASSES = 512         # type objects: each top class has 511 subclasses + itself
+PRED_FREQ = np.array([.30, .12, .10, .08, .06, .05, .05, .04, .04, .03,
+                      .03, .02, .02, .015, .015, .01, .01, .005, .003, .002])
+# per predicate: (kind, domain classes, range classes or literal exponent)
+#   kind "type": object is a class ID of the subject's own top class, Zipf(0.5)
+#                over its 512 (sub)classes
+#   kind "lit":  object is LIT_BASE + uniform[0, 10^k)
+#   kind "ent":  object is an entity of the range classes, Zipf(1.1) within a class
+PRED_KIND = [
+    ("type", range(8), None),
+    ("lit", (0, 1), 2),
+    ("lit", range(8), 4),
+    ("lit", (2, 3), 7),
+    ("ent", (0,), (1,)),
+    ("lit", (0, 1, 2, 3), 5),
+    ("ent", (0, 1), (2,)),
+    ("ent", range(8), range(8)),
+    ("ent", (1,), (3,)),
+    ("lit", (4, 5, 6, 7), 3),
+    ("ent", (0,), (0,)),
+    ("lit", range(8), 6),
+    ("ent", (2, 3), (4, 5)),
+    ("ent", (4,), (5,)),
+    ("ent", (5, 6), (0,)),
+    ("ent", (1, 2), (6, 7)),
+    ("ent", (3,), (1, 2)),
+    ("ent", (6,), (3,)),
+    ("ent", (7,), (0, 1)),
+    ("ent", range(8), (7,)),
+]
+
+
+def uni_layout(subjects: int):
+    """ID layout of the university store for a given subject count."""
+    sizes = np.floor(CLASS_FRACTIONS * subjects).astype(np.int64)
+    sizes[0] += subjects - sizes.sum()
+    starts = 1 + np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    class_base = subjects + 1                       # 8 x 512 class IDs
+    pred_base = class_base + 8 * SUBCLASSES         # 20 predicate IDs
+    return {"sizes": sizes, "starts": starts, "class_base": class_base,
+            "pred_base": pred_base, "pred_ids": pred_base + np.arange(len(PRED_FREQ))}
+
+
+def uni_subjects(n: int) -> int:
+    # 5M subjects at 200M triples (40 triples per subject), scaled with n
+    return max(64, n // 40)
+
+
+def university_store(n: int = UNI_FULL, seed: int = STORE_SEED) -> Store:
+    subjects = uni_subjects(n)
+    lay = uni_layout(subjects)
+
+    def build():
+        rng = np.random.default_rng(seed)
+        cdf_sub = zipf_cdf(0.5, SUBCLASSES)
+        ccdf = {}
+
+        def class_cdf(c):
+            if c not in ccdf:
+                ccdf[c] = zipf_cdf(1.1, int(lay["sizes"][c]))
+            return ccdf[c]
+
+        sizes, starts = lay["sizes"], lay["starts"]
+
+        def draw_subjects(m, dom):
+            dom = np.asarray(list(dom))
+            w = sizes[dom] / sizes[dom].sum()
+            cls = dom[np.searchsorted(np.cumsum(w), rng.random(m), side="right").clip(0, len(dom) - 1)]
+            off = (rng.random(m) * sizes[cls]).astype(np.int64)
+            return starts[cls] + off, cls
+
+        def draw(m):
+            counts = rng.multinomial(m, PRED_FREQ)
+            parts = []
+            for j, (kind, dom, rng_or_k) in enumerate(PRED_KIND):
+                mj = int(counts[j])
+                if mj == 0:
+                    continue
+                s, cls = draw_subjects(mj, dom)
+                if kind == "type":
+                    o = lay["class_base"] + cls * SUBCLASSES + (zipf_ranks(rng, mj, cdf_sub) - 1)
+                elif kind == "lit":
+                    o = LIT_BASE + rng.integers(0, 10 ** rng_or_k, size=mj)
+                else:
+                    rcls = np.asarray(list(rng_or_k))
+                    w = sizes[rcls] / sizes[rcls].sum()
+                    pick = rcls[np.searchsorted(np.cumsum(w), rng.random(mj), side="right").clip(0, len(rcls) - 1)]
+                    o = np.empty(mj, np.int64)
+                    for c in np.unique(pick):
+                        sel = pick == c
+                        o[sel] = starts[c] + zipf_ranks(rng, int(sel.sum()), class_cdf(int(c))) - 1
+                parts.append(_pack(s, np.full(mj, j), o))
+            return np.concatenate(parts)
+
+        keys = _unique_topup(rng, n, draw)
+        s, pidx, o = _unpack(keys)
+        p = lay["pred_ids"][pidx].astype(np.int32)
+        return (np.ascontiguousarray(s), np.ascontiguousarray(p),
+                np.ascontiguousarray(o))
+
+    s, p, o = _cached(f"uni|{n}|{seed}", build)
+    return Store(s, p, o, name=f"university-{n}",
+                 meta={"seed": seed, "subjects": subjects, **{k: v for k, v in lay.items()}})
+
+
+def _tally(a: np.ndarray):
+    """Distinct values of a and how often each occurs (sort based)."""
+    a = np.sort(a)
+    if a.shape[0] == 0:
+        return a, np.zeros(0, np.int64)
+    start = np.flatnonzero(np.concatenate([[True], a[1:] != a[:-1]]))
+    counts = np.diff(np.concatenate([start, [a.shape[0]]]))
+    return a[start], counts
+
+
+def university_queries(store: Store, m: int = 64, seed: int = QUERY_SEED,
+                       lo: float = 1e-6, hi: float = 0.3):
+    """m single-pattern queries whose result size is as close as the store allows to a
+    target selectivity drawn log-uniformly on [lo, hi].  Candidate shapes are
+    (?,p,?), (?,p,o), (?,?,o) and (s,?,?); their sizes come from value tallies of
+    the store (these choose constants; they are not query answers)."""
+    rng = np.random.default_rng(seed)
+    n = store.n
+    cands = []  # (count, pattern)
+    pv, pc = _tally(store.p)
+    cands += [(int(c), Pattern(0, int(v), 0, var=(0, -1, 1))) for v, c in zip(pv, pc)]
+    po = (store.p.astype(np.int64) << 32) | store.o.astype(np.int64)
+    pov, poc = _tally(po)
+    ov, oc = _tally(store.o)
+    sv, sc = _tally(store.s)
+    # keep the candidate lists small: one representative per distinct count bucket
+    def reps(vals, counts, mk, per_decade=24):
+        keyb = np.floor(np.log10(counts.astype(np.float64)) * per_decade).astype(np.int64)
+        _, first = np.unique(keyb, return_index=True)
+        return [(int(counts[i]), mk(int(vals[i]))) for i in first]
+    cands += reps(pov, poc, lambda x: Pattern(0, x >> 32, x & 0xFFFFFFFF, var=(0, -1, -1)))
+    cands += reps(ov, oc, lambda x: Pattern(0, 0, x, var=(0, 1, -1)))
+    cands += reps(sv, sc, lambda x: Pattern(x, 0, 0, var=(-1, 0, 1)))
+    counts = np.array([c for c, _ in cands], dtype=np.float64)
+    targets = np.exp(rng.uniform(np.log(lo), np.log(hi), size=m))
+    out = []
+    for t in targets:
+        i = int(np.argmin(np.abs(np.log(counts) - np.log(t * n))))
+        c, pat = cands[i]
+        out.append((pat, float(t), c / n))
+    return out

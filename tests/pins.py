@@ -1,0 +1,291 @@
+"""Pins for the CPU oracle: facts fixed by the paper or by mathematics, computed
+WITHOUT the oracle's own formulas.
+
+* the worked example the paper prints (Rule 11, golden file);
+* solution-mapping brute force: a pattern's answers are the substitutions of
+  its variables, drawn from the store's domain, whose instantiated triple is in
+  the graph -- a different statement of "matches" than the oracle's per-slot
+  wildcard test, and the one that also defines joins of several patterns;
+* value tallies (np.bincount / sort-based counts) for single- and two-bound
+  patterns, and the total N for (?,?,?);
+* algebraic laws of union, filter and join (cross product then selection).
+
+Each pin raises AssertionError when the oracle disagrees.  ``ALL_PINS`` is run
+both against the real oracle and against mutated copies of it, which must fail.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+from collections import Counter
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ---------------------------------------------------------------------------
+# solution-mapping brute force (independent of the oracle)
+# ---------------------------------------------------------------------------
+
+def tiny_graph(seed, n, ids=8):
+    """A random set of <= n triples over IDs 1..ids, in random order."""
+    rng = np.random.default_rng(seed)
+    t = rng.integers(1, ids + 1, size=(n, 3))
+    seen, rows = set(), []
+    for r in map(tuple, t.tolist()):
+        if r not in seen:
+            seen.add(r)
+            rows.append(r)
+    a = np.array(rows, dtype=np.int32).reshape(-1, 3)
+    return a[:, 0].copy(), a[:, 1].copy(), a[:, 2].copy()
+
+
+def _slots(key, var, fresh):
+    """Slot terms: ('c', id) for a constant, ('v', name) for a variable."""
+    out = []
+    for j in range(3):
+        if int(key[j]) != 0:
+            out.append(("c", int(key[j])))
+        elif int(var[j]) >= 0:
+            out.append(("v", ("named", int(var[j]))))
+        else:
+            out.append(("v", ("anon", next(fresh))))
+    return out
+
+
+def solutions(S, P, O, patterns, project_vars):
+    """Distinct projections of the substitutions (over the graph's domain) under
+    which every pattern instantiates to a stored triple."""
+    G = set(zip(S.tolist(), P.tolist(), O.tolist()))
+    dom = sorted(set(S.tolist()) | set(P.tolist()) | set(O.tolist()))
+    fresh = itertools.count()
+    slotted = [_slots(k, v, fresh) for k, v in patterns]
+    names = []
+    for sl in slotted:
+        for kind, x in sl:
+            if kind == "v" and x not in names:
+                names.append(x)
+    out = set()
+    for theta in itertools.product(dom, repeat=len(names)):
+        env = dict(zip(names, theta))
+        if all(tuple(x if kind == "c" else env[x] for kind, x in sl) in G for sl in slotted):
+            out.add(tuple(env[("named", v)] for v in project_vars))
+    return sorted(out)
+
+
+def positions(S, P, O, key):
+    """Positions of the stored triples that are instances of the key (0 = "?"),
+    by enumerating substitutions of the "?" slots."""
+    index = {t: i for i, t in enumerate(zip(S.tolist(), P.tolist(), O.tolist()))}
+    dom = sorted(set(S.tolist()) | set(P.tolist()) | set(O.tolist()))
+    free = [j for j in range(3) if int(key[j]) == 0]
+    hits = []
+    for theta in itertools.product(dom, repeat=len(free)):
+        t = [int(x) for x in key]
+        for j, v in zip(free, theta):
+            t[j] = v
+        i = index.get(tuple(t))
+        if i is not None:
+            hits.append(i)
+    return sorted(hits)
+
+
+# ---------------------------------------------------------------------------
+# pins
+# ---------------------------------------------------------------------------
+
+def pin_golden_rule11(o):
+    """Section 5, Rule (11) worked example: values printed in the paper."""
+    g = json.load(open(os.path.join(GOLDEN, "rule11_worked_example.json")))
+    st = np.array(g["store"], np.int32)
+    S, P, O = st[:, 0].copy(), st[:, 1].copy(), st[:, 2].copy()
+    n = len(st)
+    idx = o.match(S, P, O, g["step1"]["key"])
+    flags = np.zeros(n, int)
+    flags[idx] = 1
+    assert flags.tolist() == g["step1"]["flags"], (flags, g["step1"])
+    lists = o.match_multi(S, P, O, g["step2"]["keys"])
+    flags2 = np.zeros(n, int)
+    for lst in lists:
+        flags2[lst] = 1
+    assert flags2.tolist() == g["step2"]["flags"], (flags2, g["step2"])
+    # x subClassOf y . y subClassOf z  -> (x, z)
+    X, Y, Z = 0, 1, 2
+    a = o.bind(S, P, O, (0, 84, 0), (X, -1, Y), o.match(S, P, O, (0, 84, 0)))
+    b = o.bind(S, P, O, (0, 84, 0), (Y, -1, Z), o.match(S, P, O, (0, 84, 0)))
+    r = o.project(o.join(a, b), (X, Z))
+    assert r.vars == (X, Z)
+    assert sorted(map(tuple, r.rows.tolist())) == sorted(map(tuple, g["result_xz"])), r.rows
+
+
+def pin_match_bruteforce(o):
+    """Every key in {0..8}^3 on small random graphs: positions equal the
+    substitution-enumeration answer."""
+    for seed, n in ((1, 40), (2, 64), (3, 7)):
+        S, P, O = tiny_graph(seed, n)
+        for key in itertools.product(range(9), repeat=3):
+            got = o.match(S, P, O, key).tolist()
+            assert got == positions(S, P, O, key), (seed, key)
+    S, P, O = (np.zeros(0, np.int32),) * 3
+    assert o.match(S, P, O, (0, 0, 0)).tolist() == []
+
+
+def pin_match_tallies(o):
+    """Counts equal value tallies: count(s,?,?) = occurrences of s in S (and for
+    p, o); count(s,p,?) = occurrences of the pair; count(?,?,?) = N."""
+    rng = np.random.default_rng(7)
+    n = 20000
+    S = rng.integers(1, 300, n).astype(np.int32)
+    P = rng.integers(1, 12, n).astype(np.int32)
+    O = rng.integers(1, 500, n).astype(np.int32)
+    assert o.match(S, P, O, (0, 0, 0)).shape[0] == n
+    for col, pos in ((S, 0), (P, 1), (O, 2)):
+        h = np.bincount(col)
+        for v in rng.choice(np.unique(col), 10, replace=False):
+            key = [0, 0, 0]
+            key[pos] = int(v)
+            assert o.match(S, P, O, key).shape[0] == h[v], (pos, v)
+    pair = Counter(zip(S.tolist(), P.tolist()))
+    for (s, p) in list(pair)[:40]:
+        assert o.match(S, P, O, (s, p, 0)).shape[0] == pair[(s, p)]
+    pairo = Counter(zip(P.tolist(), O.tolist()))
+    for (p, oo) in list(pairo)[:40]:
+        assert o.match(S, P, O, (0, p, oo)).shape[0] == pairo[(p, oo)]
+    tot = sum(o.match(S, P, O, (0, int(p), 0)).shape[0] for p in np.unique(P))
+    assert tot == n
+    # multi-key lists equal the single-key lists (one pass vs many)
+    keys = [(0, 3, 0), (5, 0, 0), (0, 0, 7), (0, 3, 0), (5, 3, 0)]
+    multi = o.match_multi(S, P, O, keys)
+    for k, lst in zip(keys, multi):
+        assert lst.shape[0] == o.match(S, P, O, k).shape[0]
+
+
+def pin_bind_join_bruteforce(o):
+    """Two-pattern conjunctions in all nine relationship types of the paper's
+    table (shared variable at S/P/O on either side), plus repeated variables:
+    bind + join + project equals the solution-mapping enumeration."""
+    X, Y, Z, W = 0, 1, 2, 3
+    # (pattern A, pattern B) with keys drawn per case; slot of the shared var varies
+    shapes = []
+    for ia in range(3):
+        for ib in range(3):
+            va, vb = [-1, -1, -1], [-1, -1, -1]
+            va[ia] = X
+            vb[ib] = X
+            va[(ia + 1) % 3] = Y
+            vb[(ib + 2) % 3] = Z
+            shapes.append((tuple(va), tuple(vb)))
+    shapes.append(((X, -1, X), (X, -1, Y)))          # repeated variable
+    shapes.append(((X, Y, -1), (X, Y, Z)))           # two shared variables
+    shapes.append(((X, -1, Y), (W, -1, Z)))          # no shared variable: cross product
+    for seed in (11, 12):
+        S, P, O = tiny_graph(seed, 30, ids=5)
+        rng = np.random.default_rng(seed)
+        for va, vb in shapes:
+            ka = tuple(0 if va[j] >= 0 else int(rng.integers(1, 6)) for j in range(3))
+            kb = tuple(0 if vb[j] >= 0 else int(rng.integers(1, 6)) for j in range(3))
+            # keep some cases all-variable in the unconstrained slot
+            a = o.bind(S, P, O, ka, va, o.match(S, P, O, ka))
+            b = o.bind(S, P, O, kb, vb, o.match(S, P, O, kb))
+            j = o.join(a, b)
+            want = solutions(S, P, O, [(ka, va), (kb, vb)], j.vars)
+            assert sorted(map(tuple, j.rows.tolist())) == want, (seed, va, vb, ka, kb)
+            assert j.rows.tolist() == [list(r) for r in want]  # canonical order
+            # |join| = sum over keys of cntL * cntR (no zero keys here)
+            sh = [v for v in a.vars if v in b.vars]
+            ca = Counter(tuple(r[a.vars.index(v)] for v in sh) for r in a.rows.tolist())
+            cb = Counter(tuple(r[b.vars.index(v)] for v in sh) for r in b.rows.tolist())
+            assert j.n == sum(ca[k] * cb.get(k, 0) for k in ca)
+
+
+def pin_join_cross_product(o):
+    """join(L, R) = rows of L x R whose shared columns agree (and are bound)."""
+    rng = np.random.default_rng(5)
+    for trial in range(30):
+        kl, kr = int(rng.integers(1, 4)), int(rng.integers(1, 4))
+        lv = tuple(rng.choice(6, kl, replace=False).tolist())
+        rv = tuple(rng.choice(6, kr, replace=False).tolist())
+        L = o.TupleSet(lv, o.canonical(rng.integers(0, 4, (int(rng.integers(0, 25)), kl))))
+        R = o.TupleSet(rv, o.canonical(rng.integers(0, 4, (int(rng.integers(0, 25)), kr))))
+        j = o.join(L, R)
+        sh = [v for v in lv if v in rv]
+        want = set()
+        for l in L.rows.tolist():
+            for r in R.rows.tolist():
+                if all(l[lv.index(v)] == r[rv.index(v)] and l[lv.index(v)] != 0 for v in sh):
+                    want.add(tuple(l) + tuple(r[i] for i, v in enumerate(rv) if v not in lv))
+        assert j.rows.tolist() == [list(x) for x in sorted(want)], trial
+        js = o.join(L, R, method="sortmerge")
+        assert np.array_equal(js.rows, j.rows)
+
+
+def pin_union_laws(o):
+    """Union is commutative and idempotent, pads missing variables with 0, and
+    equals the Python set union of padded rows."""
+    rng = np.random.default_rng(9)
+    A = o.TupleSet((0, 1), o.canonical(rng.integers(1, 5, (30, 2))))
+    B = o.TupleSet((1, 2), o.canonical(rng.integers(1, 5, (30, 2))))
+    C = o.TupleSet((0, 1), o.canonical(rng.integers(1, 5, (30, 2))))
+    u = o.union([A, C])
+    assert np.array_equal(u.rows, o.union([C, A]).rows)
+    assert np.array_equal(o.union([A, A]).rows, A.rows)
+    assert np.array_equal(o.union([u, A]).rows, u.rows)
+    want = sorted(set(map(tuple, A.rows.tolist())) | set(map(tuple, C.rows.tolist())))
+    assert u.rows.tolist() == [list(x) for x in want]
+    ab = o.union([A, B])
+    assert ab.vars == (0, 1, 2)
+    want = sorted({(a, b, 0) for a, b in A.rows.tolist()} | {(0, b, c) for b, c in B.rows.tolist()})
+    assert ab.rows.tolist() == [list(x) for x in want]
+
+
+def pin_filter_algebra(o):
+    """Full range is the identity on bound rows; ranges compose by
+    intersection; EQ/NE split the bound rows; LT/LE/GT/GE are ranges; a row
+    whose value is 0 (unbound) never passes."""
+    rng = np.random.default_rng(4)
+    T = o.TupleSet((3, 4), o.canonical(rng.integers(0, 50, (400, 2))))
+    col = T.rows[:, 1]
+    bound = T.rows[col != 0]
+    full = o.filter(T, 4, "range", 1, 2 ** 31 - 1)
+    assert np.array_equal(full.rows, bound)
+    for a, b, c, d in ((3, 30, 10, 40), (0, 49, 20, 20), (5, 9, 12, 15)):
+        two = o.filter(o.filter(T, 4, "range", a, b), 4, "range", c, d)
+        one = o.filter(T, 4, "range", max(a, c), min(b, d))
+        assert np.array_equal(two.rows, one.rows)
+    for v in (0, 1, 17, 49):
+        eq = o.filter(T, 4, "eq", v)
+        ne = o.filter(T, 4, "ne", v)
+        assert eq.n + ne.n == bound.shape[0]
+        assert np.array_equal(eq.rows, o.filter(T, 4, "range", v, v).rows)
+        assert np.array_equal(o.filter(T, 4, "lt", v).rows, o.filter(T, 4, "range", -2 ** 31, v - 1).rows)
+        assert np.array_equal(o.filter(T, 4, "le", v).rows, o.filter(T, 4, "range", -2 ** 31, v).rows)
+        assert np.array_equal(o.filter(T, 4, "gt", v).rows, o.filter(T, 4, "range", v + 1, 2 ** 31 - 1).rows)
+        assert np.array_equal(o.filter(T, 4, "ge", v).rows, o.filter(T, 4, "range", v, 2 ** 31 - 1).rows)
+        assert (o.filter(T, 4, "ge", v).rows[:, 1] >= max(v, 1)).all()
+    # numbers counted directly
+    assert o.filter(T, 4, "range", 10, 20).n == int(((col >= 10) & (col <= 20)).sum())
+
+
+def pin_canonical(o):
+    """Canonical form = Python's sorted set of row tuples."""
+    rng = np.random.default_rng(3)
+    for k in (1, 2, 3, 5, 8):
+        rows = rng.integers(-3, 6, (300, k))
+        got = o.canonical(rows)
+        want = sorted(set(map(tuple, rows.tolist())))
+        assert got.tolist() == [list(x) for x in want], k
+
+
+def pin_project(o):
+    rng = np.random.default_rng(6)
+    T = o.TupleSet((0, 1, 2), o.canonical(rng.integers(1, 6, (200, 3))))
+    pr = o.project(T, (2, 0))
+    want = sorted({(c, a) for a, b, c in T.rows.tolist()})
+    assert pr.vars == (2, 0) and pr.rows.tolist() == [list(x) for x in want]
+
+
+ALL_PINS = [pin_golden_rule11, pin_match_bruteforce, pin_match_tallies,
+            pin_bind_join_bruteforce, pin_join_cross_product, pin_union_laws,
+            pin_filter_algebra, pin_canonical, pin_project]
