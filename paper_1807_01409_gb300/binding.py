@@ -1,0 +1,239 @@
+"""Thin Python binding of libtid.so (include/tid.h), by ctypes.
+
+The functions carry the C names and only marshal arguments: every step of the
+query path runs in the library's CUDA kernels.  Device buffers may be torch
+CUDA tensors (their ``data_ptr()`` is passed); host buffers numpy arrays.  If the
+library has not been built, the first call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtid.so")
+
+TID_OK, TID_ERR_ARG, TID_ERR_ID, TID_ERR_OOM, TID_ERR_CAPACITY, TID_ERR_TIMEOUT, TID_ERR_CUDA = range(7)
+TID_HOST, TID_DEVICE = 0, 1
+TID_MAX_COLS = 8
+TID_MAX_MULTI = 16
+ERR_NAMES = {0: "TID_OK", 1: "TID_ERR_ARG", 2: "TID_ERR_ID", 3: "TID_ERR_OOM",
+             4: "TID_ERR_CAPACITY", 5: "TID_ERR_TIMEOUT", 6: "TID_ERR_CUDA"}
+
+
+class TidError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class tid_pattern(C.Structure):
+    _fields_ = [("s", C.c_int32), ("p", C.c_int32), ("o", C.c_int32),
+                ("var", C.c_int8 * 3), ("reserved", C.c_int8)]
+
+
+def make_pattern(s=0, p=0, o=0, var=(-1, -1, -1)) -> tid_pattern:
+    """A pattern from (s, p, o) with 0 = "?", and variable ids per slot (-1 = none)."""
+    pt = tid_pattern()
+    pt.s, pt.p, pt.o = int(s), int(p), int(o)
+    for j in range(3):
+        pt.var[j] = int(var[j])
+    pt.reserved = 0
+    return pt
+
+
+def as_pattern(x) -> tid_pattern:
+    if isinstance(x, tid_pattern):
+        return x
+    if hasattr(x, "key") and hasattr(x, "var"):
+        return make_pattern(*x.key(), var=x.var)
+    x = tuple(x)
+    return make_pattern(*x[:3], var=x[3] if len(x) > 3 else (-1, -1, -1))
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def lib():
+    """Load libtid.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libtid.so not built ({LIB_PATH}); run paper_1807_01409_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    i32p, i64p, i8p = C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int8)
+    sig = {
+        "tid_last_error": (C.c_char_p, []),
+        "tid_ctx_create": (C.c_int, [C.c_int, _vp, C.POINTER(_vp)]),
+        "tid_ctx_sync": (C.c_int, [_vp]),
+        "tid_ctx_destroy": (C.c_int, [_vp]),
+        "tid_load": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int, C.c_int, C.POINTER(_vp)]),
+        "tid_store_info": (C.c_int, [_vp, i64p, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp)]),
+        "tid_store_free": (C.c_int, [_vp]),
+        "tid_match": (C.c_int, [_vp, _vp, tid_pattern, C.POINTER(_vp)]),
+        "tid_set_rows": (C.c_int, [_vp, i64p]),
+        "tid_set_info": (C.c_int, [_vp, C.POINTER(C.c_int), i64p, C.POINTER(i8p),
+                                   C.POINTER(C.POINTER(_vp)), C.POINTER(_vp)]),
+        "tid_set_to_host": (C.c_int, [_vp, _vp, C.c_int64, i64p]),
+        "tid_set_free": (C.c_int, [_vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return lib().tid_last_error().decode()
+
+
+def _check(rc, what):
+    if rc != TID_OK:
+        raise TidError(rc, f"{what}: {last_error()}")
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array / int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+# ---------------------------------------------------------------------------
+# C entry points (same names)
+# ---------------------------------------------------------------------------
+
+def tid_ctx_create(device: int = 0, stream=None):
+    """stream: a cudaStream_t as int (e.g. torch.cuda.current_stream().cuda_stream) or None."""
+    out = _vp()
+    _check(lib().tid_ctx_create(int(device), stream if stream else None, C.byref(out)), "tid_ctx_create")
+    return out
+
+
+def tid_ctx_sync(ctx):
+    _check(lib().tid_ctx_sync(ctx), "tid_ctx_sync")
+
+
+def tid_ctx_destroy(ctx):
+    _check(lib().tid_ctx_destroy(ctx), "tid_ctx_destroy")
+
+
+def tid_load(ctx, s, p, o, n=None, where=None, copy=1):
+    """Columns are torch CUDA tensors (where=TID_DEVICE), or numpy / CPU tensors (TID_HOST)."""
+    if n is None:
+        n = int(s.shape[0])
+    if where is None:
+        where = TID_DEVICE if (hasattr(s, "is_cuda") and s.is_cuda) else TID_HOST
+    for c in (s, p, o):
+        if hasattr(c, "dtype") and str(c.dtype) not in ("int32", "torch.int32"):
+            raise TypeError("store columns must be int32")
+        if isinstance(c, np.ndarray) and not c.flags["C_CONTIGUOUS"]:
+            raise ValueError("store columns must be contiguous")
+        if hasattr(c, "is_contiguous") and not c.is_contiguous():
+            raise ValueError("store columns must be contiguous")
+    out = _vp()
+    _check(lib().tid_load(ctx, _ptr(s), _ptr(p), _ptr(o), int(n), int(where), int(copy), C.byref(out)),
+           "tid_load")
+    return out
+
+
+def tid_store_info(st):
+    n = C.c_int64()
+    s, p, o = _vp(), _vp(), _vp()
+    _check(lib().tid_store_info(st, C.byref(n), C.byref(s), C.byref(p), C.byref(o)), "tid_store_info")
+    return n.value, s.value, p.value, o.value
+
+
+def tid_store_free(st):
+    _check(lib().tid_store_free(st), "tid_store_free")
+
+
+def tid_match(ctx, st, pattern):
+    out = _vp()
+    _check(lib().tid_match(ctx, st, as_pattern(pattern), C.byref(out)), "tid_match")
+    return out
+
+
+def tid_set_rows(set_) -> int:
+    r = C.c_int64()
+    _check(lib().tid_set_rows(set_, C.byref(r)), "tid_set_rows")
+    return r.value
+
+
+def tid_set_info(set_):
+    k = C.c_int()
+    cap = C.c_int64()
+    vars_ = C.POINTER(C.c_int8)()
+    cols = C.POINTER(_vp)()
+    drows = _vp()
+    _check(lib().tid_set_info(set_, C.byref(k), C.byref(cap), C.byref(vars_), C.byref(cols),
+                              C.byref(drows)), "tid_set_info")
+    return {"cols": k.value, "capacity": cap.value,
+            "vars": tuple(vars_[i] for i in range(k.value)),
+            "dev_cols": tuple(cols[i] for i in range(k.value)), "dev_rows": drows.value}
+
+
+def tid_set_to_host(set_, buf=None):
+    """Rows as a (rows, k) int32 numpy array (row-major)."""
+    info = tid_set_info(set_)
+    rows = tid_set_rows(set_)
+    if buf is None:
+        buf = np.empty((rows, info["cols"]), np.int32)
+    got = C.c_int64()
+    _check(lib().tid_set_to_host(set_, _ptr(buf) if buf.size else None, buf.shape[0], C.byref(got)),
+           "tid_set_to_host")
+    return buf[:got.value]
+
+
+def tid_set_free(set_):
+    _check(lib().tid_set_free(set_), "tid_set_free")
+
+
+# ---------------------------------------------------------------------------
+# small conveniences (no computation)
+# ---------------------------------------------------------------------------
+
+class Context:
+    """Owns a tid_ctx; frees the stores and sets made through it on close()."""
+
+    def __init__(self, device=0, stream=None):
+        self.h = tid_ctx_create(device, stream)
+        self._owned = []
+
+    def load(self, s, p, o, **kw):
+        st = tid_load(self.h, s, p, o, **kw)
+        self._owned.append(("store", st))
+        return st
+
+    def track(self, set_):
+        self._owned.append(("set", set_))
+        return set_
+
+    def sync(self):
+        tid_ctx_sync(self.h)
+
+    def close(self):
+        for kind, h in reversed(self._owned):
+            (tid_store_free if kind == "store" else tid_set_free)(h)
+        self._owned = []
+        if self.h:
+            tid_ctx_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

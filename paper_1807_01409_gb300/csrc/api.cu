@@ -1,0 +1,450 @@
+// Context, store and tuple-set management behind the C ABI (include/tid.h).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "tid_internal.cuh"
+
+namespace tid {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int fail_cuda(cudaError_t e, const char *what) {
+    cudaGetLastError();  // clear a non-sticky error so later calls can proceed
+    if (e == cudaErrorMemoryAllocation) return fail(TID_ERR_OOM, "%s: out of device memory", what);
+    return fail(TID_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void clear_error() { g_err.clear(); }
+
+int launch_check(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e, what);
+    return TID_OK;
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+}
+DeviceGuard::~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+}
+
+// ---------------------------------------------------------------------------
+// memory
+// ---------------------------------------------------------------------------
+int dev_alloc(tid_ctx *ctx, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail_cuda(e, "device allocation");
+    }
+    return TID_OK;
+}
+
+void dev_free(tid_ctx *ctx, void *p) {
+    if (p) cudaFreeAsync(p, ctx->stream);
+}
+
+int next_epoch(tid_ctx *ctx) {
+    ctx->epoch = (ctx->epoch + 1) & ((1u << 30) - 1);
+    if (ctx->epoch == 0) ctx->epoch = 1;
+    return (int)ctx->epoch;
+}
+
+// Look-back scratch for `num_tiles` tiles: grown on demand (new words are
+// zeroed, i.e. "not ready" for every epoch), ticket counter at 0.
+int lookback_scratch(tid_ctx *ctx, unsigned int num_tiles, Lookback *lb) {
+    if (num_tiles > ctx->lb_cap) {
+        size_t want = 1024;
+        while (want < num_tiles) want *= 2;
+        if (ctx->lb_status) dev_free(ctx, ctx->lb_status);
+        ctx->lb_status = nullptr;
+        ctx->lb_cap = 0;
+        void *p = nullptr;
+        TID_TRY(dev_alloc(ctx, &p, want * sizeof(unsigned long long) + 256));
+        TID_TRY_CUDA(cudaMemsetAsync(p, 0, want * sizeof(unsigned long long) + 256, ctx->stream),
+                     "clear look-back scratch");
+        ctx->lb_status = (unsigned long long *)p;
+        ctx->lb_ticket = (unsigned int *)((char *)p + want * sizeof(unsigned long long));
+        ctx->lb_cap = want;
+    }
+    lb->status = ctx->lb_status;
+    lb->ticket = ctx->lb_ticket;
+    lb->epoch = (unsigned)next_epoch(ctx);
+    lb->num_tiles = num_tiles;
+    lb->err = ctx->err_dev;
+    return TID_OK;
+}
+
+// ---------------------------------------------------------------------------
+// row-count slots (mapped pinned host memory)
+// ---------------------------------------------------------------------------
+static constexpr int SLAB_SLOTS = 4096;
+
+static void sweep_pending(tid_ctx *ctx, bool wait) {
+    auto &pend = ctx->pending;
+    size_t w = 0;
+    for (size_t i = 0; i < pend.size(); ++i) {
+        cudaError_t q = wait ? cudaEventSynchronize(pend[i].ev) : cudaEventQuery(pend[i].ev);
+        if (q == cudaSuccess || q != cudaErrorNotReady) {
+            cudaEventDestroy(pend[i].ev);
+            ctx->free_slots.push_back({pend[i].slot.slab, pend[i].slot.index});
+        } else {
+            pend[w++] = pend[i];
+        }
+    }
+    pend.resize(w);
+}
+
+static int slot_acquire(tid_ctx *ctx, Slot *s) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->free_slots.empty()) sweep_pending(ctx, false);
+    if (ctx->free_slots.empty()) {
+        void *h = nullptr;
+        TID_TRY_CUDA(cudaHostAlloc(&h, SLAB_SLOTS * sizeof(int64_t), cudaHostAllocMapped),
+                     "pinned slot slab");
+        void *d = nullptr;
+        cudaError_t e = cudaHostGetDevicePointer(&d, h, 0);
+        if (e != cudaSuccess) {
+            cudaFreeHost(h);
+            return fail_cuda(e, "mapped slot slab");
+        }
+        const int slab = (int)ctx->slabs_host.size();
+        ctx->slabs_host.push_back((int64_t *)h);
+        ctx->slabs_dev.push_back((int64_t *)d);
+        for (int i = SLAB_SLOTS - 1; i >= 0; --i) ctx->free_slots.push_back({slab, i});
+    }
+    auto si = ctx->free_slots.back();
+    ctx->free_slots.pop_back();
+    s->slab = si.first;
+    s->index = si.second;
+    s->host = ctx->slabs_host[si.first] + si.second;
+    s->dev = ctx->slabs_dev[si.first] + si.second;
+    *(volatile int64_t *)s->host = -1;
+    return TID_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sets
+// ---------------------------------------------------------------------------
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int set_alloc(tid_ctx *ctx, int k, const int8_t *vars, int64_t cap, tid_set **out) {
+    *out = nullptr;
+    if (k < 1 || k > TID_MAX_COLS) return fail(TID_ERR_ARG, "set with %d columns", k);
+    if (cap < 0) cap = 0;
+    tid_set *s = new (std::nothrow) tid_set();
+    if (!s) return fail(TID_ERR_OOM, "host allocation");
+    s->ctx = ctx;
+    s->k = k;
+    for (int c = 0; c < k; ++c) s->vars[c] = vars[c];
+    s->cap = cap;
+    const size_t colb = align_up((size_t)cap * sizeof(int32_t), 256);
+    const size_t bytes = colb * (size_t)k + 256;
+    int rc = dev_alloc(ctx, &s->block, bytes);
+    if (rc != TID_OK) {
+        delete s;
+        return rc;
+    }
+    for (int c = 0; c < k; ++c) s->col[c] = (int32_t *)((char *)s->block + colb * c);
+    s->d_rows = (int64_t *)((char *)s->block + colb * k);
+    rc = slot_acquire(ctx, &s->slot);
+    if (rc == TID_OK) {
+        cudaError_t e = cudaEventCreateWithFlags(&s->ready, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            s->ready = nullptr;
+            rc = fail_cuda(e, "event");
+        }
+    }
+    if (rc != TID_OK) {
+        tid_set_free(s);
+        return rc;
+    }
+    *out = s;
+    return TID_OK;
+}
+
+int set_ready(tid_set *set) {
+    TID_TRY_CUDA(cudaEventRecord(set->ready, set->ctx->stream), "event record");
+    return TID_OK;
+}
+
+int check_ctx_error(tid_ctx *ctx) {
+    int e = *(volatile int *)ctx->err_host;
+    if (e != 0) {
+        *(volatile int *)ctx->err_host = 0;
+        // a launch that gave up may leave the ticket counter off zero
+        if (ctx->lb_ticket) cudaMemsetAsync(ctx->lb_ticket, 0, sizeof(unsigned int), ctx->stream);
+        if (e == TID_ERR_TIMEOUT) return fail(TID_ERR_TIMEOUT, "an in-kernel wait gave up");
+        return fail(e, "kernel reported error %d", e);
+    }
+    return TID_OK;
+}
+
+// rows x k row-major from k columns
+__global__ void k_interleave(const int32_t *const *cols, int k, const int64_t *d_rows, int32_t *out) {
+    const int64_t n = *d_rows;
+    const int64_t total = n * k;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / k;
+        const int c = (int)(i - r * k);
+        out[i] = cols[c][r];
+    }
+}
+
+}  // namespace tid
+
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+using namespace tid;
+
+extern "C" const char *tid_last_error(void) { return g_err.c_str(); }
+
+extern "C" int tid_ctx_create(int device, void *cuda_stream, tid_ctx **out) {
+    clear_error();
+    if (!out) return fail(TID_ERR_ARG, "tid_ctx_create: null out");
+    *out = nullptr;
+    int ndev = 0;
+    TID_TRY_CUDA(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(TID_ERR_ARG, "tid_ctx_create: no device %d", device);
+    DeviceGuard g(device);
+    tid_ctx *c = new (std::nothrow) tid_ctx();
+    if (!c) return fail(TID_ERR_OOM, "host allocation");
+    c->device = device;
+    cudaError_t e = cudaSuccess;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        c->own_stream = true;
+    }
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        e = cudaMemPoolCreate(&c->pool, &props);
+        if (e == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    }
+    void *h = nullptr;
+    if (e == cudaSuccess) e = cudaHostAlloc(&h, 256, cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        c->err_host = (int *)h;
+        *c->err_host = 0;
+        void *d = nullptr;
+        e = cudaHostGetDevicePointer(&d, h, 0);
+        c->err_dev = (int *)d;
+    }
+    if (e != cudaSuccess) {
+        int rc = fail_cuda(e, "tid_ctx_create");
+        if (c->err_host) cudaFreeHost(c->err_host);
+        if (c->pool) cudaMemPoolDestroy(c->pool);
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return TID_OK;
+}
+
+extern "C" int tid_ctx_sync(tid_ctx *ctx) {
+    clear_error();
+    if (!ctx) return fail(TID_ERR_ARG, "tid_ctx_sync: null ctx");
+    DeviceGuard g(ctx->device);
+    TID_TRY_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    return check_ctx_error(ctx);
+}
+
+extern "C" int tid_ctx_destroy(tid_ctx *ctx) {
+    clear_error();
+    if (!ctx) return TID_OK;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        sweep_pending(ctx, true);
+    }
+    if (ctx->lb_status) cudaFreeAsync(ctx->lb_status, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto *h : ctx->slabs_host) cudaFreeHost(h);
+    if (ctx->err_host) cudaFreeHost(ctx->err_host);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return TID_OK;
+}
+
+extern "C" int tid_load(tid_ctx *ctx, const int32_t *s, const int32_t *p, const int32_t *o,
+                        int64_t n, int where, int copy, tid_store **out) {
+    clear_error();
+    if (!ctx || !out) return fail(TID_ERR_ARG, "tid_load: null argument");
+    *out = nullptr;
+    if (n < 0 || n > INT32_MAX) return fail(TID_ERR_ARG, "tid_load: n = %lld out of range", (long long)n);
+    if (n > 0 && (!s || !p || !o)) return fail(TID_ERR_ARG, "tid_load: null column");
+    if (where != TID_HOST && where != TID_DEVICE) return fail(TID_ERR_ARG, "tid_load: bad `where`");
+    DeviceGuard g(ctx->device);
+    tid_store *st = new (std::nothrow) tid_store();
+    if (!st) return fail(TID_ERR_OOM, "host allocation");
+    st->ctx = ctx;
+    st->n = n;
+    if (where == TID_DEVICE && !copy) {
+        st->s = s;
+        st->p = p;
+        st->o = o;
+    } else {
+        const size_t colb = align_up((size_t)n * sizeof(int32_t), 256);
+        int rc = dev_alloc(ctx, &st->owned, 3 * colb);
+        if (rc != TID_OK) {
+            delete st;
+            return rc;
+        }
+        int32_t *base = (int32_t *)st->owned;
+        int32_t *cs = base, *cp = (int32_t *)((char *)base + colb), *co = (int32_t *)((char *)base + 2 * colb);
+        const cudaMemcpyKind kind = where == TID_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        cudaError_t e = cudaSuccess;
+        if (n > 0) {
+            e = cudaMemcpyAsync(cs, s, (size_t)n * 4, kind, ctx->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(cp, p, (size_t)n * 4, kind, ctx->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(co, o, (size_t)n * 4, kind, ctx->stream);
+        }
+        if (e != cudaSuccess) {
+            dev_free(ctx, st->owned);
+            delete st;
+            return fail_cuda(e, "tid_load copy");
+        }
+        st->s = cs;
+        st->p = cp;
+        st->o = co;
+    }
+    st->aligned16 = ((uintptr_t)st->s % 16 == 0) && ((uintptr_t)st->p % 16 == 0) &&
+                    ((uintptr_t)st->o % 16 == 0);
+    *out = st;
+    return TID_OK;
+}
+
+extern "C" int tid_store_info(const tid_store *st, int64_t *n, const int32_t **s, const int32_t **p,
+                              const int32_t **o) {
+    clear_error();
+    if (!st) return fail(TID_ERR_ARG, "tid_store_info: null store");
+    if (n) *n = st->n;
+    if (s) *s = st->s;
+    if (p) *p = st->p;
+    if (o) *o = st->o;
+    return TID_OK;
+}
+
+extern "C" int tid_store_free(tid_store *st) {
+    clear_error();
+    if (!st) return TID_OK;
+    DeviceGuard g(st->ctx->device);
+    if (st->owned) dev_free(st->ctx, st->owned);
+    delete st;
+    return TID_OK;
+}
+
+extern "C" int tid_set_rows(tid_set *set, int64_t *rows) {
+    clear_error();
+    if (!set || !rows) return fail(TID_ERR_ARG, "tid_set_rows: null argument");
+    if (set->rows_known < 0) {
+        DeviceGuard g(set->ctx->device);
+        TID_TRY_CUDA(cudaEventSynchronize(set->ready), "wait for set");
+        TID_TRY(check_ctx_error(set->ctx));
+        const int64_t r = *(volatile int64_t *)set->slot.host;
+        if (r < 0) return fail(TID_ERR_CUDA, "row count was not produced");
+        set->rows_known = r;
+    }
+    *rows = set->rows_known;
+    return TID_OK;
+}
+
+extern "C" int tid_set_info(const tid_set *set, int *cols, int64_t *capacity, const int8_t **var_ids,
+                            int32_t *const **dev_cols, const int64_t **dev_rows) {
+    clear_error();
+    if (!set) return fail(TID_ERR_ARG, "tid_set_info: null set");
+    if (cols) *cols = set->k;
+    if (capacity) *capacity = set->cap;
+    if (var_ids) *var_ids = set->vars;
+    if (dev_cols) *dev_cols = set->col;
+    if (dev_rows) *dev_rows = set->d_rows;
+    return TID_OK;
+}
+
+extern "C" int tid_set_to_host(tid_set *set, int32_t *buf, int64_t cap_rows, int64_t *rows_out) {
+    clear_error();
+    if (!set) return fail(TID_ERR_ARG, "tid_set_to_host: null set");
+    int64_t rows = 0;
+    TID_TRY(tid_set_rows(set, &rows));
+    if (rows_out) *rows_out = rows;
+    if (rows > cap_rows) return fail(TID_ERR_CAPACITY, "tid_set_to_host: %lld rows > %lld", (long long)rows, (long long)cap_rows);
+    if (rows == 0) return TID_OK;
+    if (!buf) return fail(TID_ERR_ARG, "tid_set_to_host: null buffer");
+    tid_ctx *ctx = set->ctx;
+    DeviceGuard g(ctx->device);
+    const size_t bytes = (size_t)rows * set->k * sizeof(int32_t);
+    if (set->k == 1) {
+        TID_TRY_CUDA(cudaMemcpyAsync(buf, set->col[0], bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy set");
+    } else {
+        void *tmp = nullptr;
+        TID_TRY(dev_alloc(ctx, &tmp, bytes + 256));
+        int32_t **dcols = (int32_t **)((char *)tmp + align_up(bytes, 256));
+        cudaError_t e = cudaMemcpyAsync(dcols, set->col, sizeof(int32_t *) * set->k, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) {
+            const int64_t blocks = ceil_div(rows * set->k, 256);
+            k_interleave<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, ctx->stream>>>(
+                dcols, set->k, set->d_rows, (int32_t *)tmp);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(buf, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+        dev_free(ctx, tmp);
+        if (e != cudaSuccess) return fail_cuda(e, "copy set");
+    }
+    TID_TRY_CUDA(cudaStreamSynchronize(ctx->stream), "copy set");
+    return check_ctx_error(ctx);
+}
+
+extern "C" int tid_set_free(tid_set *set) {
+    clear_error();
+    if (!set) return TID_OK;
+    tid_ctx *ctx = set->ctx;
+    DeviceGuard g(ctx->device);
+    if (set->block) dev_free(ctx, set->block);
+    if (set->slot.slab >= 0) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (set->ready) {
+            // the producer may still be writing the slot: recycle it once done
+            ctx->pending.push_back({set->slot, set->ready});
+            set->ready = nullptr;
+        } else {
+            ctx->free_slots.push_back({set->slot.slab, set->slot.index});
+        }
+    }
+    if (set->ready) cudaEventDestroy(set->ready);
+    delete set;
+    return TID_OK;
+}

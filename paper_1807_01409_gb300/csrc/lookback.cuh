@@ -1,0 +1,94 @@
+// Device side of the single-pass tile prefix (decoupled look-back).
+//
+// A kernel that compacts in one pass gives every CTA a tile number from a
+// ticket counter (so tiles start in order and every predecessor of a tile is
+// already running), lets warp 0 publish the tile's count, and then walks
+// back over predecessors' status words until it meets an inclusive prefix.
+// Every wait is bounded: after LB_SPIN_LIMIT polls the tile marks itself
+// "gave up", sets TID_ERR_TIMEOUT in the error word and returns -1; a tile
+// that sees a predecessor that gave up gives up at once.
+#pragma once
+
+#include "tid_internal.cuh"
+
+namespace tid {
+
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void lb_store(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long lb_word(unsigned epoch, unsigned flag, unsigned value) {
+    return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | value;
+}
+
+// Called by thread 0: draws this CTA's tile number.  Returns num_tiles (an
+// invalid tile) if the counter was not at 0 when the launch began.
+__device__ __forceinline__ unsigned lb_ticket(const Lookback &lb) {
+    unsigned t = atomicAdd(lb.ticket, 1u);
+    if (t == lb.num_tiles - 1) atomicExch(lb.ticket, 0u);
+    if (t >= lb.num_tiles) {
+        atomicExch(lb.err, TID_ERR_CUDA);
+        return lb.num_tiles;
+    }
+    return t;
+}
+
+// Called by all 32 lanes of ONE warp.  Publishes `total` for `tile` and
+// returns the tile's exclusive prefix (sum of the totals of tiles < tile), or
+// -1 if a wait gave up.
+__device__ __forceinline__ long long lb_exclusive_prefix(const Lookback &lb, unsigned tile,
+                                                         unsigned total) {
+    const unsigned lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) lb_store(lb.status, lb_word(lb.epoch, LB_FLAG_PREFIX, total));
+        return 0;
+    }
+    if (lane == 0) lb_store(lb.status + tile, lb_word(lb.epoch, LB_FLAG_AGG, total));
+    long long excl = 0;
+    long long pos = (long long)tile - 1;
+    unsigned polls = 0;
+    bool gave_up = false;
+    while (true) {
+        const long long idx = pos - (long long)lane;
+        unsigned long long w = idx >= 0 ? lb_load(lb.status + idx)
+                                        : lb_word(lb.epoch, LB_FLAG_PREFIX, 0);
+        unsigned flag = ((unsigned)(w >> 34) == lb.epoch) ? (unsigned)(w >> 32) & 3u : 0u;
+        const unsigned val = (unsigned)w;
+        const unsigned pref = __ballot_sync(0xffffffffu, flag == LB_FLAG_PREFIX);
+        const unsigned notready = __ballot_sync(0xffffffffu, flag == 0);
+        const unsigned aborted = __ballot_sync(0xffffffffu, flag == LB_FLAG_ABORT);
+        const int stop = pref ? __ffs(pref) - 1 : 31;
+        const unsigned upto = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
+        if (aborted & upto) { gave_up = true; break; }
+        if (notready & upto) {
+            if (++polls > LB_SPIN_LIMIT) {
+                if (lane == 0) atomicExch(lb.err, TID_ERR_TIMEOUT);
+                gave_up = true;
+                break;
+            }
+            __nanosleep(polls < 64 ? 32 : 256);
+            continue;
+        }
+        unsigned long long v = (int)lane <= stop ? val : 0ull;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+        excl += (long long)v;
+        if (pref) break;
+        pos -= 32;
+    }
+    if (gave_up) {
+        if (lane == 0) lb_store(lb.status + tile, lb_word(lb.epoch, LB_FLAG_ABORT, 0));
+        return -1;
+    }
+    if (lane == 0)
+        lb_store(lb.status + tile, lb_word(lb.epoch, LB_FLAG_PREFIX, (unsigned)(excl + total)));
+    return excl;
+}
+
+}  // namespace tid
