@@ -124,6 +124,120 @@ int tid_store_free(tid_store *st);
  * Errors: TID_ERR_ID if a pattern value is negative.  Does not synchronise. */
 int tid_match(tid_ctx *ctx, const tid_store *st, tid_pattern pat, tid_set **out);
 
+/* Several patterns in ONE pass over the store (Section 4.1: the key array
+ * holds the keys of all subqueries and every triple is marked with each
+ * subquery it answers; one triple may answer several).  outs[j] receives the
+ * ascending index list of pats[j], exactly as tid_match(pats[j]) would.
+ * 1 <= m <= TID_MAX_MULTI.  The union of the patterns' bound columns is read
+ * once.  Does not synchronise. */
+int tid_match_multi(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, int m,
+                    tid_set **outs);
+
+/* ------------------------------------------------------------------------ */
+/* operators on tuple sets -- Section 4                                      */
+/* ------------------------------------------------------------------------ */
+
+/* comparison of a FILTER predicate */
+#define TID_CMP_EQ    0  /* x == a */
+#define TID_CMP_NE    1  /* x != a */
+#define TID_CMP_LT    2  /* x <  a */
+#define TID_CMP_LE    3  /* x <= a */
+#define TID_CMP_GT    4  /* x >  a */
+#define TID_CMP_GE    5  /* x >= a */
+#define TID_CMP_RANGE 6  /* a <= x <= b */
+
+/* A FILTER predicate on variable `var`.  It compares the int32 ID itself:
+ * literals encoded in ID order (an integer literal of value v has ID
+ * 2^30 + v) make value ranges ID ranges (Section 4.3 proposes such an
+ * order-preserving ID assignment).  An unbound value (0) never passes. */
+typedef struct {
+    int32_t var;
+    int32_t op;
+    int32_t a, b;
+} tid_pred;
+
+#define TID_MAX_PREDS 4
+
+/* Result vector of one subquery (Section 4.2, vectors R_qi): for every index
+ * in `idx` (a set from tid_match on the same store and pattern), the terms
+ * at the pattern's variable slots.  Columns are the distinct variables of
+ * pat.var[] in slot order (s, p, o).  A variable that occurs in two slots
+ * keeps only triples whose two terms are equal.  The n_preds (<= 4)
+ * predicates, all on variables of the pattern, are applied in the same pass
+ * (Section 4.3: the filter is applied while the subquery's triples are
+ * extracted).  The result is canonical: rows sorted lexicographically in
+ * column order, without duplicates.  Synchronises once to size the output.
+ * Errors: TID_ERR_ARG if the pattern has no variable, a bound slot carries a
+ * variable, or a predicate names a variable not in the pattern. */
+int tid_bind(tid_ctx *ctx, const tid_store *st, tid_pattern pat, const tid_set *idx,
+             const tid_pred *preds, int n_preds, tid_set **out);
+
+/* FILTER: rows of `in` for which every predicate holds, in the same order
+ * (a canonical input gives a canonical output). */
+int tid_filter(tid_ctx *ctx, const tid_set *in, const tid_pred *preds, int n_preds, tid_set **out);
+
+#define TID_JOIN_AUTO       0
+#define TID_JOIN_SORT_MERGE 1
+#define TID_JOIN_HASH       2
+
+/* Inner join of L and R on ALL their shared variables (Section 4.2 and its
+ * relationship table: the shared term may come from any of S/P/O on either
+ * side).  A pair joins when every shared column is equal and non-zero.
+ * Output columns: L's, then R's non-shared ones in R's order (at most
+ * TID_MAX_COLS).  No shared variable gives the cross product.  Algorithms:
+ * sort-merge (sort both sides on the key, count matches per left row by
+ * binary search, scan, write) or hash (group the smaller side by key in an
+ * open-addressing table, probe with the other).  Output canonical.  The
+ * count phase is followed by one synchronisation to size the output; more
+ * than 2^31-1 output rows is TID_ERR_CAPACITY. */
+int tid_join(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out);
+
+/* Set union of k >= 1 sets (Section 4.1).  The output schema lists the
+ * variables of in[0], then the new ones of in[1], ...; a row from a branch
+ * that lacks a variable carries 0 (unbound) there.  Duplicates are removed
+ * (Section 4.3 keeps only distinct final values).  Output canonical. */
+int tid_union(tid_ctx *ctx, const tid_set *const *in, int k, tid_set **out);
+
+/* SELECT the n_vars listed variables (in that order) with DISTINCT
+ * (Section 4.3).  Output canonical. */
+int tid_project(tid_ctx *ctx, const tid_set *in, const int8_t *vars, int n_vars, tid_set **out);
+
+/* A set from `rows` x `cols` int32 in host memory (row-major), labelled with
+ * vars[0..cols-1] (distinct, 0..127); made canonical.  For inputs built
+ * outside the library. */
+int tid_set_from_host(tid_ctx *ctx, const int32_t *buf, int64_t rows, int cols,
+                      const int8_t *vars, tid_set **out);
+
+/* ------------------------------------------------------------------------ */
+/* subquery plans -- Section 4.3, Fig. "Integration of several operations"   */
+/* ------------------------------------------------------------------------ */
+
+#define TID_OP_MATCH   1  /* search + extract one pattern (tid_match + tid_bind) */
+#define TID_OP_FILTER  2  /* tid_filter(in[0], pred)                             */
+#define TID_OP_JOIN    3  /* tid_join(in[0], in[1], algo)                        */
+#define TID_OP_UNION   4  /* tid_union(in[0..n_in-1])                            */
+#define TID_OP_PROJECT 5  /* tid_project(in[0], vars[0..n_vars-1])               */
+
+typedef struct {
+    int32_t op;
+    int32_t n_in;       /* inputs used (JOIN 2, UNION 1..4, FILTER/PROJECT 1) */
+    int32_t in[4];      /* indices of earlier nodes */
+    tid_pattern pattern;/* MATCH */
+    tid_pred pred;      /* FILTER */
+    int32_t algo;       /* JOIN: TID_JOIN_* */
+    int32_t n_vars;     /* PROJECT */
+    int8_t vars[TID_MAX_COLS];
+} tid_plan_node;
+
+/* Evaluate a plan: nodes[i] may only read nodes[j], j < i; the last node is
+ * the result.  All MATCH nodes are searched in one multi-pattern pass over
+ * the store (up to TID_MAX_MULTI per pass); a FILTER whose input is a MATCH
+ * read by nothing else is fused into that MATCH's extraction; joins run in
+ * plan order (left-deep, as the paper's REL list).  The result is canonical
+ * and equal to evaluating the nodes one by one with the calls above. */
+int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *nodes, int n_nodes,
+             tid_set **out);
+
 /* ------------------------------------------------------------------------ */
 /* tuple sets                                                                */
 /* ------------------------------------------------------------------------ */

@@ -43,7 +43,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 
 OPS = {"eq": 0, "ne": 1, "lt": 2, "le": 3, "gt": 4, "ge": 5, "range": 6}
-NESTED_LOOP_CAP = 2_000_000_000  # |L|*|R| above this switches to the sort-merge join
+NESTED_LOOP_CAP = 100_000_000  # |L|*|R| above this switches to the sort-merge join
 
 _lib = None
 

@@ -34,6 +34,21 @@ class tid_pattern(C.Structure):
                 ("var", C.c_int8 * 3), ("reserved", C.c_int8)]
 
 
+class tid_pred(C.Structure):
+    _fields_ = [("var", C.c_int32), ("op", C.c_int32), ("a", C.c_int32), ("b", C.c_int32)]
+
+
+class tid_plan_node(C.Structure):
+    _fields_ = [("op", C.c_int32), ("n_in", C.c_int32), ("in_", C.c_int32 * 4),
+                ("pattern", tid_pattern), ("pred", tid_pred), ("algo", C.c_int32),
+                ("n_vars", C.c_int32), ("vars", C.c_int8 * 8)]
+
+
+CMP = {"eq": 0, "ne": 1, "lt": 2, "le": 3, "gt": 4, "ge": 5, "range": 6}
+JOIN = {"auto": 0, "sort_merge": 1, "sortmerge": 1, "hash": 2}
+OP = {"match": 1, "filter": 2, "join": 3, "union": 4, "project": 5}
+
+
 def make_pattern(s=0, p=0, o=0, var=(-1, -1, -1)) -> tid_pattern:
     """A pattern from (s, p, o) with 0 = "?", and variable ids per slot (-1 = none)."""
     pt = tid_pattern()
@@ -80,6 +95,14 @@ def lib():
                                    C.POINTER(C.POINTER(_vp)), C.POINTER(_vp)]),
         "tid_set_to_host": (C.c_int, [_vp, _vp, C.c_int64, i64p]),
         "tid_set_free": (C.c_int, [_vp]),
+        "tid_match_multi": (C.c_int, [_vp, _vp, C.POINTER(tid_pattern), C.c_int, C.POINTER(_vp)]),
+        "tid_bind": (C.c_int, [_vp, _vp, tid_pattern, _vp, C.POINTER(tid_pred), C.c_int, C.POINTER(_vp)]),
+        "tid_filter": (C.c_int, [_vp, _vp, C.POINTER(tid_pred), C.c_int, C.POINTER(_vp)]),
+        "tid_join": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(_vp)]),
+        "tid_union": (C.c_int, [_vp, C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
+        "tid_project": (C.c_int, [_vp, _vp, C.POINTER(C.c_int8), C.c_int, C.POINTER(_vp)]),
+        "tid_set_from_host": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, C.POINTER(C.c_int8), C.POINTER(_vp)]),
+        "tid_exec": (C.c_int, [_vp, _vp, C.POINTER(tid_plan_node), C.c_int, C.POINTER(_vp)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -199,6 +222,106 @@ def tid_set_to_host(set_, buf=None):
 
 def tid_set_free(set_):
     _check(lib().tid_set_free(set_), "tid_set_free")
+
+
+def _preds(preds):
+    preds = list(preds or [])
+    arr = (tid_pred * max(1, len(preds)))()
+    for i, q in enumerate(preds):
+        if isinstance(q, dict):
+            var, op, a, b = q["var"], q["cmp"], q["a"], q.get("b", 0)
+        else:
+            var, op, a, b = (tuple(q) + (0,))[:4]
+        arr[i].var, arr[i].op = int(var), CMP[op] if isinstance(op, str) else int(op)
+        arr[i].a, arr[i].b = int(a), int(b)
+    return arr, len(preds)
+
+
+def tid_match_multi(ctx, st, patterns):
+    pats = [as_pattern(p) for p in patterns]
+    arr = (tid_pattern * len(pats))(*pats)
+    outs = (_vp * len(pats))()
+    _check(lib().tid_match_multi(ctx, st, arr, len(pats), outs), "tid_match_multi")
+    return [_vp(outs[i]) for i in range(len(pats))]
+
+
+def tid_bind(ctx, st, pattern, idx, preds=()):
+    arr, n = _preds(preds)
+    out = _vp()
+    _check(lib().tid_bind(ctx, st, as_pattern(pattern), idx, arr, n, C.byref(out)), "tid_bind")
+    return out
+
+
+def tid_filter(ctx, set_, preds):
+    arr, n = _preds(preds)
+    out = _vp()
+    _check(lib().tid_filter(ctx, set_, arr, n, C.byref(out)), "tid_filter")
+    return out
+
+
+def tid_join(ctx, L, R, algo="auto"):
+    out = _vp()
+    _check(lib().tid_join(ctx, L, R, JOIN[algo] if isinstance(algo, str) else int(algo), C.byref(out)),
+           "tid_join")
+    return out
+
+
+def tid_union(ctx, sets):
+    arr = (_vp * len(sets))(*[s.value if isinstance(s, _vp) else s for s in sets])
+    out = _vp()
+    _check(lib().tid_union(ctx, arr, len(sets), C.byref(out)), "tid_union")
+    return out
+
+
+def tid_project(ctx, set_, vars_):
+    arr = (C.c_int8 * max(1, len(vars_)))(*[int(v) for v in vars_])
+    out = _vp()
+    _check(lib().tid_project(ctx, set_, arr, len(vars_), C.byref(out)), "tid_project")
+    return out
+
+
+def tid_set_from_host(ctx, rows, vars_):
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    if rows.ndim != 2 or rows.shape[1] != len(vars_):
+        raise ValueError("rows must be (n, len(vars))")
+    arr = (C.c_int8 * len(vars_))(*[int(v) for v in vars_])
+    out = _vp()
+    _check(lib().tid_set_from_host(ctx, rows.ctypes.data if rows.size else None, rows.shape[0],
+                                   rows.shape[1], arr, C.byref(out)), "tid_set_from_host")
+    return out
+
+
+def plan_nodes(plan):
+    """A plan given as a list of dicts (op, pattern / input(s) / var, cmp, a, b /
+    algo / vars) as a tid_plan_node array."""
+    nodes = (tid_plan_node * len(plan))()
+    for i, nd in enumerate(plan):
+        x = nodes[i]
+        x.op = OP[nd["op"]]
+        ins = nd.get("inputs", [nd["input"]] if "input" in nd else [])
+        x.n_in = len(ins)
+        for j, v in enumerate(ins):
+            x.in_[j] = int(v)
+        if nd["op"] == "match":
+            x.pattern = as_pattern(nd["pattern"])
+        if nd["op"] == "filter":
+            p, _ = _preds([nd])
+            x.pred = p[0]
+        if nd["op"] == "join":
+            a = nd.get("algo", "auto")
+            x.algo = JOIN[a] if isinstance(a, str) else int(a)
+        if nd["op"] == "project":
+            x.n_vars = len(nd["vars"])
+            for j, v in enumerate(nd["vars"]):
+                x.vars[j] = int(v)
+    return nodes
+
+
+def tid_exec(ctx, st, plan):
+    nodes = plan if isinstance(plan, C.Array) else plan_nodes(plan)
+    out = _vp()
+    _check(lib().tid_exec(ctx, st, nodes, len(nodes), C.byref(out)), "tid_exec")
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -5,7 +5,7 @@
 
 #include <new>
 
-#include "tid_internal.cuh"
+#include "ops.cuh"
 
 namespace tid {
 
@@ -368,9 +368,8 @@ extern "C" int tid_store_free(tid_store *st) {
     return TID_OK;
 }
 
-extern "C" int tid_set_rows(tid_set *set, int64_t *rows) {
-    clear_error();
-    if (!set || !rows) return fail(TID_ERR_ARG, "tid_set_rows: null argument");
+namespace tid {
+int set_rows_host(tid_set *set, int64_t *rows) {
     if (set->rows_known < 0) {
         DeviceGuard g(set->ctx->device);
         TID_TRY_CUDA(cudaEventSynchronize(set->ready), "wait for set");
@@ -381,6 +380,14 @@ extern "C" int tid_set_rows(tid_set *set, int64_t *rows) {
     }
     *rows = set->rows_known;
     return TID_OK;
+}
+int set_rows_host(const tid_set *set, int64_t *rows) { return set_rows_host(const_cast<tid_set *>(set), rows); }
+}  // namespace tid
+
+extern "C" int tid_set_rows(tid_set *set, int64_t *rows) {
+    clear_error();
+    if (!set || !rows) return fail(TID_ERR_ARG, "tid_set_rows: null argument");
+    return set_rows_host(set, rows);
 }
 
 extern "C" int tid_set_info(const tid_set *set, int *cols, int64_t *capacity, const int8_t **var_ids,

@@ -1,0 +1,302 @@
+// Single-pass row compaction over tuple sets, and a device-wide exclusive scan.
+//
+// One kernel template serves three operators that keep a subset of rows in
+// their original order and write k output columns:
+//   * bind    -- from triple indices, the terms at a pattern's variable slots,
+//                dropping rows whose repeated variable disagrees; the FILTER
+//                predicates of the subquery are applied in the same pass
+//                (Section 4.3: the filter is applied while the matched triples
+//                are extracted into the subquery's vector);
+//   * filter  -- a predicate on one column of a set;
+//   * unique  -- after a sort, a row is kept when it differs from its
+//                predecessor in sorted order (DISTINCT, Section 4.3).
+// A CTA owns 2048 consecutive rows (256 threads x 8, striped so each warp
+// instruction touches 32 consecutive rows); ranks come from ballots, the
+// tile offset from the decoupled look-back (lookback.cuh).
+
+#include "lookback.cuh"
+#include "ops.cuh"
+
+namespace tid {
+
+namespace {
+
+constexpr int CP_THREADS = 256;
+constexpr int CP_WARPS = CP_THREADS / 32;
+constexpr int CP_ITEMS = 8;
+constexpr int CP_TILE = CP_THREADS * CP_ITEMS;
+
+__device__ __forceinline__ bool pred_ok(const Pred &p, int32_t x) {
+    if (x == 0) return false;  // unbound never passes
+    switch (p.op) {
+        case TID_CMP_EQ: return x == p.a;
+        case TID_CMP_NE: return x != p.a;
+        case TID_CMP_LT: return x < p.a;
+        case TID_CMP_LE: return x <= p.a;
+        case TID_CMP_GT: return x > p.a;
+        case TID_CMP_GE: return x >= p.a;
+        case TID_CMP_RANGE: return p.a <= x && x <= p.b;
+        default: return false;
+    }
+}
+
+// ---- row sources -----------------------------------------------------------
+
+struct BindRow {  // triple index -> variable values
+    const int32_t *S, *P, *O;
+    const int32_t *idx;
+    int k;
+    int8_t src[TID_MAX_COLS];   // slot (0,1,2) giving output column c
+    int8_t eq_a[3], eq_b[3];    // pairs of slots that must be equal
+    int n_eq;
+    Pred preds[MAX_PREDS];
+    int n_preds;
+    __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
+        const int64_t t = idx[r];
+        int32_t term[3];
+        term[0] = S[t];
+        term[1] = P[t];
+        term[2] = O[t];
+        bool ok = true;
+        for (int e = 0; e < n_eq; ++e) ok = ok && term[eq_a[e]] == term[eq_b[e]];
+        for (int c = 0; c < k; ++c) v[c] = term[src[c]];
+        for (int q = 0; q < n_preds; ++q) ok = ok && pred_ok(preds[q], v[preds[q].col]);
+        return ok;
+    }
+};
+
+struct FilterRow {
+    const int32_t *col[TID_MAX_COLS];
+    int k;
+    Pred preds[MAX_PREDS];
+    int n_preds;
+    __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
+        for (int c = 0; c < k; ++c) v[c] = col[c][r];
+        bool ok = true;
+        for (int q = 0; q < n_preds; ++q) ok = ok && pred_ok(preds[q], v[preds[q].col]);
+        return ok;
+    }
+};
+
+struct UniqueRow {  // rows in perm order; keep the first of each run of equal rows
+    const int32_t *col[TID_MAX_COLS];
+    const int32_t *perm;  // may be null (rows already in order)
+    int k;
+    __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
+        const int64_t a = perm ? perm[r] : r;
+        for (int c = 0; c < k; ++c) v[c] = col[c][a];
+        if (r == 0) return true;
+        const int64_t b = perm ? perm[r - 1] : r - 1;
+        bool same = true;
+        for (int c = 0; c < k; ++c) same = same && col[c][b] == v[c];
+        return !same;
+    }
+};
+
+template <class Row>
+__global__ void __launch_bounds__(CP_THREADS)
+k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__restrict__ d_rows,
+          int64_t *__restrict__ h_rows, Lookback lb) {
+    __shared__ unsigned s_tile;
+    __shared__ unsigned s_off[CP_ITEMS * CP_WARPS];
+    __shared__ long long s_prefix;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = lb_ticket(lb);
+    __syncthreads();
+    const unsigned tile = s_tile;
+    if (tile >= lb.num_tiles) return;
+    const int64_t base = (int64_t)tile * CP_TILE;
+    const unsigned lt = (1u << lane) - 1u;
+
+    unsigned keep = 0, wpre[CP_ITEMS];
+#pragma unroll
+    for (int j = 0; j < CP_ITEMS; ++j) {
+        const int64_t r = base + j * CP_THREADS + threadIdx.x;
+        int32_t v[TID_MAX_COLS];
+        const bool kp = r < n && row.load(r, v);
+        keep |= (unsigned)kp << j;
+        const unsigned b = __ballot_sync(0xffffffffu, kp);
+        wpre[j] = __popc(b & lt);
+        if (lane == 0) s_off[j * CP_WARPS + warp] = __popc(b);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // 64 (item, warp) counts in order; each lane scans two consecutive entries
+        const unsigned a0 = s_off[2 * lane], a1 = s_off[2 * lane + 1];
+        unsigned x = a0 + a1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+            if ((int)lane >= d) x += y;
+        }
+        const unsigned ex = x - a0 - a1;
+        s_off[2 * lane] = ex;
+        s_off[2 * lane + 1] = ex + a0;
+        const unsigned total = __shfl_sync(0xffffffffu, x, 31);
+        const long long excl = lb_exclusive_prefix(lb, tile, total);
+        if (lane == 0) {
+            s_prefix = excl;
+            if (tile == lb.num_tiles - 1 && excl >= 0) {
+                *d_rows = excl + total;
+                *h_rows = excl + total;
+            }
+        }
+    }
+    __syncthreads();
+    const long long prefix = s_prefix;
+    if (prefix < 0) return;
+#pragma unroll
+    for (int j = 0; j < CP_ITEMS; ++j) {
+        if (!((keep >> j) & 1u)) continue;
+        const int64_t r = base + j * CP_THREADS + threadIdx.x;
+        int32_t v[TID_MAX_COLS];
+        row.load(r, v);  // second read of a kept row (cached in L1/L2)
+        const long long pos = prefix + s_off[j * CP_WARPS + warp] + wpre[j];
+        if (pos < cap)
+            for (int c = 0; c < k_out; ++c) out.col[c][pos] = v[c];
+    }
+}
+
+template <class Row>
+int launch_compact(tid_ctx *ctx, const Row &row, int64_t n, int k_out, const OutCols &out, int64_t cap,
+                   int64_t *d_rows, int64_t *h_rows_dev) {
+    if (n == 0) {
+        TID_TRY_CUDA(cudaMemsetAsync(d_rows, 0, sizeof(int64_t), ctx->stream), "memset rows");
+        TID_TRY_CUDA(cudaMemsetAsync(h_rows_dev, 0, sizeof(int64_t), ctx->stream), "memset rows");
+        return TID_OK;
+    }
+    const unsigned tiles = (unsigned)ceil_div(n, CP_TILE);
+    Lookback lb{};
+    TID_TRY(lookback_scratch(ctx, tiles, &lb));
+    k_compact<Row><<<tiles, CP_THREADS, 0, ctx->stream>>>(row, n, k_out, out, cap, d_rows, h_rows_dev, lb);
+    return launch_check("k_compact");
+}
+
+// ---- exclusive scan of uint32 (look-back) --------------------------------------
+
+constexpr int SC_THREADS = 256, SC_ITEMS = 16, SC_TILE = SC_THREADS * SC_ITEMS;
+
+__global__ void __launch_bounds__(SC_THREADS)
+k_scan_u32(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
+           unsigned long long *__restrict__ total_out, Lookback lb) {
+    __shared__ unsigned s_tile;
+    __shared__ uint32_t s_w[SC_THREADS / 32];
+    __shared__ long long s_prefix;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = lb_ticket(lb);
+    __syncthreads();
+    const unsigned tile = s_tile;
+    if (tile >= lb.num_tiles) return;
+    // blocked: thread t owns items base + t*16 .. +15
+    const int64_t base = (int64_t)tile * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+    uint32_t v[SC_ITEMS];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0u;
+        sum += v[i];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if ((int)lane >= d) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < SC_THREADS / 32 ? s_w[lane] : 0u;
+        uint32_t y = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t z = __shfl_up_sync(0xffffffffu, y, d);
+            if ((int)lane >= d) y += z;
+        }
+        if (lane < SC_THREADS / 32) s_w[lane] = y - w;
+        const uint32_t total = __shfl_sync(0xffffffffu, y, 31);
+        const long long excl = lb_exclusive_prefix(lb, tile, total);
+        if (lane == 0) {
+            s_prefix = excl;
+            if (tile == lb.num_tiles - 1 && excl >= 0 && total_out) *total_out = excl + total;
+        }
+    }
+    __syncthreads();
+    if (s_prefix < 0) return;
+    uint32_t run = (uint32_t)s_prefix + s_w[warp] + (x - sum);
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+}  // namespace
+
+int scan_exclusive_u32(tid_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
+                       unsigned long long *total_dev) {
+    if (n == 0) {
+        if (total_dev) TID_TRY_CUDA(cudaMemsetAsync(total_dev, 0, 8, ctx->stream), "memset");
+        return TID_OK;
+    }
+    const unsigned tiles = (unsigned)ceil_div(n, SC_TILE);
+    Lookback lb{};
+    TID_TRY(lookback_scratch(ctx, tiles, &lb));
+    k_scan_u32<<<tiles, SC_THREADS, 0, ctx->stream>>>(in, out, n, total_dev, lb);
+    return launch_check("k_scan_u32");
+}
+
+int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, const int32_t *idx, int64_t n,
+                 const Pred *preds, int n_preds, tid_set *out) {
+    BindRow r{};
+    r.S = st->s;
+    r.P = st->p;
+    r.O = st->o;
+    r.idx = idx;
+    r.k = out->k;
+    const int8_t var[3] = {pat.var[0], pat.var[1], pat.var[2]};
+    for (int c = 0; c < out->k; ++c) {
+        r.src[c] = -1;
+        for (int j = 0; j < 3; ++j)
+            if (var[j] == out->vars[c]) {
+                r.src[c] = (int8_t)j;
+                break;
+            }
+    }
+    r.n_eq = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b)
+            if (var[a] >= 0 && var[a] == var[b]) {
+                r.eq_a[r.n_eq] = (int8_t)a;
+                r.eq_b[r.n_eq] = (int8_t)b;
+                r.n_eq++;
+            }
+    r.n_preds = n_preds;
+    for (int q = 0; q < n_preds; ++q) r.preds[q] = preds[q];
+    OutCols oc{};
+    for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
+    return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev);
+}
+
+int compact_filter(tid_ctx *ctx, const tid_set *in, int64_t n, const Pred *preds, int n_preds, tid_set *out) {
+    FilterRow r{};
+    r.k = in->k;
+    for (int c = 0; c < in->k; ++c) r.col[c] = in->col[c];
+    r.n_preds = n_preds;
+    for (int q = 0; q < n_preds; ++q) r.preds[q] = preds[q];
+    OutCols oc{};
+    for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
+    return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev);
+}
+
+int compact_unique(tid_ctx *ctx, const int32_t *const *cols, int k, const int32_t *perm, int64_t n,
+                   tid_set *out) {
+    UniqueRow r{};
+    r.k = k;
+    for (int c = 0; c < k; ++c) r.col[c] = cols[c];
+    r.perm = perm;
+    OutCols oc{};
+    for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
+    return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev);
+}
+
+}  // namespace tid

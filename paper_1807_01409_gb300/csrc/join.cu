@@ -1,0 +1,441 @@
+// K5 / K6: inner join of two tuple sets on all shared variables.
+//
+// Section 4.2 joins subquery result vectors by copying the related terms into
+// key vectors, sorting them, and running a merge-join that returns pairs of
+// matching positions, from which the remaining values are gathered; the
+// relationship table lists the nine S/P/O position pairings a shared term can
+// take, which here are simply the columns of the shared variables.
+//
+// Both algorithms follow the same three phases (the two-phase output sizing
+// of He et al. that the paper cites): count matches per row, exclusive-scan
+// the counts (one synchronisation reads the total to size the output), then
+// write every output row with one thread -- an output row finds its left row
+// by binary search over the scanned counts, so a key with millions of matches
+// is spread over as many threads (no per-row serial loops).
+//
+//  * sort-merge: both sides ordered by the key (free when the key columns are
+//    a prefix of a canonical set's column order; else a radix-sorted
+//    permutation); per left row, lower/upper bound in the right keys.
+//  * hash: the smaller side is grouped by key in an open-addressing table
+//    (key -> [start, count) into a grouped row array, built with CAS inserts,
+//    a scan and a scatter); the other side probes it.  A table of at most
+//    2048 slots is copied into shared memory by every probing CTA.
+// A key value 0 (unbound) never matches.  The output is sorted to canonical
+// order; a join of two sets is a set, so no duplicate removal is needed.
+
+#include <algorithm>
+
+#include "lookback.cuh"
+#include "ops.cuh"
+
+namespace tid {
+
+int set_rows_const(tid_set *set, int64_t n);
+
+namespace {
+
+struct Cols {
+    const int32_t *c[TID_MAX_COLS];
+};
+struct MCols {
+    int32_t *c[TID_MAX_COLS];
+};
+
+__device__ __forceinline__ int cmp_rows(const Cols &A, int64_t a, const Cols &B, int64_t b, int nk) {
+    for (int c = 0; c < nk; ++c) {
+        const int32_t x = A.c[c][a], y = B.c[c][b];
+        if (x < y) return -1;
+        if (x > y) return 1;
+    }
+    return 0;
+}
+
+__device__ __forceinline__ bool has_zero(const Cols &A, int64_t a, int nk) {
+    for (int c = 0; c < nk; ++c)
+        if (A.c[c][a] == 0) return true;
+    return false;
+}
+
+__device__ __forceinline__ void block_add_u64(unsigned long long v, unsigned long long *total) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+}
+
+unsigned grid_for(int64_t n, int threads) {
+    const int64_t b = ceil_div(n, threads);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+// ---- sort-merge --------------------------------------------------------------
+
+// per left row: [lo, hi) of equal keys in the sorted right keys
+__global__ void k_sm_count(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, uint32_t *__restrict__ cnt,
+                           uint32_t *__restrict__ lo_out, unsigned long long *__restrict__ total) {
+    unsigned long long acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_iter = ceil_div(nl, stride) * stride;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n_iter; l += stride) {
+        if (l < nl) {
+            uint32_t c = 0, lo = 0;
+            if (!has_zero(LK, l, nk)) {
+                int64_t a = 0, b = nr;  // lower bound
+                while (a < b) {
+                    const int64_t m = (a + b) >> 1;
+                    if (cmp_rows(RK, m, LK, l, nk) < 0) a = m + 1;
+                    else b = m;
+                }
+                int64_t a2 = a, b2 = nr;  // upper bound
+                while (a2 < b2) {
+                    const int64_t m = (a2 + b2) >> 1;
+                    if (cmp_rows(RK, m, LK, l, nk) <= 0) a2 = m + 1;
+                    else b2 = m;
+                }
+                lo = (uint32_t)a;
+                c = (uint32_t)(a2 - a);
+            }
+            cnt[l] = c;
+            lo_out[l] = lo;
+            acc += c;
+        }
+        block_add_u64(acc, total);
+        acc = 0;
+    }
+}
+
+// one thread per output row
+__global__ void k_join_write(const uint32_t *__restrict__ off, int64_t nl, const uint32_t *__restrict__ lo,
+                             const int32_t *__restrict__ lperm, const int32_t *__restrict__ rmap,
+                             const int32_t *__restrict__ rperm, int64_t total, Cols L, int kl, Cols Rrest,
+                             int nrest, MCols out, bool left_is_probe) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = 0, b = nl;  // first l with off[l] > o
+        while (a < b) {
+            const int64_t m = (a + b) >> 1;
+            if ((int64_t)off[m] <= o) a = m + 1;
+            else b = m;
+        }
+        const int64_t l = a - 1;
+        const int64_t j = (int64_t)lo[l] + (o - (int64_t)off[l]);
+        int64_t lr, rr;
+        if (left_is_probe) {
+            lr = lperm ? lperm[l] : l;
+            rr = rmap ? rmap[j] : j;
+            if (rperm) rr = rperm[rr];
+        } else {  // hash join built on the left: "l" walks right rows, j indexes grouped left rows
+            rr = l;
+            lr = rmap[j];
+        }
+        for (int c = 0; c < kl; ++c) out.c[c][o] = L.c[c][lr];
+        for (int c = 0; c < nrest; ++c) out.c[kl + c][o] = Rrest.c[c][rr];
+    }
+}
+
+// ---- hash ---------------------------------------------------------------------
+
+constexpr unsigned long long EMPTY = ~0ull;
+constexpr int SMEM_SLOTS = 2048;
+
+__device__ __forceinline__ unsigned long long hash_key(const Cols &K, int64_t r, int nk) {
+    unsigned long long h = 0x9E3779B97F4A7C15ull;
+    for (int c = 0; c < nk; ++c) {
+        h ^= (unsigned long long)(uint32_t)K.c[c][r];
+        h *= 0xFF51AFD7ED558CCDull;
+        h ^= h >> 33;
+        h *= 0xC4CEB9FE1A85EC53ull;
+        h ^= h >> 29;
+    }
+    return h;
+}
+
+__device__ __forceinline__ unsigned long long make_entry(unsigned long long h, int64_t row) {
+    return ((h >> 32) << 32) | (unsigned long long)(uint32_t)row;
+}
+
+__global__ void k_hash_build(Cols BK, int64_t nb, int nk, unsigned long long *__restrict__ slots,
+                             uint32_t *__restrict__ cnt, uint32_t mask, int *__restrict__ err) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        if (has_zero(BK, b, nk)) continue;
+        const unsigned long long h = hash_key(BK, b, nk);
+        const unsigned long long e = make_entry(h, b);
+        uint32_t idx = (uint32_t)h & mask;
+        bool done = false;
+        for (uint32_t probe = 0; probe <= mask && !done; ++probe) {
+            unsigned long long cur = slots[idx];
+            if (cur == EMPTY) {
+                const unsigned long long old = atomicCAS(slots + idx, EMPTY, e);
+                if (old == EMPTY) {
+                    atomicAdd(cnt + idx, 1u);
+                    done = true;
+                    break;
+                }
+                cur = old;
+            }
+            if ((cur >> 32) == (e >> 32) && cmp_rows(BK, (int64_t)(uint32_t)cur, BK, b, nk) == 0) {
+                atomicAdd(cnt + idx, 1u);
+                done = true;
+                break;
+            }
+            idx = (idx + 1) & mask;
+        }
+        if (!done) atomicExch(err, TID_ERR_CAPACITY);
+    }
+}
+
+// slot of B row b's key (its key was inserted); -1 if absent
+__device__ __forceinline__ int64_t find_slot(const unsigned long long *slots, uint32_t mask, const Cols &BK,
+                                             const Cols &QK, int64_t q, int nk, unsigned long long h) {
+    uint32_t idx = (uint32_t)h & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long cur = slots[idx];
+        if (cur == EMPTY) return -1;
+        if ((cur >> 32) == (h >> 32) && cmp_rows(BK, (int64_t)(uint32_t)cur, QK, q, nk) == 0) return idx;
+        idx = (idx + 1) & mask;
+    }
+    return -1;
+}
+
+__global__ void k_hash_scatter(Cols BK, int64_t nb, int nk, const unsigned long long *__restrict__ slots,
+                               uint32_t mask, const uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
+                               int32_t *__restrict__ grouped) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        if (has_zero(BK, b, nk)) continue;
+        const int64_t s = find_slot(slots, mask, BK, BK, b, nk, hash_key(BK, b, nk));
+        if (s < 0) continue;
+        const uint32_t pos = start[s] + atomicAdd(cursor + s, 1u);
+        grouped[pos] = (int32_t)b;
+    }
+}
+
+template <bool SMEM>
+__global__ void k_hash_count(Cols QK, int64_t nq, Cols BK, int nk, const unsigned long long *__restrict__ g_slots,
+                             const uint32_t *__restrict__ g_cnt, const uint32_t *__restrict__ g_start, uint32_t mask,
+                             uint32_t *__restrict__ cnt, uint32_t *__restrict__ qstart,
+                             unsigned long long *__restrict__ total) {
+    __shared__ unsigned long long s_slots[SMEM ? SMEM_SLOTS : 1];
+    __shared__ uint32_t s_cnt[SMEM ? SMEM_SLOTS : 1], s_start[SMEM ? SMEM_SLOTS : 1];
+    const unsigned long long *slots = g_slots;
+    const uint32_t *scnt = g_cnt, *sstart = g_start;
+    if (SMEM) {
+        for (uint32_t i = threadIdx.x; i <= mask; i += blockDim.x) {
+            s_slots[i] = g_slots[i];
+            s_cnt[i] = g_cnt[i];
+            s_start[i] = g_start[i];
+        }
+        __syncthreads();
+        slots = s_slots;
+        scnt = s_cnt;
+        sstart = s_start;
+    }
+    unsigned long long acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_iter = ceil_div(nq, stride) * stride;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_iter; q += stride) {
+        if (q < nq) {
+            uint32_t c = 0, st = 0;
+            if (!has_zero(QK, q, nk)) {
+                const int64_t s = find_slot(slots, mask, BK, QK, q, nk, hash_key(QK, q, nk));
+                if (s >= 0) {
+                    c = scnt[s];
+                    st = sstart[s];
+                }
+            }
+            cnt[q] = c;
+            qstart[q] = st;
+            acc += c;
+        }
+        block_add_u64(acc, total);
+        acc = 0;
+    }
+}
+
+struct Scratch {
+    tid_ctx *ctx;
+    std::vector<void *> ptrs;
+    explicit Scratch(tid_ctx *c) : ctx(c) {}
+    ~Scratch() {
+        for (void *p : ptrs) dev_free(ctx, p);
+    }
+    template <class T>
+    int get(T **p, size_t count) {
+        void *q = nullptr;
+        TID_TRY(dev_alloc(ctx, &q, count * sizeof(T) + 16));
+        ptrs.push_back(q);
+        *p = (T *)q;
+        return TID_OK;
+    }
+};
+
+int read_u64(tid_ctx *ctx, const unsigned long long *d, unsigned long long *h) {
+    TID_TRY_CUDA(cudaMemcpyAsync(h, d, 8, cudaMemcpyDeviceToHost, ctx->stream), "read count");
+    TID_TRY_CUDA(cudaStreamSynchronize(ctx->stream), "read count");
+    return check_ctx_error(ctx);
+}
+
+}  // namespace
+
+int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out) {
+    *out = nullptr;
+    int64_t nl = 0, nr = 0;
+    TID_TRY(set_rows_host(L, &nl));
+    TID_TRY(set_rows_host(R, &nr));
+    // schema: shared variables, R's other columns
+    int lkey[TID_MAX_COLS], rkey[TID_MAX_COLS], rrest[TID_MAX_COLS];
+    int nk = 0, nrest = 0;
+    for (int c = 0; c < L->k; ++c)
+        for (int d = 0; d < R->k; ++d)
+            if (L->vars[c] == R->vars[d]) {
+                lkey[nk] = c;
+                rkey[nk] = d;
+                ++nk;
+            }
+    for (int d = 0; d < R->k; ++d) {
+        bool shared = false;
+        for (int c = 0; c < L->k; ++c) shared = shared || L->vars[c] == R->vars[d];
+        if (!shared) rrest[nrest++] = d;
+    }
+    const int kout = L->k + nrest;
+    if (kout > TID_MAX_COLS) return fail(TID_ERR_ARG, "tid_join: output would have %d columns", kout);
+    int8_t ovars[TID_MAX_COLS];
+    for (int c = 0; c < L->k; ++c) ovars[c] = L->vars[c];
+    for (int c = 0; c < nrest; ++c) ovars[L->k + c] = R->vars[rrest[c]];
+    if (algo != TID_JOIN_AUTO && algo != TID_JOIN_SORT_MERGE && algo != TID_JOIN_HASH)
+        return fail(TID_ERR_ARG, "tid_join: unknown algorithm %d", algo);
+
+    if (nl == 0 || nr == 0) {
+        tid_set *e = nullptr;
+        TID_TRY(set_alloc(ctx, kout, ovars, 0, &e));
+        int rc = set_rows_const(e, 0);
+        if (rc == TID_OK) rc = set_ready(e);
+        if (rc != TID_OK) {
+            tid_set_free(e);
+            return rc;
+        }
+        *out = e;
+        return TID_OK;
+    }
+    bool lprefix = true, rprefix = true;
+    for (int i = 0; i < nk; ++i) {
+        lprefix = lprefix && lkey[i] == i;
+        rprefix = rprefix && rkey[i] == i;
+    }
+    if (algo == TID_JOIN_AUTO) algo = (nk == 0 || (lprefix && rprefix)) ? TID_JOIN_SORT_MERGE : TID_JOIN_HASH;
+    if (nk == 0) algo = TID_JOIN_SORT_MERGE;  // cross product
+
+    cudaStream_t st = ctx->stream;
+    Scratch s(ctx);
+    Cols Lall{}, Rrest{};
+    for (int c = 0; c < L->k; ++c) Lall.c[c] = L->col[c];
+    for (int c = 0; c < nrest; ++c) Rrest.c[c] = R->col[rrest[c]];
+    unsigned long long *d_total = nullptr;
+    TID_TRY(s.get(&d_total, 1));
+    TID_TRY_CUDA(cudaMemsetAsync(d_total, 0, 8, st), "memset");
+
+    uint32_t *off = nullptr, *lo = nullptr;
+    const int32_t *lperm = nullptr, *rperm = nullptr, *rmap = nullptr;
+    int64_t n_probe = nl;
+    bool left_is_probe = true;
+
+    if (algo == TID_JOIN_SORT_MERGE) {
+        Cols LK{}, RK{};
+        // left keys in key order
+        if (lprefix) {
+            for (int i = 0; i < nk; ++i) LK.c[i] = L->col[i];
+        } else {
+            int32_t *p = nullptr;
+            TID_TRY(s.get(&p, nl));
+            const int32_t *kc[TID_MAX_COLS];
+            for (int i = 0; i < nk; ++i) kc[i] = L->col[lkey[i]];
+            TID_TRY(sort_perm(ctx, kc, nk, nl, p));
+            int32_t *g[TID_MAX_COLS];
+            for (int i = 0; i < nk; ++i) TID_TRY(s.get(&g[i], nl));
+            TID_TRY(gather_cols(ctx, kc, nk, p, nl, g));
+            for (int i = 0; i < nk; ++i) LK.c[i] = g[i];
+            lperm = p;
+        }
+        if (rprefix) {
+            for (int i = 0; i < nk; ++i) RK.c[i] = R->col[i];
+        } else {
+            int32_t *p = nullptr;
+            TID_TRY(s.get(&p, nr));
+            const int32_t *kc[TID_MAX_COLS];
+            for (int i = 0; i < nk; ++i) kc[i] = R->col[rkey[i]];
+            TID_TRY(sort_perm(ctx, kc, nk, nr, p));
+            int32_t *g[TID_MAX_COLS];
+            for (int i = 0; i < nk; ++i) TID_TRY(s.get(&g[i], nr));
+            TID_TRY(gather_cols(ctx, kc, nk, p, nr, g));
+            for (int i = 0; i < nk; ++i) RK.c[i] = g[i];
+            rperm = p;
+        }
+        uint32_t *cnt = nullptr;
+        TID_TRY(s.get(&cnt, nl));
+        TID_TRY(s.get(&lo, nl));
+        TID_TRY(s.get(&off, nl));
+        k_sm_count<<<grid_for(nl, 256), 256, 0, st>>>(LK, nl, RK, nr, nk, cnt, lo, d_total);
+        TID_TRY(launch_check("k_sm_count"));
+        TID_TRY(scan_exclusive_u32(ctx, cnt, off, nl, nullptr));
+    } else {
+        // build on the smaller side
+        const bool build_left = nl < nr;
+        const tid_set *B = build_left ? L : R;
+        const tid_set *Q = build_left ? R : L;
+        const int *bkey = build_left ? lkey : rkey;
+        const int *qkey = build_left ? rkey : lkey;
+        const int64_t nb = build_left ? nl : nr, nq = build_left ? nr : nl;
+        Cols BK{}, QK{};
+        for (int i = 0; i < nk; ++i) {
+            BK.c[i] = B->col[bkey[i]];
+            QK.c[i] = Q->col[qkey[i]];
+        }
+        uint32_t T = 64;
+        while ((int64_t)T < 2 * nb) T <<= 1;
+        const uint32_t mask = T - 1;
+        unsigned long long *slots = nullptr;
+        uint32_t *scnt = nullptr, *sstart = nullptr, *cursor = nullptr, *cnt = nullptr;
+        int32_t *grouped = nullptr;
+        TID_TRY(s.get(&slots, T));
+        TID_TRY(s.get(&scnt, T));
+        TID_TRY(s.get(&sstart, T));
+        TID_TRY(s.get(&cursor, T));
+        TID_TRY(s.get(&grouped, nb));
+        TID_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, (size_t)T * 8, st), "memset");
+        TID_TRY_CUDA(cudaMemsetAsync(scnt, 0, (size_t)T * 4, st), "memset");
+        TID_TRY_CUDA(cudaMemsetAsync(cursor, 0, (size_t)T * 4, st), "memset");
+        k_hash_build<<<grid_for(nb, 256), 256, 0, st>>>(BK, nb, nk, slots, scnt, mask, ctx->err_dev);
+        TID_TRY(launch_check("k_hash_build"));
+        TID_TRY(scan_exclusive_u32(ctx, scnt, sstart, T, nullptr));
+        k_hash_scatter<<<grid_for(nb, 256), 256, 0, st>>>(BK, nb, nk, slots, mask, sstart, cursor, grouped);
+        TID_TRY(launch_check("k_hash_scatter"));
+        TID_TRY(s.get(&cnt, nq));
+        TID_TRY(s.get(&lo, nq));
+        TID_TRY(s.get(&off, nq));
+        if (T <= (uint32_t)SMEM_SLOTS)
+            k_hash_count<true><<<grid_for(nq, 256), 256, 0, st>>>(QK, nq, BK, nk, slots, scnt, sstart, mask, cnt, lo, d_total);
+        else
+            k_hash_count<false><<<grid_for(nq, 256), 256, 0, st>>>(QK, nq, BK, nk, slots, scnt, sstart, mask, cnt, lo, d_total);
+        TID_TRY(launch_check("k_hash_count"));
+        TID_TRY(scan_exclusive_u32(ctx, cnt, off, nq, nullptr));
+        rmap = grouped;
+        n_probe = nq;
+        left_is_probe = !build_left;
+    }
+
+    unsigned long long total = 0;
+    TID_TRY(read_u64(ctx, d_total, &total));
+    if (total > (unsigned long long)INT32_MAX)
+        return fail(TID_ERR_CAPACITY, "tid_join: %llu output rows exceed 2^31-1", total);
+    // write, then sort to canonical order
+    MCols oc{};
+    for (int c = 0; c < kout; ++c) TID_TRY(s.get(&oc.c[c], total > 0 ? total : 1));
+    if (total > 0) {
+        k_join_write<<<grid_for((int64_t)total, 256), 256, 0, st>>>(
+            off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, Lall, L->k, Rrest, nrest, oc, left_is_probe);
+        TID_TRY(launch_check("k_join_write"));
+    }
+    const int32_t *ocols[TID_MAX_COLS];
+    for (int c = 0; c < kout; ++c) ocols[c] = oc.c[c];
+    return canonicalize(ctx, ocols, kout, ovars, (int64_t)total, false, out);
+}
+
+}  // namespace tid

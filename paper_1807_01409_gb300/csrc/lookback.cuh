@@ -39,6 +39,20 @@ __device__ __forceinline__ unsigned lb_ticket(const Lookback &lb) {
     return t;
 }
 
+// Persistent kernels: every CTA draws tickets until it gets one >= num_tiles,
+// so one launch draws exactly num_tiles + grid tickets; the last draw resets
+// the counter.  Called by thread 0.
+__device__ __forceinline__ unsigned lb_ticket_persistent(const Lookback &lb, unsigned grid) {
+    unsigned t = atomicAdd(lb.ticket, 1u);
+    if (t == lb.num_tiles + grid - 1) atomicExch(lb.ticket, 0u);
+    return t;
+}
+
+// Mark a tile as given up without waiting (its CTA already gave up once).
+__device__ __forceinline__ void lb_abort(const Lookback &lb, unsigned tile) {
+    if ((threadIdx.x & 31) == 0) lb_store(lb.status + tile, lb_word(lb.epoch, LB_FLAG_ABORT, 0));
+}
+
 // Called by all 32 lanes of ONE warp.  Publishes `total` for `tile` and
 // returns the tile's exclusive prefix (sum of the totals of tiles < tile), or
 // -1 if a wait gave up.

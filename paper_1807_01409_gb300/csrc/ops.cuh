@@ -1,0 +1,53 @@
+// Internal interfaces of the tuple-set operators (bind, filter, sort, join,
+// union, project) shared by the translation units.
+#pragma once
+
+#include "tid_internal.cuh"
+
+namespace tid {
+
+constexpr int MAX_PREDS = 4;  // predicates fused into one compaction pass
+
+struct Pred {  // a FILTER predicate on column `col` of the set being produced
+    int col;
+    int op;
+    int32_t a, b;
+};
+
+struct OutCols {
+    int32_t *col[TID_MAX_COLS];
+};
+
+// exclusive scan of n uint32 (out may alias in); *total_dev receives the sum
+int scan_exclusive_u32(tid_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
+                       unsigned long long *total_dev);
+
+// single-pass compactions (compact.cu); `out` must have capacity >= n
+int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, const int32_t *idx, int64_t n,
+                 const Pred *preds, int n_preds, tid_set *out);
+int compact_filter(tid_ctx *ctx, const tid_set *in, int64_t n, const Pred *preds, int n_preds, tid_set *out);
+int compact_unique(tid_ctx *ctx, const int32_t *const *cols, int k, const int32_t *perm, int64_t n,
+                   tid_set *out);
+
+// sorting (sort.cu)
+// perm receives the stable permutation that orders rows 0..n-1 lexicographically
+// by the key columns keys[0..nk-1] (signed int32 order).
+int sort_perm(tid_ctx *ctx, const int32_t *const *keys, int nk, int64_t n, int32_t *perm);
+// out[c][i] = in[c][perm[i]] for c < k, i < n
+int gather_cols(tid_ctx *ctx, const int32_t *const *in, int k, const int32_t *perm, int64_t n,
+                int32_t *const *out);
+// canonical form (rows sorted in column order; duplicates dropped if dedupe)
+int canonicalize(tid_ctx *ctx, const int32_t *const *cols, int k, const int8_t *vars, int64_t n,
+                 bool dedupe, tid_set **out);
+
+// write a known row count into a set (device count and host mirror)
+int set_rows_const(tid_set *set, int64_t n);
+
+// row count known on the host (waits for the producer if needed)
+int set_rows_host(tid_set *set, int64_t *rows);
+int set_rows_host(const tid_set *set, int64_t *rows);
+
+// joins (join.cu)
+int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out);
+
+}  // namespace tid

@@ -132,8 +132,8 @@ int launch_match(cudaStream_t stream, const int32_t *S, const int32_t *P, const 
                  int64_t n, bool aligned16, int32_t ks, int32_t kp, int32_t ko,
                  int32_t *out, int64_t cap, int64_t *d_rows, int64_t *h_rows_dev,
                  const Lookback &lb);
-unsigned int match_tiles(int64_t n);
+unsigned int match_tiles(int64_t n, int mask);  // mask: bit0 s, bit1 p, bit2 o bound
 
-inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace tid

@@ -361,3 +361,116 @@ def university_queries(store: Store, m: int = 64, seed: int = QUERY_SEED,
         c, pat = cands[i]
         out.append((pat, float(t), c / n))
     return out
+
+
+# ----------------------------------------------------------------------------
+# multi-pattern plans on the university store: star joins, chains, unions, filters
+# ----------------------------------------------------------------------------
+
+X, Y, Z, W = 0, 1, 2, 3   # variable ids; extra star variables use 4, 5, ...
+
+
+def _dom(j):
+    return set(PRED_KIND[j][1])
+
+
+def _rng_classes(j):
+    kind, _, r = PRED_KIND[j]
+    return set(r) if kind == "ent" else set()
+
+
+def university_plans(store: Store, seed: int = QUERY_SEED, n_star: int = 16, n_chain: int = 16,
+                     n_union: int = 8, n_filter: int = 8):
+    """Plans (lists of node dicts, last node = result) of the multi-pattern workload:
+    star-shaped joins on one subject (like the paper's five-pattern listing, all SS),
+    chains through object->subject joins (like subclass transitivity, OS), unions of
+    2-4 subqueries (including overlapping branches), and range FILTERs on encoded
+    literals.  Constants are drawn from stored triples' classes and predicates."""
+    rng = np.random.default_rng(seed + 7)
+    lay = uni_layout(store.meta["subjects"])
+    pid = lay["pred_ids"]
+    cbase = lay["class_base"]
+    ent = [j for j in range(1, len(PRED_KIND)) if PRED_KIND[j][0] == "ent"]
+    lit = [j for j in range(1, len(PRED_KIND)) if PRED_KIND[j][0] == "lit"]
+    plans = []
+
+    def cls_const(k):
+        return int(cbase + k * SUBCLASSES + int(rng.integers(0, 6)))
+
+    def left_deep(nodes, first, rest):
+        cur = first
+        for r in rest:
+            nodes.append({"op": "join", "inputs": [cur, r], "algo": "auto"})
+            cur = len(nodes) - 1
+        return cur
+
+    for i in range(n_star):
+        k = int(rng.choice(8, p=CLASS_FRACTIONS))
+        cand = [j for j in range(1, len(PRED_KIND)) if k in _dom(j)]
+        npat = int(rng.integers(1, min(4, len(cand)) + 1))
+        chosen = [int(x) for x in rng.choice(cand, size=npat, replace=False)]
+        nodes = [{"op": "match", "pattern": Pattern(0, int(pid[0]), cls_const(k), var=(X, -1, -1))}]
+        for t, j in enumerate(chosen):
+            nodes.append({"op": "match", "pattern": Pattern(0, int(pid[j]), 0, var=(X, -1, 4 + t))})
+        cur = left_deep(nodes, 0, list(range(1, len(chosen) + 1)))
+        if i % 2 == 1:
+            nodes.append({"op": "project", "input": cur, "vars": [X, 4]})
+        plans.append((f"star{i}", nodes))
+
+    for i in range(n_chain):
+        # p_a: range meets the domain of p_b (and p_b's range meets p_c's domain)
+        while True:
+            a = int(rng.choice(ent))
+            nb = [j for j in ent if _rng_classes(a) & _dom(j)]
+            if nb:
+                break
+        b = int(rng.choice(nb))
+        k = int(rng.choice(sorted(_dom(a))))
+        nodes = [{"op": "match", "pattern": Pattern(0, int(pid[0]), cls_const(k), var=(X, -1, -1))},
+                 {"op": "match", "pattern": Pattern(0, int(pid[a]), 0, var=(X, -1, Y))},
+                 {"op": "match", "pattern": Pattern(0, int(pid[b]), 0, var=(Y, -1, Z))}]
+        rest = [1, 2]
+        nc = [j for j in ent if _rng_classes(b) & _dom(j)]
+        if i % 3 == 2 and nc:
+            c = int(rng.choice(nc))
+            nodes.append({"op": "match", "pattern": Pattern(0, int(pid[c]), 0, var=(Z, -1, W))})
+            rest.append(3)
+        cur = left_deep(nodes, 0, rest)
+        nodes.append({"op": "project", "input": cur, "vars": [X, Z]})
+        plans.append((f"chain{i}", nodes))
+
+    for i in range(n_union):
+        r = int(rng.integers(0, store.n))
+        s0 = int(store.s[r])
+        nb = 2 + i % 3
+        nodes = []
+        if i % 4 == 3:
+            # overlapping branches: (s ?p ?o) UNION (?s p ?o), a triple may answer both
+            p0 = int(store.p[r])
+            nodes.append({"op": "match", "pattern": Pattern(s0, 0, 0, var=(-1, X, Y))})
+            nodes.append({"op": "match", "pattern": Pattern(0, p0, int(store.o[r]), var=(Z, -1, -1))})
+            nodes.append({"op": "union", "inputs": [0, 1]})
+        else:
+            # same subject, different predicates: (s p_j ?v), mostly predicates s has
+            own = np.unique(store.p[store.s == s0])
+            js = [int(x) for x in rng.choice(own, size=min(nb - 1, len(own)), replace=False)]
+            js.append(int(pid[int(rng.integers(0, len(pid)))]))
+            for pj in js:
+                nodes.append({"op": "match", "pattern": Pattern(s0, pj, 0, var=(-1, -1, Y))})
+            nb = len(js)
+            nodes.append({"op": "union", "inputs": list(range(nb))})
+        plans.append((f"union{i}", nodes))
+
+    for i in range(n_filter):
+        j = int(rng.choice(lit))
+        kexp = PRED_KIND[j][2]
+        lo = int(rng.integers(0, 10 ** kexp // 2))
+        hi = lo + int(10 ** kexp * rng.uniform(0.001, 0.2))
+        k = int(rng.choice(sorted(_dom(j))))
+        nodes = [{"op": "match", "pattern": Pattern(0, int(pid[j]), 0, var=(X, -1, Y))},
+                 {"op": "filter", "input": 0, "var": Y, "cmp": "range", "a": LIT_BASE + lo, "b": LIT_BASE + hi}]
+        if i % 2 == 0:
+            nodes.append({"op": "match", "pattern": Pattern(0, int(pid[0]), cls_const(k), var=(X, -1, -1))})
+            nodes.append({"op": "join", "inputs": [1, 2], "algo": "auto"})
+        plans.append((f"filter{i}", nodes))
+    return plans
