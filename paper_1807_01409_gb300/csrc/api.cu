@@ -65,18 +65,13 @@ void dev_free(tid_ctx *ctx, void *p) {
     if (p) cudaFreeAsync(p, ctx->stream);
 }
 
-int next_epoch(tid_ctx *ctx) {
-    ctx->epoch = (ctx->epoch + 1) & ((1u << 30) - 1);
-    if (ctx->epoch == 0) ctx->epoch = 1;
-    return (int)ctx->epoch;
-}
-
-// Look-back scratch for `num_tiles` tiles: grown on demand (new words are
-// zeroed, i.e. "not ready" for every epoch), ticket counter at 0.
-int lookback_scratch(tid_ctx *ctx, unsigned int num_tiles, Lookback *lb) {
-    if (num_tiles > ctx->lb_cap) {
+// The context's look-back scratch, grown on demand to >= `words` status words
+// (new words are zeroed, i.e. "not ready" for every epoch) plus a ticket
+// counter that is 0 between launches.
+int ctx_scratch(tid_ctx *ctx, size_t words, LbScratch *sc) {
+    if (words > ctx->lb_cap) {
         size_t want = 1024;
-        while (want < num_tiles) want *= 2;
+        while (want < words) want *= 2;
         if (ctx->lb_status) dev_free(ctx, ctx->lb_status);
         ctx->lb_status = nullptr;
         ctx->lb_cap = 0;
@@ -88,12 +83,33 @@ int lookback_scratch(tid_ctx *ctx, unsigned int num_tiles, Lookback *lb) {
         ctx->lb_ticket = (unsigned int *)((char *)p + want * sizeof(unsigned long long));
         ctx->lb_cap = want;
     }
-    lb->status = ctx->lb_status;
-    lb->ticket = ctx->lb_ticket;
-    lb->epoch = (unsigned)next_epoch(ctx);
-    lb->num_tiles = num_tiles;
-    lb->err = ctx->err_dev;
+    sc->status = ctx->lb_status;
+    sc->cap = ctx->lb_cap;
+    sc->ticket = ctx->lb_ticket;
+    sc->err = ctx->err_dev;
+    sc->epoch = &ctx->epoch;
     return TID_OK;
+}
+
+// Look-back state for one launch of `num_tiles` tiles: a fresh epoch, so the
+// status words of earlier launches read as "not ready".
+int make_lookback(const LbScratch &sc, unsigned int num_tiles, Lookback *lb) {
+    if (num_tiles > sc.cap) return fail(TID_ERR_ARG, "look-back scratch holds %zu tiles, %u needed", sc.cap, num_tiles);
+    unsigned e = (*sc.epoch + 1) & ((1u << 30) - 1);
+    if (e == 0) e = 1;
+    *sc.epoch = e;
+    lb->status = sc.status;
+    lb->ticket = sc.ticket;
+    lb->epoch = e;
+    lb->num_tiles = num_tiles;
+    lb->err = sc.err;
+    return TID_OK;
+}
+
+int lookback_scratch(tid_ctx *ctx, unsigned int num_tiles, Lookback *lb) {
+    LbScratch sc{};
+    TID_TRY(ctx_scratch(ctx, num_tiles, &sc));
+    return make_lookback(sc, num_tiles, lb);
 }
 
 // ---------------------------------------------------------------------------
@@ -418,7 +434,7 @@ extern "C" int tid_set_to_host(tid_set *set, int32_t *buf, int64_t cap_rows, int
         TID_TRY_CUDA(cudaMemcpyAsync(buf, set->col[0], bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy set");
     } else {
         void *tmp = nullptr;
-        TID_TRY(dev_alloc(ctx, &tmp, bytes + 256));
+        TID_TRY(dev_alloc(ctx, &tmp, align_up(bytes, 256) + sizeof(int32_t *) * TID_MAX_COLS));
         int32_t **dcols = (int32_t **)((char *)tmp + align_up(bytes, 256));
         cudaError_t e = cudaMemcpyAsync(dcols, set->col, sizeof(int32_t *) * set->k, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) {

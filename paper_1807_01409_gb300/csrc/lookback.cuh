@@ -55,7 +55,10 @@ __device__ __forceinline__ void lb_abort(const Lookback &lb, unsigned tile) {
 
 // Called by all 32 lanes of ONE warp.  Publishes `total` for `tile` and
 // returns the tile's exclusive prefix (sum of the totals of tiles < tile), or
-// -1 if a wait gave up.
+// -1 if a wait gave up.  Each lane reads LB_DEPTH consecutive predecessors, so
+// one round trip to L2 inspects a window of 32 * LB_DEPTH tiles.
+constexpr int LB_DEPTH = 8;
+
 __device__ __forceinline__ long long lb_exclusive_prefix(const Lookback &lb, unsigned tile,
                                                          unsigned total) {
     const unsigned lane = threadIdx.x & 31;
@@ -69,18 +72,31 @@ __device__ __forceinline__ long long lb_exclusive_prefix(const Lookback &lb, uns
     unsigned polls = 0;
     bool gave_up = false;
     while (true) {
-        const long long idx = pos - (long long)lane;
-        unsigned long long w = idx >= 0 ? lb_load(lb.status + idx)
-                                        : lb_word(lb.epoch, LB_FLAG_PREFIX, 0);
-        unsigned flag = ((unsigned)(w >> 34) == lb.epoch) ? (unsigned)(w >> 32) & 3u : 0u;
-        const unsigned val = (unsigned)w;
-        const unsigned pref = __ballot_sync(0xffffffffu, flag == LB_FLAG_PREFIX);
-        const unsigned notready = __ballot_sync(0xffffffffu, flag == 0);
-        const unsigned aborted = __ballot_sync(0xffffffffu, flag == LB_FLAG_ABORT);
+        unsigned long long w[LB_DEPTH];
+#pragma unroll
+        for (int i = 0; i < LB_DEPTH; ++i) {
+            const long long idx = pos - (long long)(lane * LB_DEPTH + i);
+            w[i] = idx >= 0 ? lb_load(lb.status + idx) : lb_word(lb.epoch, LB_FLAG_PREFIX, 0);
+        }
+        // nearest-first scan of this lane's entries up to (and with) its first prefix
+        bool has_pref = false, notready = false, aborted = false;
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int i = 0; i < LB_DEPTH; ++i) {
+            if (has_pref) continue;
+            const unsigned f = ((unsigned)(w[i] >> 34) == lb.epoch) ? (unsigned)(w[i] >> 32) & 3u : 0u;
+            notready = notready || f == 0;
+            aborted = aborted || f == LB_FLAG_ABORT;
+            sum += (unsigned)w[i];
+            has_pref = f == LB_FLAG_PREFIX;
+        }
+        const unsigned pref = __ballot_sync(0xffffffffu, has_pref);
+        const unsigned nr = __ballot_sync(0xffffffffu, notready);
+        const unsigned ab = __ballot_sync(0xffffffffu, aborted);
         const int stop = pref ? __ffs(pref) - 1 : 31;
         const unsigned upto = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
-        if (aborted & upto) { gave_up = true; break; }
-        if (notready & upto) {
+        if (ab & upto) { gave_up = true; break; }
+        if (nr & upto) {
             if (++polls > LB_SPIN_LIMIT) {
                 if (lane == 0) atomicExch(lb.err, TID_ERR_TIMEOUT);
                 gave_up = true;
@@ -89,12 +105,12 @@ __device__ __forceinline__ long long lb_exclusive_prefix(const Lookback &lb, uns
             __nanosleep(polls < 64 ? 32 : 256);
             continue;
         }
-        unsigned long long v = (int)lane <= stop ? val : 0ull;
+        unsigned long long v = (int)lane <= stop ? sum : 0ull;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
         excl += (long long)v;
         if (pref) break;
-        pos -= 32;
+        pos -= 32 * LB_DEPTH;
     }
     if (gave_up) {
         if (lane == 0) lb_store(lb.status + tile, lb_word(lb.epoch, LB_FLAG_ABORT, 0));

@@ -3,22 +3,26 @@
 // Section 3 / Algorithm 1 of the paper: every triple is tested against the key
 // (0 = "?") by its own thread, and the matching positions are reported.  The
 // paper marks a boolean positionArray and copies it back to the host; here the
-// hits are compacted on the device, in ascending order, in ONE pass over the
-// bound columns:
+// hits are compacted on the device, in ascending order, reading the bound
+// columns once and writing each index once:
 //
-//  * persistent CTAs of 256 threads (grid = SMs x resident CTAs) loop over
-//    tiles of 8192 (one bound column) or 4096 (two or three) consecutive
-//    triples drawn from a ticket counter; each thread issues 16-byte loads
-//    (streamed past L1, 256-byte L2 prefetch) for the NEXT tile before the
-//    current tile's look-back and writes, so a CTA keeps 32-48 KB in flight;
-//  * the hit mask is ranked inside the warp with ballots and inside the CTA
-//    with a 32-entry scan of the (load group, warp) totals;
-//  * the tile's output offset comes from a decoupled look-back over the tile
-//    status words (lookback.cuh), so the store is read once and the index list
-//    written once;
-//  * only the columns a pattern binds are read (template on the bound mask).
+//  * every CTA owns one contiguous chunk of the store (up to 512K triples; the
+//    grid is sized to what is resident, so chunks are ~n / (SMs x CTAs/SM));
+//  * phase 1 streams the chunk with 16-byte loads (past L1, 256-byte L2
+//    prefetch; the next step's loads are issued before the current step's
+//    ballots) and keeps a 1-bit-per-triple hit bitmap in shared memory plus a
+//    hit count -- nothing else waits in this phase;
+//  * one decoupled look-back over the chunk counts (lookback.cuh, 256 chunks
+//    per L2 round trip) gives the chunk's output offset;
+//  * phase 2 expands the bitmap: each warp walks a contiguous run of 128-triple
+//    cells, ranks the hits with popc and writes ascending indices contiguously.
+// Only the columns a pattern binds are read (template on the bound mask).
+// Stores larger than (resident CTAs x 512K) triples take several launches;
+// each continues the output where the previous one ended.
 //
-// Bytes moved per launch: 4 * (bound columns) * n read + 4 * hits written.
+// Bytes per launch: 4 * (bound columns) * n read + 4 * hits written.
+
+#include <algorithm>
 
 #include "lookback.cuh"
 
@@ -28,15 +32,10 @@ namespace {
 
 constexpr int K1_THREADS = 256;
 constexpr int K1_WARPS = K1_THREADS / 32;
-
-// Load groups (16-byte loads per thread per bound column) by bound-column
-// count: one column -> 8 (tile of 8192 triples), two or three -> 4 (4096).
-template <int MASK>
-struct K1Shape {
-    static constexpr int B = ((MASK & 1) ? 1 : 0) + ((MASK & 2) ? 1 : 0) + ((MASK & 4) ? 1 : 0);
-    static constexpr int G = B == 1 ? 8 : 4;
-    static constexpr int TILE = K1_THREADS * 4 * G;
-};
+constexpr int K1_G = 4;                                   // 16-byte loads per column per thread per step
+constexpr int K1_STEP = K1_THREADS * 4 * K1_G;            // 4096 triples per step
+constexpr int K1_BITMAP_BYTES = 64 * 1024;                // shared-memory hit bitmap per CTA
+constexpr int64_t K1_CHUNK_MAX = (int64_t)K1_BITMAP_BYTES * 8;  // 524288 triples
 
 __device__ __forceinline__ int4 ld_stream_v4(const int32_t *p) {
     int4 v;
@@ -69,131 +68,118 @@ __device__ __forceinline__ unsigned eq4(int4 v, int32_t k) {
            ((unsigned)(v.z == k) << 2) | ((unsigned)(v.w == k) << 3);
 }
 
-// Persistent, software-pipelined scan: each CTA loops over tiles drawn from the
-// ticket counter.  The next tile's ticket is drawn and its loads are issued
-// before the current tile's look-back and writes, so those latencies overlap
-// the next tile's memory traffic.
 template <int MASK, bool VEC>
 __global__ void __launch_bounds__(K1_THREADS)
 k1_match(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int32_t *__restrict__ O,
-         int64_t n, int32_t ks, int32_t kp, int32_t ko, int32_t *__restrict__ out, int64_t cap,
+         int64_t n, int64_t seg_begin, int64_t seg_end, int64_t chunk_len, int first_seg,
+         int32_t ks, int32_t kp, int32_t ko, int32_t *__restrict__ out, int64_t cap,
          int64_t *__restrict__ d_rows, int64_t *__restrict__ h_rows, Lookback lb) {
-    constexpr int G = K1Shape<MASK>::G;
-    constexpr int TILE = K1Shape<MASK>::TILE;
-    constexpr int NOFF = G * K1_WARPS;   // (group, warp) counts per tile: 32 or 64
-    constexpr int PER_LANE = NOFF / 32;  // 1 or 2
-    __shared__ unsigned s_next;
-    __shared__ unsigned s_off[NOFF];
-    __shared__ long long s_prefix;
+    extern __shared__ uint32_t s_bits[];  // 4 words per 128-triple cell
+    __shared__ unsigned s_tile;
+    __shared__ unsigned s_wtot[K1_WARPS];
+    __shared__ long long s_base, s_prefix;
 
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    if (threadIdx.x == 0) s_next = lb_ticket_persistent(lb, gridDim.x);
+    if (threadIdx.x == 0) {
+        s_tile = lb_ticket(lb);
+        s_base = first_seg ? 0 : *d_rows;  // hits of the earlier segments
+    }
     __syncthreads();
-    unsigned tile = s_next;
-    bool dead = false;  // this CTA gave up a wait: mark its remaining tiles aborted
+    const unsigned tile = s_tile;
+    if (tile >= lb.num_tiles) return;
+    const int64_t c0 = seg_begin + (int64_t)tile * chunk_len;
+    const int64_t c1 = min(c0 + chunk_len, seg_end);
+    const int steps = (int)ceil_div(c1 - c0, K1_STEP);
 
-    int4 vs[G], vp[G], vo[G];
-    auto issue = [&](unsigned t) {
-        const int64_t tb = (int64_t)t * TILE;
+    // ---- phase 1: stream the chunk into the shared-memory bitmap
+    int4 vs[K1_G], vp[K1_G], vo[K1_G];
+    auto issue = [&](int64_t base) {
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const int64_t e0 = tb + g * (K1_THREADS * 4) + threadIdx.x * 4;
+        for (int g = 0; g < K1_G; ++g) {
+            const int64_t e0 = base + g * (K1_THREADS * 4) + threadIdx.x * 4;
             if (MASK & 1) vs[g] = load4<VEC>(S, e0, n);
             if (MASK & 2) vp[g] = load4<VEC>(P, e0, n);
             if (MASK & 4) vo[g] = load4<VEC>(O, e0, n);
         }
     };
-    if (tile < lb.num_tiles) issue(tile);
-
-    while (tile < lb.num_tiles) {
-        const int64_t tile_base = (int64_t)tile * TILE;
-        __syncthreads();  // every thread has read s_next / s_off / s_prefix of the last round
-        if (threadIdx.x == 0) s_next = lb_ticket_persistent(lb, gridDim.x);
-
-        unsigned m[G];
+    unsigned cnt = 0;  // this warp's hits (same value in every lane)
+    issue(c0);
+    for (int st = 0; st < steps; ++st) {
+        const int64_t base = c0 + (int64_t)st * K1_STEP;
+        unsigned m[K1_G];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const int64_t e0 = tile_base + g * (K1_THREADS * 4) + threadIdx.x * 4;
+        for (int g = 0; g < K1_G; ++g) {
             unsigned mm = 0xFu;
             if (MASK & 1) mm &= eq4(vs[g], ks);
             if (MASK & 2) mm &= eq4(vp[g], kp);
             if (MASK & 4) mm &= eq4(vo[g], ko);
-            if (e0 + 3 >= n) {  // ragged last tile
-                const int64_t left = n - e0;
-                mm &= left <= 0 ? 0u : (left >= 4 ? 0xFu : ((1u << left) - 1u));
-            }
+            const int64_t left = c1 - (base + g * (K1_THREADS * 4) + threadIdx.x * 4);
+            if (left < 4) mm &= left <= 0 ? 0u : ((1u << left) - 1u);
             m[g] = mm;
         }
-        unsigned wpre[G];
+        if (st + 1 < steps) issue(base + K1_STEP);
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            unsigned pre = 0, tot = 0;
+        for (int g = 0; g < K1_G; ++g) {
+            const int cell = (st * K1_G + g) * K1_WARPS + warp;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const unsigned b = __ballot_sync(0xffffffffu, (m[g] >> e) & 1u);
-                pre += __popc(b & lt);
-                tot += __popc(b);
+                const unsigned word = __ballot_sync(0xffffffffu, (m[g] >> e) & 1u);
+                if (lane == (unsigned)e) s_bits[cell * 4 + e] = word;
+                cnt += __popc(word);
             }
-            wpre[g] = pre;
-            if (lane == 0) s_off[g * K1_WARPS + warp] = tot;
         }
-        __syncthreads();
-        const unsigned next = s_next;
-        if (next < lb.num_tiles) issue(next);  // in flight during the look-back and writes
+    }
+    if (lane == 0) s_wtot[warp] = cnt;
+    __syncthreads();
 
-        if (warp == 0) {
-            unsigned a[PER_LANE], sum = 0;
+    // ---- chunk offset: one look-back over the chunk counts
+    if (warp == 0) {
+        unsigned t = lane < K1_WARPS ? s_wtot[lane] : 0u;
 #pragma unroll
-            for (int i = 0; i < PER_LANE; ++i) {
-                a[i] = s_off[lane * PER_LANE + i];
-                sum += a[i];
-            }
-            unsigned x = sum;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
-                if ((int)lane >= d) x += y;
-            }
-            unsigned run = x - sum;
-#pragma unroll
-            for (int i = 0; i < PER_LANE; ++i) {
-                s_off[lane * PER_LANE + i] = run;
-                run += a[i];
-            }
-            const unsigned total = __shfl_sync(0xffffffffu, x, 31);
-            long long excl = -1;
-            if (!dead) excl = lb_exclusive_prefix(lb, tile, total);
-            else lb_abort(lb, tile);
-            if (lane == 0) {
-                s_prefix = excl;
-                if (tile == lb.num_tiles - 1 && excl >= 0) {
-                    *d_rows = excl + total;
-                    *h_rows = excl + total;
-                }
+        for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+        const long long excl = lb_exclusive_prefix(lb, tile, t);
+        if (lane == 0) {
+            s_prefix = excl;
+            if (tile == lb.num_tiles - 1 && excl >= 0) {
+                *d_rows = s_base + excl + t;
+                *h_rows = s_base + excl + t;
             }
         }
-        __syncthreads();
-        const long long prefix = s_prefix;
-        if (prefix < 0) {
-            dead = true;
-        } else {
+    }
+    __syncthreads();
+    if (s_prefix < 0) return;
+
+    // ---- phase 2: expand the bitmap; warp w owns cells [q0, q1)
+    const int ncells = steps * K1_G * K1_WARPS;
+    const int per = (ncells + K1_WARPS - 1) / K1_WARPS;
+    const int q0 = min(ncells, (int)warp * per), q1 = min(ncells, q0 + per);
+    unsigned wt = 0;
+    for (int q = q0 + (int)lane; q < q1; q += 32)
+        wt += __popc(s_bits[q * 4]) + __popc(s_bits[q * 4 + 1]) + __popc(s_bits[q * 4 + 2]) +
+              __popc(s_bits[q * 4 + 3]);
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const unsigned mm = m[g];
-                if (!mm) continue;
-                long long pos = prefix + s_off[g * K1_WARPS + warp] + wpre[g];
-                const int64_t e0 = tile_base + g * (K1_THREADS * 4) + threadIdx.x * 4;
+    for (int d = 16; d > 0; d >>= 1) wt += __shfl_xor_sync(0xffffffffu, wt, d);
+    __syncthreads();  // s_wtot is reused
+    if (lane == 0) s_wtot[warp] = wt;
+    __syncthreads();
+    long long run = s_base + s_prefix;
+    for (unsigned w = 0; w < warp; ++w) run += s_wtot[w];
+    for (int q = q0; q < q1; ++q) {
+        const uint4 wd = *reinterpret_cast<const uint4 *>(s_bits + q * 4);
+        if ((wd.x | wd.y | wd.z | wd.w) == 0u) continue;
+        const unsigned nib = ((wd.x >> lane) & 1u) | (((wd.y >> lane) & 1u) << 1) |
+                             (((wd.z >> lane) & 1u) << 2) | (((wd.w >> lane) & 1u) << 3);
+        long long pos = run + __popc(wd.x & lt) + __popc(wd.y & lt) + __popc(wd.z & lt) + __popc(wd.w & lt);
+        const int64_t elem = c0 + (int64_t)q * 128 + lane * 4;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if ((mm >> e) & 1u) {
-                        if (pos < cap) out[pos] = (int32_t)(e0 + e);
-                        ++pos;
-                    }
-                }
+        for (int e = 0; e < 4; ++e) {
+            if ((nib >> e) & 1u) {
+                if (pos < cap) out[pos] = (int32_t)(elem + e);
+                ++pos;
             }
         }
-        tile = next;
+        run += __popc(wd.x) + __popc(wd.y) + __popc(wd.z) + __popc(wd.w);
     }
 }
 
@@ -226,56 +212,70 @@ int sm_count() {
     return cached;
 }
 
+// resident CTAs of one k1 instance (opts the kernel into 64 KB of dynamic shared memory)
 template <int MASK, bool VEC>
-unsigned persistent_grid(unsigned tiles) {
-    static int per_sm = 0;
-    if (!per_sm) {
+unsigned resident_ctas() {
+    static unsigned cached = 0;
+    if (!cached) {
+        cudaFuncSetAttribute(k1_match<MASK, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, K1_BITMAP_BYTES);
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k1_match<MASK, VEC>, K1_THREADS, 0) != cudaSuccess ||
-            v <= 0)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k1_match<MASK, VEC>, K1_THREADS, K1_BITMAP_BYTES) !=
+                cudaSuccess || v <= 0)
             v = 1;
-        per_sm = v;
+        cached = (unsigned)(v * sm_count());
     }
-    const unsigned g = (unsigned)(per_sm * sm_count());
-    return tiles < g ? tiles : g;
+    return cached;
 }
 
-template <int MASK>
-int launch_mask(bool vec, cudaStream_t st, const int32_t *S, const int32_t *P, const int32_t *O,
-                int64_t n, int32_t ks, int32_t kp, int32_t ko, int32_t *out, int64_t cap,
-                int64_t *d_rows, int64_t *h_rows, const Lookback &lb) {
-    if (vec)
-        k1_match<MASK, true><<<persistent_grid<MASK, true>(lb.num_tiles), K1_THREADS, 0, st>>>(
-            S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows, lb);
-    else
-        k1_match<MASK, false><<<persistent_grid<MASK, false>(lb.num_tiles), K1_THREADS, 0, st>>>(
-            S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows, lb);
+template <int MASK, bool VEC>
+int run_segments(cudaStream_t st, const int32_t *S, const int32_t *P, const int32_t *O, int64_t n,
+                 int32_t ks, int32_t kp, int32_t ko, int32_t *out, int64_t cap, int64_t *d_rows,
+                 int64_t *h_rows, const LbScratch &sc) {
+    const unsigned grid_max = resident_ctas<MASK, VEC>();
+    const int64_t seg_max = (int64_t)grid_max * K1_CHUNK_MAX;
+    for (int64_t sb = 0; sb < n; sb += seg_max) {
+        const int64_t len = std::min<int64_t>(n - sb, seg_max);
+        int64_t chunks = std::min<int64_t>(grid_max, ceil_div(len, K1_STEP));
+        const int64_t chunk_len = ceil_div(ceil_div(len, chunks), K1_STEP) * K1_STEP;
+        chunks = ceil_div(len, chunk_len);
+        Lookback lb{};
+        TID_TRY(make_lookback(sc, (unsigned)chunks, &lb));
+        k1_match<MASK, VEC><<<(unsigned)chunks, K1_THREADS, (size_t)(chunk_len / 8), st>>>(
+            S, P, O, n, sb, sb + len, chunk_len, sb == 0, ks, kp, ko, out, cap, d_rows, h_rows, lb);
+        TID_TRY(launch_check("k1_match"));
+    }
     return TID_OK;
 }
 
-int tile_of_mask(int mask) {
-    switch (mask) {
-        case 1: return K1Shape<1>::TILE;
-        case 2: return K1Shape<2>::TILE;
-        case 4: return K1Shape<4>::TILE;
-        case 3: return K1Shape<3>::TILE;
-        case 5: return K1Shape<5>::TILE;
-        case 6: return K1Shape<6>::TILE;
-        default: return K1Shape<7>::TILE;
-    }
+template <int MASK>
+int run_mask(bool vec, cudaStream_t st, const int32_t *S, const int32_t *P, const int32_t *O, int64_t n,
+             int32_t ks, int32_t kp, int32_t ko, int32_t *out, int64_t cap, int64_t *d_rows, int64_t *h_rows,
+             const LbScratch &sc) {
+    return vec ? run_segments<MASK, true>(st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows, sc)
+               : run_segments<MASK, false>(st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows, sc);
 }
 
 }  // namespace
 
-unsigned int match_tiles(int64_t n, int mask) { return (unsigned int)ceil_div(n, tile_of_mask(mask)); }
+// Status words one K1 launch needs at most (one per CTA of the largest grid).
+unsigned int match_scratch_words() {
+    unsigned m = 0;
+    m = std::max(m, resident_ctas<1, true>());
+    m = std::max(m, resident_ctas<1, false>());
+    m = std::max(m, resident_ctas<3, true>());
+    m = std::max(m, resident_ctas<3, false>());
+    m = std::max(m, resident_ctas<7, true>());
+    m = std::max(m, resident_ctas<7, false>());
+    return m;
+}
 
 // Launch K1 (or the iota kernel for (?,?,?)).  The caller guarantees: n >= 0,
-// cap >= 0, out holds cap int32, lb has room for match_tiles(n) status words
-// and a zero ticket, d_rows / h_rows_dev are device-visible int64 slots.
+// cap >= 0, out holds cap int32, sc holds at least match_scratch_words()
+// status words and a zero ticket, d_rows / h_rows_dev are device-visible int64.
 int launch_match(cudaStream_t st, const int32_t *S, const int32_t *P, const int32_t *O,
                  int64_t n, bool aligned16, int32_t ks, int32_t kp, int32_t ko,
                  int32_t *out, int64_t cap, int64_t *d_rows, int64_t *h_rows_dev,
-                 const Lookback &lb) {
+                 const LbScratch &sc) {
     const int mask = (ks != 0 ? 1 : 0) | (kp != 0 ? 2 : 0) | (ko != 0 ? 4 : 0);
     if (n == 0) {
         TID_TRY_CUDA(cudaMemsetAsync(d_rows, 0, sizeof(int64_t), st), "memset rows");
@@ -288,17 +288,16 @@ int launch_match(cudaStream_t st, const int32_t *S, const int32_t *P, const int3
         k1_iota<<<grid, 256, 0, st>>>(n, out, cap, d_rows, h_rows_dev);
         return launch_check("k1_iota");
     }
-    if (lb.num_tiles != match_tiles(n, mask)) return fail(TID_ERR_ARG, "k1_match: look-back scratch sized for another tiling");
+    if (sc.cap < match_scratch_words()) return fail(TID_ERR_ARG, "k1_match: look-back scratch too small");
     switch (mask) {
-        case 1: launch_mask<1>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, lb); break;
-        case 2: launch_mask<2>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, lb); break;
-        case 3: launch_mask<3>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, lb); break;
-        case 4: launch_mask<4>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, lb); break;
-        case 5: launch_mask<5>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, lb); break;
-        case 6: launch_mask<6>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, lb); break;
-        default: launch_mask<7>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, lb); break;
+        case 1: return run_mask<1>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, sc);
+        case 2: return run_mask<2>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, sc);
+        case 3: return run_mask<3>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, sc);
+        case 4: return run_mask<4>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, sc);
+        case 5: return run_mask<5>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, sc);
+        case 6: return run_mask<6>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, sc);
+        default: return run_mask<7>(aligned16, st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows_dev, sc);
     }
-    return launch_check("k1_match");
 }
 
 }  // namespace tid
@@ -318,13 +317,11 @@ extern "C" int tid_match(tid_ctx *ctx, const tid_store *st, tid_pattern pat, tid
     const int8_t var = -1;
     tid_set *set = nullptr;
     TID_TRY(set_alloc(ctx, 1, &var, n, &set));
-    Lookback lb{};
-    int rc = TID_OK;
-    const int mask = (pat.s != 0) | ((pat.p != 0) << 1) | ((pat.o != 0) << 2);
-    if (n > 0 && mask != 0) rc = lookback_scratch(ctx, match_tiles(n, mask), &lb);
+    LbScratch sc{};
+    int rc = ctx_scratch(ctx, match_scratch_words(), &sc);
     if (rc == TID_OK)
         rc = launch_match(ctx->stream, st->s, st->p, st->o, n, st->aligned16, pat.s, pat.p, pat.o,
-                          set->col[0], set->cap, set->d_rows, set->slot.dev, lb);
+                          set->col[0], set->cap, set->d_rows, set->slot.dev, sc);
     if (rc == TID_OK) rc = set_ready(set);
     if (rc != TID_OK) {
         tid_set_free(set);

@@ -4,16 +4,18 @@
 // subqueries: every triple is compared with each key and marked with the list
 // of subqueries it answers (a triple may answer several, as in the paper's
 // second union example).  Here the marks become one ascending index list per
-// pattern, built in the same pass:
-//  * the union of the patterns' bound columns is loaded once per tile, with the
-//    same persistent, software-pipelined loop as K1 (next tile's loads issued
-//    before the current tile's look-backs and writes);
-//  * each pattern has its own look-back chain (status words j*tiles..), all
-//    chains share one ticket; warp w resolves the chains of patterns w, w+8;
-//  * per-pattern hit masks are kept packed (16 bits per pattern); the in-warp
-//    ranks are recomputed from ballots in the write phase instead of being held
-//    in registers.
+// pattern, built in the same pass, with the structure of K1:
+//  * each CTA streams one contiguous chunk per segment, loading the union of
+//    the patterns' bound columns once, and keeps one shared-memory hit bitmap
+//    per pattern (64 KB in all, so chunks shrink as patterns are added);
+//  * every pattern has one look-back chain over (segment, chunk) in store
+//    order; warp w resolves the chains of patterns w and w + 8;
+//  * each warp expands a contiguous run of 128-triple cells per pattern and
+//    writes ascending indices contiguously.
+// A launch walks all segments of the store (segment = resident CTAs x chunk).
 // Bytes per launch: 4 * |union of bound columns| * n read + 4 * sum of hits written.
+
+#include <algorithm>
 
 #include "lookback.cuh"
 
@@ -23,9 +25,9 @@ namespace {
 
 constexpr int K2_THREADS = 256;
 constexpr int K2_WARPS = K2_THREADS / 32;
-constexpr int K2_G = 4;                           // 16-byte loads per column per thread
-constexpr int K2_TILE = K2_THREADS * 4 * K2_G;    // 4096 triples
-constexpr int K2_NOFF = K2_G * K2_WARPS;          // 32 (group, warp) counts per pattern
+constexpr int K2_G = 4;                          // 16-byte loads per column per thread per step
+constexpr int K2_STEP = K2_THREADS * 4 * K2_G;   // 4096 triples
+constexpr int K2_BITMAP_BYTES = 64 * 1024;       // all patterns' bitmaps per CTA
 
 struct MultiArgs {
     int m;
@@ -71,129 +73,159 @@ __device__ __forceinline__ unsigned eq4w(int4 v, int32_t k) {
 template <int U, bool VEC>
 __global__ void __launch_bounds__(K2_THREADS)
 k2_match_multi(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int32_t *__restrict__ O,
-               int64_t n, MultiArgs args, Lookback lb) {
-    __shared__ unsigned s_next;
-    __shared__ unsigned s_off[TID_MAX_MULTI][K2_NOFF];
+               int64_t n, int64_t chunk_len, int n_seg, MultiArgs args, Lookback lb) {
+    extern __shared__ uint32_t s_bits[];  // pattern j: words [j * wpp, (j+1) * wpp)
+    __shared__ unsigned s_tile;
+    __shared__ unsigned s_cnt[TID_MAX_MULTI][K2_WARPS];
     __shared__ long long s_prefix[TID_MAX_MULTI];
 
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int m = args.m;
-    if (threadIdx.x == 0) s_next = lb_ticket_persistent(lb, gridDim.x);
+    const unsigned G = lb.num_tiles;  // chunks per segment (= grid)
+    const int wpp = (int)(chunk_len / 32);
+    if (threadIdx.x == 0) s_tile = lb_ticket(lb);
     __syncthreads();
-    unsigned tile = s_next;
+    const unsigned t = s_tile;
+    if (t >= G) return;
     bool dead = false;
-
     int4 vs[K2_G], vp[K2_G], vo[K2_G];
-    auto issue = [&](unsigned t) {
-        const int64_t tb = (int64_t)t * K2_TILE;
+    auto issue = [&](int64_t base) {
 #pragma unroll
         for (int g = 0; g < K2_G; ++g) {
-            const int64_t e0 = tb + g * (K2_THREADS * 4) + threadIdx.x * 4;
+            const int64_t e0 = base + g * (K2_THREADS * 4) + threadIdx.x * 4;
             if (U & 1) vs[g] = load4<VEC>(S, e0, n);
             if (U & 2) vp[g] = load4<VEC>(P, e0, n);
             if (U & 4) vo[g] = load4<VEC>(O, e0, n);
         }
     };
-    if (tile < lb.num_tiles) issue(tile);
 
-    while (tile < lb.num_tiles) {
-        const int64_t tile_base = (int64_t)tile * K2_TILE;
-        __syncthreads();
-        if (threadIdx.x == 0) s_next = lb_ticket_persistent(lb, gridDim.x);
+    for (int sg = 0; sg < n_seg; ++sg) {
+        const int64_t c0 = ((int64_t)sg * G + t) * chunk_len;
+        const int64_t c1 = min(c0 + chunk_len, n);
+        const int steps = (!dead && c1 > c0) ? (int)ceil_div(c1 - c0, K2_STEP) : 0;
+        unsigned cnt[TID_MAX_MULTI];
+#pragma unroll
+        for (int j = 0; j < TID_MAX_MULTI; ++j) cnt[j] = 0;
 
-        // valid-element mask per group (ragged last tile)
-        unsigned valid = 0;
+        // ---- stream the chunk: one bitmap per pattern
+        if (steps > 0) issue(c0);
+        for (int st = 0; st < steps; ++st) {
+            const int64_t base = c0 + (int64_t)st * K2_STEP;
+            unsigned valid = 0;
 #pragma unroll
-        for (int g = 0; g < K2_G; ++g) {
-            const int64_t left = n - (tile_base + g * (K2_THREADS * 4) + threadIdx.x * 4);
-            const unsigned vm = left <= 0 ? 0u : (left >= 4 ? 0xFu : ((1u << left) - 1u));
-            valid |= vm << (4 * g);
-        }
-        // packed hit masks: bits 4g..4g+3 of hm[j] for load group g
-        uint16_t hm[TID_MAX_MULTI];
-#pragma unroll
-        for (int j = 0; j < TID_MAX_MULTI; ++j) {
-            unsigned bits = 0;
-            if (j < m) {
-#pragma unroll
-                for (int g = 0; g < K2_G; ++g) {
-                    unsigned mm = 0xFu;
-                    if (U & 1) mm &= eq4w(vs[g], args.key[j][0]);
-                    if (U & 2) mm &= eq4w(vp[g], args.key[j][1]);
-                    if (U & 4) mm &= eq4w(vo[g], args.key[j][2]);
-                    bits |= mm << (4 * g);
-                }
-                bits &= valid;
-#pragma unroll
-                for (int g = 0; g < K2_G; ++g) {
-                    unsigned tot = 0;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) tot += __popc(__ballot_sync(0xffffffffu, (bits >> (4 * g + e)) & 1u));
-                    if (lane == 0) s_off[j][g * K2_WARPS + warp] = tot;
-                }
+            for (int g = 0; g < K2_G; ++g) {
+                const int64_t left = c1 - (base + g * (K2_THREADS * 4) + threadIdx.x * 4);
+                const unsigned vm = left <= 0 ? 0u : (left >= 4 ? 0xFu : ((1u << left) - 1u));
+                valid |= vm << (4 * g);
             }
-            hm[j] = (uint16_t)bits;
-        }
-        __syncthreads();
-        const unsigned next = s_next;
-        if (next < lb.num_tiles) issue(next);
-
-        for (int j = warp; j < m; j += K2_WARPS) {
-            const unsigned v = s_off[j][lane];
-            unsigned x = v;
+            uint16_t hm[TID_MAX_MULTI];
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
-                if ((int)lane >= d) x += y;
-            }
-            s_off[j][lane] = x - v;
-            const unsigned total = __shfl_sync(0xffffffffu, x, 31);
-            Lookback lj = lb;
-            lj.status = lb.status + (size_t)j * lb.num_tiles;
-            long long excl = -1;
-            if (!dead) excl = lb_exclusive_prefix(lj, tile, total);
-            else lb_abort(lj, tile);
-            if (lane == 0) {
-                s_prefix[j] = excl;
-                if (tile == lb.num_tiles - 1 && excl >= 0) {
-                    *args.d_rows[j] = excl + total;
-                    *args.h_rows[j] = excl + total;
+            for (int j = 0; j < TID_MAX_MULTI; ++j) {
+                unsigned bits = 0;
+                if (j < m) {
+#pragma unroll
+                    for (int g = 0; g < K2_G; ++g) {
+                        unsigned mm = 0xFu;
+                        if (U & 1) mm &= eq4w(vs[g], args.key[j][0]);
+                        if (U & 2) mm &= eq4w(vp[g], args.key[j][1]);
+                        if (U & 4) mm &= eq4w(vo[g], args.key[j][2]);
+                        bits |= mm << (4 * g);
+                    }
                 }
+                hm[j] = (uint16_t)(bits & valid);
             }
-        }
-        __syncthreads();
-        bool any_dead = false;
-        for (int j = 0; j < m; ++j) any_dead = any_dead || s_prefix[j] < 0;
-        if (any_dead) {
-            dead = true;
-        } else {
+            if (st + 1 < steps) issue(base + K2_STEP);
 #pragma unroll
             for (int j = 0; j < TID_MAX_MULTI; ++j) {
                 if (j >= m) break;
-                const unsigned bits = hm[j];
-                const long long prefix = s_prefix[j];
 #pragma unroll
                 for (int g = 0; g < K2_G; ++g) {
-                    unsigned pre = 0;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        pre += __popc(__ballot_sync(0xffffffffu, (bits >> (4 * g + e)) & 1u) & lt);
-                    const unsigned mm = (bits >> (4 * g)) & 0xFu;
-                    if (!mm) continue;
-                    long long pos = prefix + s_off[j][g * K2_WARPS + warp] + pre;
-                    const int64_t e0 = tile_base + g * (K2_THREADS * 4) + threadIdx.x * 4;
+                    const int cell = (st * K2_G + g) * K2_WARPS + warp;
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        if ((mm >> e) & 1u) {
-                            if (pos < args.cap[j]) args.out[j][pos] = (int32_t)(e0 + e);
-                            ++pos;
-                        }
+                        const unsigned word = __ballot_sync(0xffffffffu, (hm[j] >> (4 * g + e)) & 1u);
+                        if (lane == (unsigned)e) s_bits[j * wpp + cell * 4 + e] = word;
+                        cnt[j] += __popc(word);
                     }
                 }
             }
         }
-        tile = next;
+        if (lane == 0)
+            for (int j = 0; j < m; ++j) s_cnt[j][warp] = cnt[j];
+        __syncthreads();
+
+        // ---- chunk offsets: chain of pattern j over (segment, chunk)
+        const unsigned idx = (unsigned)sg * G + t;
+        for (int j = (int)warp; j < m; j += K2_WARPS) {
+            unsigned tot = lane < K2_WARPS ? s_cnt[j][lane] : 0u;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, d);
+            Lookback lj = lb;
+            lj.status = lb.status + (size_t)j * n_seg * G;
+            lj.num_tiles = (unsigned)n_seg * G;
+            long long excl = -1;
+            if (!dead) excl = lb_exclusive_prefix(lj, idx, tot);
+            else lb_abort(lj, idx);
+            if (lane == 0) {
+                s_prefix[j] = excl;
+                if (idx == lj.num_tiles - 1 && excl >= 0) {
+                    *args.d_rows[j] = excl + tot;
+                    *args.h_rows[j] = excl + tot;
+                }
+            }
+        }
+        __syncthreads();
+        for (int j = 0; j < m; ++j) dead = dead || s_prefix[j] < 0;
+
+        // ---- expand: warp w owns cells [q0, q1) of every pattern
+        if (!dead && steps > 0) {
+            const int ncells = steps * K2_G * K2_WARPS;
+            const int per = (ncells + K2_WARPS - 1) / K2_WARPS;
+            const int q0 = min(ncells, (int)warp * per), q1 = min(ncells, q0 + per);
+            unsigned blk[TID_MAX_MULTI];
+#pragma unroll
+            for (int j = 0; j < TID_MAX_MULTI; ++j) {
+                unsigned wt = 0;
+                if (j < m) {
+                    const uint32_t *b = s_bits + j * wpp;
+                    for (int q = q0 + (int)lane; q < q1; q += 32)
+                        wt += __popc(b[q * 4]) + __popc(b[q * 4 + 1]) + __popc(b[q * 4 + 2]) + __popc(b[q * 4 + 3]);
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) wt += __shfl_xor_sync(0xffffffffu, wt, d);
+                }
+                blk[j] = wt;
+            }
+            __syncthreads();  // s_cnt is reused
+            if (lane == 0)
+                for (int j = 0; j < m; ++j) s_cnt[j][warp] = blk[j];
+            __syncthreads();
+            for (int j = 0; j < m; ++j) {
+                long long run = s_prefix[j];
+                for (unsigned w = 0; w < warp; ++w) run += s_cnt[j][w];
+                const uint32_t *b = s_bits + j * wpp;
+                int32_t *out = args.out[j];
+                const int64_t cap = args.cap[j];
+                for (int q = q0; q < q1; ++q) {
+                    const uint4 wd = *reinterpret_cast<const uint4 *>(b + q * 4);
+                    if ((wd.x | wd.y | wd.z | wd.w) == 0u) continue;
+                    const unsigned nib = ((wd.x >> lane) & 1u) | (((wd.y >> lane) & 1u) << 1) |
+                                         (((wd.z >> lane) & 1u) << 2) | (((wd.w >> lane) & 1u) << 3);
+                    long long pos = run + __popc(wd.x & lt) + __popc(wd.y & lt) + __popc(wd.z & lt) +
+                                    __popc(wd.w & lt);
+                    const int64_t elem = c0 + (int64_t)q * 128 + lane * 4;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if ((nib >> e) & 1u) {
+                            if (pos < cap) out[pos] = (int32_t)(elem + e);
+                            ++pos;
+                        }
+                    }
+                    run += __popc(wd.x) + __popc(wd.y) + __popc(wd.z) + __popc(wd.w);
+                }
+            }
+        }
+        __syncthreads();  // bitmaps and counts are rewritten by the next segment
     }
 }
 
@@ -209,26 +241,46 @@ int sm_count_k2() {
 }
 
 template <int U, bool VEC>
-int launch_u(cudaStream_t st, const int32_t *S, const int32_t *P, const int32_t *O, int64_t n,
-             const MultiArgs &a, const Lookback &lb) {
-    static int per_sm = 0;
-    if (!per_sm) {
+unsigned resident_k2() {
+    static unsigned cached = 0;
+    if (!cached) {
+        cudaFuncSetAttribute(k2_match_multi<U, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, K2_BITMAP_BYTES);
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k2_match_multi<U, VEC>, K2_THREADS, 0) != cudaSuccess ||
-            v <= 0)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k2_match_multi<U, VEC>, K2_THREADS, K2_BITMAP_BYTES) !=
+                cudaSuccess || v <= 0)
             v = 1;
-        per_sm = v;
+        cached = (unsigned)(v * sm_count_k2());
     }
-    unsigned grid = (unsigned)(per_sm * sm_count_k2());
-    if (grid > lb.num_tiles) grid = lb.num_tiles;
-    k2_match_multi<U, VEC><<<grid, K2_THREADS, 0, st>>>(S, P, O, n, a, lb);
+    return cached;
+}
+
+// chunk length for m patterns: all m bitmaps fit K2_BITMAP_BYTES
+int64_t k2_chunk_len(int m) {
+    const int64_t bits = (int64_t)K2_BITMAP_BYTES * 8 / m;
+    return std::max<int64_t>(K2_STEP, bits / K2_STEP * K2_STEP);
+}
+
+template <int U, bool VEC>
+int launch_u(tid_ctx *ctx, const int32_t *S, const int32_t *P, const int32_t *O, int64_t n, const MultiArgs &a) {
+    const unsigned gmax = resident_k2<U, VEC>();
+    int64_t chunk = k2_chunk_len(a.m);
+    // fewer, longer chunks are never needed: shrink the grid for small stores
+    int64_t chunks = std::min<int64_t>(gmax, ceil_div(n, chunk));
+    if (chunks < (int64_t)gmax) chunk = ceil_div(ceil_div(n, chunks), K2_STEP) * K2_STEP;
+    chunks = std::min<int64_t>(chunks, ceil_div(n, chunk));
+    const int n_seg = (int)ceil_div(n, chunks * chunk);
+    Lookback lb{};
+    TID_TRY(lookback_scratch(ctx, (unsigned)(chunks * n_seg * a.m), &lb));
+    lb.num_tiles = (unsigned)chunks;
+    k2_match_multi<U, VEC><<<(unsigned)chunks, K2_THREADS, (size_t)(chunk / 8) * a.m, ctx->stream>>>(
+        S, P, O, n, chunk, n_seg, a, lb);
     return launch_check("k2_match_multi");
 }
 
 template <int U>
-int launch_vec(bool vec, cudaStream_t st, const int32_t *S, const int32_t *P, const int32_t *O, int64_t n,
-               const MultiArgs &a, const Lookback &lb) {
-    return vec ? launch_u<U, true>(st, S, P, O, n, a, lb) : launch_u<U, false>(st, S, P, O, n, a, lb);
+int launch_vec(bool vec, tid_ctx *ctx, const int32_t *S, const int32_t *P, const int32_t *O, int64_t n,
+               const MultiArgs &a) {
+    return vec ? launch_u<U, true>(ctx, S, P, O, n, a) : launch_u<U, false>(ctx, S, P, O, n, a);
 }
 
 }  // namespace
@@ -270,26 +322,20 @@ extern "C" int tid_match_multi(tid_ctx *ctx, const tid_store *st, const tid_patt
         if (n == 0 || U == 0) {
             // nothing bound anywhere: every list is 0..n-1 (tid_match handles it)
             for (int j = 0; j < m && rc == TID_OK; ++j) {
-                Lookback none{};
+                LbScratch none{};
                 rc = launch_match(ctx->stream, st->s, st->p, st->o, n, st->aligned16, 0, 0, 0, outs[j]->col[0],
                                   outs[j]->cap, outs[j]->d_rows, outs[j]->slot.dev, none);
             }
         } else {
-            const unsigned tiles = (unsigned)ceil_div(n, K2_TILE);
-            Lookback lb{};
-            rc = lookback_scratch(ctx, tiles * (unsigned)m, &lb);
-            lb.num_tiles = tiles;
-            if (rc == TID_OK) {
-                const bool v = st->aligned16;
-                switch (U) {
-                    case 1: rc = launch_vec<1>(v, ctx->stream, st->s, st->p, st->o, n, a, lb); break;
-                    case 2: rc = launch_vec<2>(v, ctx->stream, st->s, st->p, st->o, n, a, lb); break;
-                    case 3: rc = launch_vec<3>(v, ctx->stream, st->s, st->p, st->o, n, a, lb); break;
-                    case 4: rc = launch_vec<4>(v, ctx->stream, st->s, st->p, st->o, n, a, lb); break;
-                    case 5: rc = launch_vec<5>(v, ctx->stream, st->s, st->p, st->o, n, a, lb); break;
-                    case 6: rc = launch_vec<6>(v, ctx->stream, st->s, st->p, st->o, n, a, lb); break;
-                    default: rc = launch_vec<7>(v, ctx->stream, st->s, st->p, st->o, n, a, lb); break;
-                }
+            const bool v = st->aligned16;
+            switch (U) {
+                case 1: rc = launch_vec<1>(v, ctx, st->s, st->p, st->o, n, a); break;
+                case 2: rc = launch_vec<2>(v, ctx, st->s, st->p, st->o, n, a); break;
+                case 3: rc = launch_vec<3>(v, ctx, st->s, st->p, st->o, n, a); break;
+                case 4: rc = launch_vec<4>(v, ctx, st->s, st->p, st->o, n, a); break;
+                case 5: rc = launch_vec<5>(v, ctx, st->s, st->p, st->o, n, a); break;
+                case 6: rc = launch_vec<6>(v, ctx, st->s, st->p, st->o, n, a); break;
+                default: rc = launch_vec<7>(v, ctx, st->s, st->p, st->o, n, a); break;
             }
         }
     }

@@ -49,6 +49,16 @@ struct Lookback {
     int *err;                    // device-visible error word (TID_ERR_*)
 };
 
+// Where look-back scratch lives: `cap` status words, a ticket counter, the
+// error word, and the host-side epoch counter advanced by every launch.
+struct LbScratch {
+    unsigned long long *status;
+    size_t cap;
+    unsigned int *ticket;
+    int *err;
+    unsigned int *epoch;
+};
+
 constexpr unsigned LB_FLAG_AGG = 1, LB_FLAG_PREFIX = 2, LB_FLAG_ABORT = 3;
 constexpr unsigned LB_SPIN_LIMIT = 1u << 21;  // polls before a wait gives up
 
@@ -120,8 +130,9 @@ struct DeviceGuard {
 };
 int dev_alloc(tid_ctx *ctx, void **p, size_t bytes);
 void dev_free(tid_ctx *ctx, void *p);
-int next_epoch(tid_ctx *ctx);
 int lookback_scratch(tid_ctx *ctx, unsigned int num_tiles, Lookback *lb);
+int ctx_scratch(tid_ctx *ctx, size_t words, LbScratch *sc);    // the context's scratch, >= words
+int make_lookback(const LbScratch &sc, unsigned int num_tiles, Lookback *lb);  // next epoch
 int set_alloc(tid_ctx *ctx, int k, const int8_t *vars, int64_t cap, tid_set **out);
 int set_ready(tid_set *set);      // record the producer event
 int check_ctx_error(tid_ctx *ctx); // reads and clears the kernel error word
@@ -131,8 +142,8 @@ int launch_check(const char *what);
 int launch_match(cudaStream_t stream, const int32_t *S, const int32_t *P, const int32_t *O,
                  int64_t n, bool aligned16, int32_t ks, int32_t kp, int32_t ko,
                  int32_t *out, int64_t cap, int64_t *d_rows, int64_t *h_rows_dev,
-                 const Lookback &lb);
-unsigned int match_tiles(int64_t n, int mask);  // mask: bit0 s, bit1 p, bit2 o bound
+                 const LbScratch &sc);
+unsigned int match_scratch_words();  // status words one K1 launch may need
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
