@@ -9,13 +9,16 @@
 //  * every CTA owns one contiguous chunk of the store (up to 512K triples; the
 //    grid is sized to what is resident, so chunks are ~n / (SMs x CTAs/SM));
 //  * phase 1 streams the chunk with 16-byte loads (past L1, 256-byte L2
-//    prefetch; the next step's loads are issued before the current step's
-//    ballots) and keeps a 1-bit-per-triple hit bitmap in shared memory plus a
-//    hit count -- nothing else waits in this phase;
+//    prefetch; the next step's loads are issued before the current step is
+//    recorded) and keeps a 1-bit-per-triple hit bitmap in shared memory, in
+//    triple order: eight lanes merge their 4-bit masks into one 32-bit word
+//    with three xor-shuffles and one of them stores it; plus a hit count --
+//    nothing else waits in this phase;
 //  * one decoupled look-back over the chunk counts (lookback.cuh, 256 chunks
 //    per L2 round trip) gives the chunk's output offset;
-//  * phase 2 expands the bitmap: each warp walks a contiguous run of 128-triple
-//    cells, ranks the hits with popc and writes ascending indices contiguously.
+//  * phase 2 expands the bitmap: each warp takes a contiguous run of words,
+//    32 at a time (one per lane): popc, a warp prefix sum, then each lane
+//    writes the indices of its set bits -- work in proportion to the hits.
 // Only the columns a pattern binds are read (template on the bound mask).
 // Stores larger than (resident CTAs x 512K) triples take several launches;
 // each continues the output where the previous one ended.
@@ -32,8 +35,8 @@ namespace {
 
 constexpr int K1_THREADS = 256;
 constexpr int K1_WARPS = K1_THREADS / 32;
-constexpr int K1_G = 4;                                   // 16-byte loads per column per thread per step
-constexpr int K1_STEP = K1_THREADS * 4 * K1_G;            // 4096 triples per step
+constexpr int K1_G = 8;                                   // 16-byte loads per column per thread per step
+constexpr int K1_STEP = K1_THREADS * 4 * K1_G;            // 8192 triples per step
 constexpr int K1_BITMAP_BYTES = 64 * 1024;                // shared-memory hit bitmap per CTA
 constexpr int64_t K1_CHUNK_MAX = (int64_t)K1_BITMAP_BYTES * 8;  // 524288 triples
 
@@ -74,13 +77,17 @@ k1_match(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int
          int64_t n, int64_t seg_begin, int64_t seg_end, int64_t chunk_len, int first_seg,
          int32_t ks, int32_t kp, int32_t ko, int32_t *__restrict__ out, int64_t cap,
          int64_t *__restrict__ d_rows, int64_t *__restrict__ h_rows, Lookback lb) {
-    extern __shared__ uint32_t s_bits[];  // 4 words per 128-triple cell
+    // Linear hit bitmap: bit b of word W is triple c0 + 32 W + b.  A step covers
+    // 8192 triples = 256 words; thread (warp w, lane 8k+i) loads, in load group
+    // g, triples c0 + st*8192 + g*1024 + w*128 + 32k + 4i + (0..3), so the eight
+    // lanes 8k..8k+7 together hold word ((st*8 + g)*8 + w)*4 + k.
+    static_assert(K1_G == 8 && K1_STEP == 8192, "bitmap layout assumes 8 load groups per step");
+    extern __shared__ uint32_t s_bits[];
     __shared__ unsigned s_tile;
     __shared__ unsigned s_wtot[K1_WARPS];
     __shared__ long long s_base, s_prefix;
 
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     if (threadIdx.x == 0) {
         s_tile = lb_ticket(lb);
         s_base = first_seg ? 0 : *d_rows;  // hits of the earlier segments
@@ -95,15 +102,26 @@ k1_match(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int
     // ---- phase 1: stream the chunk into the shared-memory bitmap
     int4 vs[K1_G], vp[K1_G], vo[K1_G];
     auto issue = [&](int64_t base) {
+        const int64_t t0 = base + threadIdx.x * 4;
+        if (VEC && base + K1_STEP <= n) {  // whole step in bounds: no per-load checks
 #pragma unroll
-        for (int g = 0; g < K1_G; ++g) {
-            const int64_t e0 = base + g * (K1_THREADS * 4) + threadIdx.x * 4;
-            if (MASK & 1) vs[g] = load4<VEC>(S, e0, n);
-            if (MASK & 2) vp[g] = load4<VEC>(P, e0, n);
-            if (MASK & 4) vo[g] = load4<VEC>(O, e0, n);
+            for (int g = 0; g < K1_G; ++g) {
+                if (MASK & 1) vs[g] = ld_stream_v4(S + t0 + g * (K1_THREADS * 4));
+                if (MASK & 2) vp[g] = ld_stream_v4(P + t0 + g * (K1_THREADS * 4));
+                if (MASK & 4) vo[g] = ld_stream_v4(O + t0 + g * (K1_THREADS * 4));
+            }
+        } else {
+#pragma unroll
+            for (int g = 0; g < K1_G; ++g) {
+                const int64_t e0 = t0 + g * (K1_THREADS * 4);
+                if (MASK & 1) vs[g] = load4<VEC>(S, e0, n);
+                if (MASK & 2) vp[g] = load4<VEC>(P, e0, n);
+                if (MASK & 4) vo[g] = load4<VEC>(O, e0, n);
+            }
         }
     };
-    unsigned cnt = 0;  // this warp's hits (same value in every lane)
+    const unsigned sub = lane & 7u;  // position of this lane's 4 triples in its word
+    unsigned cnt = 0;                 // hits recorded by this lane
     issue(c0);
     for (int st = 0; st < steps; ++st) {
         const int64_t base = c0 + (int64_t)st * K1_STEP;
@@ -114,22 +132,31 @@ k1_match(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int
             if (MASK & 1) mm &= eq4(vs[g], ks);
             if (MASK & 2) mm &= eq4(vp[g], kp);
             if (MASK & 4) mm &= eq4(vo[g], ko);
-            const int64_t left = c1 - (base + g * (K1_THREADS * 4) + threadIdx.x * 4);
-            if (left < 4) mm &= left <= 0 ? 0u : ((1u << left) - 1u);
             m[g] = mm;
         }
+        if (base + K1_STEP > c1) {  // ragged last step of the chunk
+#pragma unroll
+            for (int g = 0; g < K1_G; ++g) {
+                const int64_t left = c1 - (base + g * (K1_THREADS * 4) + threadIdx.x * 4);
+                m[g] &= left <= 0 ? 0u : (left >= 4 ? 0xFu : ((1u << left) - 1u));
+            }
+        }
         if (st + 1 < steps) issue(base + K1_STEP);
+        uint32_t *row = s_bits + (size_t)st * (K1_THREADS);
 #pragma unroll
         for (int g = 0; g < K1_G; ++g) {
-            const int cell = (st * K1_G + g) * K1_WARPS + warp;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const unsigned word = __ballot_sync(0xffffffffu, (m[g] >> e) & 1u);
-                if (lane == (unsigned)e) s_bits[cell * 4 + e] = word;
-                cnt += __popc(word);
+            unsigned v = m[g] << (4 * sub);
+            v |= __shfl_xor_sync(0xffffffffu, v, 1);
+            v |= __shfl_xor_sync(0xffffffffu, v, 2);
+            v |= __shfl_xor_sync(0xffffffffu, v, 4);
+            if (sub == (unsigned)g) {
+                row[(g * K1_WARPS + warp) * 4 + (lane >> 3)] = v;
+                cnt += __popc(v);
             }
         }
     }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
     if (lane == 0) s_wtot[warp] = cnt;
     __syncthreads();
 
@@ -150,14 +177,12 @@ k1_match(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int
     __syncthreads();
     if (s_prefix < 0) return;
 
-    // ---- phase 2: expand the bitmap; warp w owns cells [q0, q1)
-    const int ncells = steps * K1_G * K1_WARPS;
-    const int per = (ncells + K1_WARPS - 1) / K1_WARPS;
-    const int q0 = min(ncells, (int)warp * per), q1 = min(ncells, q0 + per);
+    // ---- phase 2: expand the bitmap; warp w owns words [w0, w1), 32 at a time
+    const int nwords = steps * K1_THREADS;
+    const int per = (nwords / 32 + K1_WARPS - 1) / K1_WARPS * 32;
+    const int w0 = min(nwords, (int)warp * per), w1 = min(nwords, w0 + per);
     unsigned wt = 0;
-    for (int q = q0 + (int)lane; q < q1; q += 32)
-        wt += __popc(s_bits[q * 4]) + __popc(s_bits[q * 4 + 1]) + __popc(s_bits[q * 4 + 2]) +
-              __popc(s_bits[q * 4 + 3]);
+    for (int i = w0 + (int)lane; i < w1; i += 32) wt += __popc(s_bits[i]);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) wt += __shfl_xor_sync(0xffffffffu, wt, d);
     __syncthreads();  // s_wtot is reused
@@ -165,21 +190,26 @@ k1_match(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int
     __syncthreads();
     long long run = s_base + s_prefix;
     for (unsigned w = 0; w < warp; ++w) run += s_wtot[w];
-    for (int q = q0; q < q1; ++q) {
-        const uint4 wd = *reinterpret_cast<const uint4 *>(s_bits + q * 4);
-        if ((wd.x | wd.y | wd.z | wd.w) == 0u) continue;
-        const unsigned nib = ((wd.x >> lane) & 1u) | (((wd.y >> lane) & 1u) << 1) |
-                             (((wd.z >> lane) & 1u) << 2) | (((wd.w >> lane) & 1u) << 3);
-        long long pos = run + __popc(wd.x & lt) + __popc(wd.y & lt) + __popc(wd.z & lt) + __popc(wd.w & lt);
-        const int64_t elem = c0 + (int64_t)q * 128 + lane * 4;
+    for (int i0 = w0; i0 < w1; i0 += 32) {
+        uint32_t word = s_bits[i0 + lane];  // w1 - w0 is a multiple of 32
+        const unsigned c = __popc(word);
+        unsigned x = c;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            if ((nib >> e) & 1u) {
-                if (pos < cap) out[pos] = (int32_t)(elem + e);
-                ++pos;
-            }
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+            if ((int)lane >= d) x += y;
         }
-        run += __popc(wd.x) + __popc(wd.y) + __popc(wd.z) + __popc(wd.w);
+        const unsigned batch = __shfl_sync(0xffffffffu, x, 31);
+        if (batch == 0) continue;
+        long long pos = run + (x - c);
+        const int64_t wbase = c0 + (int64_t)(i0 + (int)lane) * 32;
+        while (word) {
+            const int b = __ffs(word) - 1;
+            if (pos < cap) out[pos] = (int32_t)(wbase + b);
+            ++pos;
+            word &= word - 1;
+        }
+        run += batch;
     }
 }
 
