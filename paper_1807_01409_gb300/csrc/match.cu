@@ -205,7 +205,8 @@ k1_match(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int
         const int64_t wbase = c0 + (int64_t)(i0 + (int)lane) * 32;
         while (word) {
             const int b = __ffs(word) - 1;
-            if (pos < cap) out[pos] = (int32_t)(wbase + b);
+            // unsigned compare: also rejects a negative base left by a segment that gave up
+            if ((unsigned long long)pos < (unsigned long long)cap) out[pos] = (int32_t)(wbase + b);
             ++pos;
             word &= word - 1;
         }
