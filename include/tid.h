@@ -133,6 +133,36 @@ int tid_match(tid_ctx *ctx, const tid_store *st, tid_pattern pat, tid_set **out)
 int tid_match_multi(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, int m,
                     tid_set **outs);
 
+/* A variant of tid_match that allocates nothing, for callers that may not
+ * allocate device memory when they scan (for example a server that gave all
+ * free device memory to its own pool at start-up, or a latency-critical loop
+ * that cannot afford an allocation's implicit synchronisation).  The paper
+ * has no counterpart; it is the same scan as tid_match.
+ *
+ * The caller passes the store columns s/p/o (n int32 each, device memory),
+ * the output `out` (device memory, room for `cap` int32) and `count` (one
+ * int64 in device memory), and the CUDA stream to run on (NULL = the legacy
+ * default stream) of CUDA device `device`.  The call is stream-ordered and
+ * does not wait: when the work completes, *count holds the number of matches
+ * and out[0 .. min(count, cap)) the ascending matching positions (a count
+ * above cap means the list was cut at cap).  *count is set to -1 when the
+ * work starts and stays -1 if an in-kernel wait gave up.
+ *
+ * The scan's scratch (one status word per scan chunk, a ticket counter and an
+ * error word) is a fixed array in device memory, TID_NOALLOC_MAX_CHUNKS status
+ * words (32 KB), present on every GPU that loads the library until the
+ * process exits.  The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls whose GPU work overlaps race on it, so order them (one stream, or
+ * events).  Errors: TID_ERR_ARG (bad pointers, sizes or device), TID_ERR_ID
+ * (negative pattern value), TID_ERR_CAPACITY (a GPU that would run more than
+ * TID_NOALLOC_MAX_CHUNKS chunks per launch), TID_ERR_CUDA. */
+#define TID_NOALLOC_MAX_CHUNKS 4096
+int tid_match_noalloc(int device, void *cuda_stream, const int32_t *s, const int32_t *p,
+                      const int32_t *o, int64_t n, tid_pattern pat, int32_t *out, int64_t cap,
+                      int64_t *count);
+
 /* ------------------------------------------------------------------------ */
 /* operators on tuple sets -- Section 4                                      */
 /* ------------------------------------------------------------------------ */

@@ -103,6 +103,8 @@ def lib():
         "tid_project": (C.c_int, [_vp, _vp, C.POINTER(C.c_int8), C.c_int, C.POINTER(_vp)]),
         "tid_set_from_host": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, C.POINTER(C.c_int8), C.POINTER(_vp)]),
         "tid_exec": (C.c_int, [_vp, _vp, C.POINTER(tid_plan_node), C.c_int, C.POINTER(_vp)]),
+        "tid_match_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, C.c_int64, tid_pattern, _vp, C.c_int64,
+                                        _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -235,6 +237,15 @@ def _preds(preds):
         arr[i].var, arr[i].op = int(var), CMP[op] if isinstance(op, str) else int(op)
         arr[i].a, arr[i].b = int(a), int(b)
     return arr, len(preds)
+
+
+def tid_match_noalloc(device, stream, s, p, o, pattern, out, count, n=None, cap=None):
+    """tid_match into caller buffers, allocating nothing (torch CUDA tensors or raw
+    device addresses; stream as int or None)."""
+    n = int(s.shape[0]) if n is None else int(n)
+    cap = int(out.shape[0]) if cap is None else int(cap)
+    _check(lib().tid_match_noalloc(int(device), stream if stream else None, _ptr(s), _ptr(p), _ptr(o), n,
+                                   as_pattern(pattern), _ptr(out), cap, _ptr(count)), "tid_match_noalloc")
 
 
 def tid_match_multi(ctx, st, patterns):
