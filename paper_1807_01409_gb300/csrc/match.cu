@@ -6,8 +6,9 @@
 // hits are compacted on the device, in ascending order, reading the bound
 // columns once and writing each index once:
 //
-//  * every CTA owns one contiguous chunk of the store (up to 512K triples; the
-//    grid is sized to what is resident, so chunks are ~n / (SMs x CTAs/SM));
+//  * every CTA owns one contiguous chunk of the store (up to 384K or 768K
+//    triples; the grid is sized to what is resident, so chunks are
+//    ~n / (SMs x CTAs/SM));
 //  * phase 1 streams the chunk with 16-byte loads (past L1, 256-byte L2
 //    prefetch; the next step's loads are issued before the current step is
 //    recorded) and keeps a 1-bit-per-triple hit bitmap in shared memory, in
@@ -20,7 +21,7 @@
 //    32 at a time (one per lane): popc, a warp prefix sum, then each lane
 //    writes the indices of its set bits -- work in proportion to the hits.
 // Only the columns a pattern binds are read (template on the bound mask).
-// Stores larger than (resident CTAs x 512K) triples take several launches;
+// Stores larger than (resident CTAs x chunk) triples take several launches;
 // each continues the output where the previous one ended.
 //
 // Bytes per launch: 4 * (bound columns) * n read + 4 * hits written.
@@ -37,8 +38,14 @@ constexpr int K1_THREADS = 256;
 constexpr int K1_WARPS = K1_THREADS / 32;
 constexpr int K1_G = 8;                                   // 16-byte loads per column per thread per step
 constexpr int K1_STEP = K1_THREADS * 4 * K1_G;            // 8192 triples per step
-constexpr int K1_BITMAP_BYTES = 64 * 1024;                // shared-memory hit bitmap per CTA
-constexpr int64_t K1_CHUNK_MAX = (int64_t)K1_BITMAP_BYTES * 8;  // 524288 triples
+// Shared-memory hit bitmap per CTA: 48 KB (384K triples) when one column is
+// bound, so four CTAs fit an SM (registers allow four); 96 KB (768K triples)
+// for two or three columns, whose register use allows two CTAs per SM.  Either
+// way a 200M-triple store is one launch.
+template <int MASK>
+constexpr int k1_bitmap_bytes() {
+    return ((MASK & 1) + ((MASK >> 1) & 1) + ((MASK >> 2) & 1)) == 1 ? 48 * 1024 : 96 * 1024;
+}
 
 __device__ __forceinline__ int4 ld_stream_v4(const int32_t *p) {
     int4 v;
@@ -248,9 +255,9 @@ template <int MASK, bool VEC>
 unsigned resident_ctas() {
     static unsigned cached = 0;
     if (!cached) {
-        cudaFuncSetAttribute(k1_match<MASK, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, K1_BITMAP_BYTES);
+        cudaFuncSetAttribute(k1_match<MASK, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, k1_bitmap_bytes<MASK>());
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k1_match<MASK, VEC>, K1_THREADS, K1_BITMAP_BYTES) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k1_match<MASK, VEC>, K1_THREADS, k1_bitmap_bytes<MASK>()) !=
                 cudaSuccess || v <= 0)
             v = 1;
         cached = (unsigned)(v * sm_count());
@@ -263,7 +270,7 @@ int run_segments(cudaStream_t st, const int32_t *S, const int32_t *P, const int3
                  int32_t ks, int32_t kp, int32_t ko, int32_t *out, int64_t cap, int64_t *d_rows,
                  int64_t *h_rows, const LbScratch &sc) {
     const unsigned grid_max = resident_ctas<MASK, VEC>();
-    const int64_t seg_max = (int64_t)grid_max * K1_CHUNK_MAX;
+    const int64_t seg_max = (int64_t)grid_max * ((int64_t)k1_bitmap_bytes<MASK>() * 8);
     for (int64_t sb = 0; sb < n; sb += seg_max) {
         const int64_t len = std::min<int64_t>(n - sb, seg_max);
         int64_t chunks = std::min<int64_t>(grid_max, ceil_div(len, K1_STEP));
