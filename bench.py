@@ -43,6 +43,22 @@ def _env_rank():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (step times: the job ends with its slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Work of all ranks over the job's wall time (weak scaling: every rank does units_per_rank)."""
+    return units_per_rank * world / seconds
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -230,16 +246,12 @@ def run_ours(args, rank, world, local):
             step(ev[k])
         t_end.record(stream)
         barrier()
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end), world, "cuda")
     kernel_ms = [ev[k][j][0].elapsed_time(ev[k][j][1]) for k in range(args.steps) for j in range(nq)]
     total_kernel_ms = sum(kernel_ms)
     alg_bytes_step = sum(4 * b * store_np.n + 4 * h for b, h in zip(bound, hits))
     scanned_step = nq * store_np.n
-    value = world * scanned_step * args.steps / (ms / 1e3) / 1e9
+    value = whole_job_rate(scanned_step * args.steps, world, ms / 1e3) / 1e9
 
     peak, peak_kind = _peaks()
     achieved = alg_bytes_step * args.steps / (total_kernel_ms / 1e3) / 1e9
@@ -271,12 +283,8 @@ def run_ours(args, rank, world, local):
     for _ in range(e2e_steps):
         e2e_step()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * scanned_step * e2e_steps / e2e_s / 1e9
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e_value = whole_job_rate(scanned_step * e2e_steps, world, e2e_s) / 1e9
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
