@@ -187,6 +187,175 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# the other rows of the path, each through the C ABI at full size
+# ---------------------------------------------------------------------------
+
+def measure_rows(tb, ctx, store, st, stream, peak, with_oracle=True, reps=3):
+    """Multi-pattern scan, bind (+filter fused), filter, sort (project), join (both
+    algorithms), union and plan execution on the university store.  For each:
+    GPU time of the C-ABI call (CUDA events on the context stream, best of reps),
+    algorithmic bytes (the bytes the operation must move at least: inputs read once,
+    outputs written once, one read+write pass for a sort), achieved GB/s against
+    the measured peak, and the oracle's time on the same input (or a stated
+    bounded sample)."""
+    import torch
+    orc = None
+    if with_oracle:
+        from oracle import oracle as orc
+        orc.build()
+    n = st.n
+    lay = synth.uni_layout(st.meta["subjects"])
+    pid, cbase = lay["pred_ids"], lay["class_base"]
+    X, Y, Z, V = 0, 1, 2, 4
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    live = []
+
+    def timed(fn):
+        best, res = float("inf"), None
+        for _ in range(reps):
+            if res is not None:
+                for h in (res if isinstance(res, list) else [res]):
+                    tb.tid_set_free(h)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        live.extend(res if isinstance(res, list) else [res])
+        return best, res
+
+    def rows_of(h):
+        return tb.tid_set_rows(h)
+
+    def cpu(fn, scale=1.0):
+        if orc is None:
+            return None
+        t = time.perf_counter()
+        fn()
+        return (time.perf_counter() - t) * scale * 1e3
+
+    def entry(ms, alg_bytes, cpu_ms, **kw):
+        d = {"gpu_ms": round(ms, 4), "algorithmic_bytes": int(alg_bytes),
+             "achieved_GBps": round(alg_bytes / (ms / 1e3) / 1e9, 1),
+             "frac_of_measured_peak": round(alg_bytes / (ms / 1e3) / 1e9 / peak, 4)}
+        if cpu_ms is not None:
+            d["oracle_ms"] = round(cpu_ms, 1)
+            d["speedup_vs_oracle"] = round(cpu_ms / ms, 1)
+        d.update(kw)
+        return d
+
+    out = {}
+    type_c = synth.Pattern(0, int(pid[0]), int(cbase), var=(X, -1, -1))  # (?x type C), top class 0
+    lit = synth.Pattern(0, int(pid[1]), 0, var=(X, -1, V))                 # (?x p1 ?v), literal-valued
+    ent = synth.Pattern(0, int(pid[7]), 0, var=(X, -1, Y))                 # (?x p7 ?y), entity-valued
+
+    # a2: one pass for three patterns (union of bound columns: P, O)
+    pats = [type_c, lit, ent]
+    ms, hs = timed(lambda: tb.tid_match_multi(ctx, store, pats))
+    hits = [rows_of(h) for h in hs]
+    cpu_ms = cpu(lambda: orc.match_multi(st.s, st.p, st.o, [p.key() for p in pats]))
+    out["a2_match_multi"] = entry(ms, 4 * 2 * n + 4 * sum(hits), cpu_ms, patterns=3, hits=hits,
+                                  oracle_sample="full store")
+
+    # a3: bind + fused filter from the (?x p1 ?v) index list
+    idx = tb.tid_match(ctx, store, lit)
+    live.append(idx)
+    h = rows_of(idx)
+    lo_v, hi_v = synth.LIT_BASE + 10, synth.LIT_BASE + 60
+    ms, b = timed(lambda: tb.tid_bind(ctx, store, lit, idx, [(V, "range", lo_v, hi_v)]))
+    m = rows_of(b)
+    samp = min(h, 2_000_000)
+    idx_np = orc.match(st.s, st.p, st.o, lit.key())[:samp] if orc else None
+    cpu_ms = cpu(lambda: orc.filter(orc.bind(st.s, st.p, st.o, lit.key(), lit.var, idx_np), V, "range",
+                                    lo_v, hi_v), scale=h / samp) if orc else None
+    out["a3_bind_filter"] = entry(ms, 4 * h + 8 * h + 8 * m + 16 * m, cpu_ms, rows_in=h, rows_out=m,
+                                  oracle_sample=f"first {samp} indices, time scaled x{h / samp:.1f}")
+
+    # a4: filter on a bound set (x, v) of all (?x p1 ?v)
+    full = tb.tid_bind(ctx, store, lit, idx, [])
+    live.append(full)
+    nf = rows_of(full)
+    ms, f = timed(lambda: tb.tid_filter(ctx, full, [(V, "range", lo_v, hi_v)]))
+    mf = rows_of(f)
+    samp = min(nf, 4_000_000)
+    sample_set = orc.TupleSet((X, V), tb.tid_set_to_host(full)[:samp]) if orc else None
+    cpu_ms = cpu(lambda: orc.filter(sample_set, V, "range", lo_v, hi_v), scale=nf / samp) if orc else None
+    out["a4_filter"] = entry(ms, 8 * nf + 8 * mf, cpu_ms, rows_in=nf, rows_out=mf,
+                             oracle_sample=f"first {samp} rows, time scaled x{nf / samp:.1f}")
+
+    # a5/a8: sort = project (x, v) -> (v, x) with DISTINCT: a full canonical sort
+    ms, pr = timed(lambda: tb.tid_project(ctx, full, (V, X)))
+    mp = rows_of(pr)
+    cpu_ms = cpu(lambda: orc.project(sample_set, (V, X)), scale=nf / samp) if orc else None
+    out["a5_a8_sort_project"] = entry(ms, 8 * nf + 8 * mp + 16 * mp, cpu_ms, rows_in=nf, rows_out=mp,
+                                      oracle_sample=f"first {samp} rows, time scaled x{nf / samp:.1f}")
+
+    # a6: join (?x type C)(x) with (?x p7 ?y)(x, y) on x, both algorithms
+    it = tb.tid_match(ctx, store, type_c)
+    ie = tb.tid_match(ctx, store, ent)
+    live += [it, ie]
+    L = tb.tid_bind(ctx, store, type_c, it, [])
+    R = tb.tid_bind(ctx, store, ent, ie, [])
+    live += [L, R]
+    nl, nr = rows_of(L), rows_of(R)
+    Lh, Rh = (tb.tid_set_to_host(L), tb.tid_set_to_host(R)) if orc else (None, None)
+    cpu_join = cpu(lambda: orc.join(orc.TupleSet((X,), Lh), orc.TupleSet((X, Y), Rh), method="sortmerge"))
+    for algo in ("sort_merge", "hash"):
+        ms, j = timed(lambda: tb.tid_join(ctx, L, R, algo))
+        mj = rows_of(j)
+        cpu_ms = cpu_join
+        out[f"a6_join_{algo}"] = entry(ms, 4 * nl + 8 * nr + 8 * mj + 16 * mj, cpu_ms, rows_l=nl, rows_r=nr,
+                                       rows_out=mj, oracle_sample="full inputs (oracle sort-merge join)")
+
+    # a7: union of (x, v) and (x, y): schema (x, v, y), padded with 0
+    ms, u = timed(lambda: tb.tid_union(ctx, [full, R]))
+    mu = rows_of(u)
+    cpu_ms = None
+    if orc:
+        su = min(samp, nr)
+        a_s = orc.TupleSet((X, V), tb.tid_set_to_host(full)[:su])
+        b_s = orc.TupleSet((X, Y), Rh[:su])
+        cpu_ms = cpu(lambda: orc.union([a_s, b_s]), scale=(nf + nr) / (2 * su))
+    out["a7_union"] = entry(ms, 8 * nf + 8 * nr + 12 * mu + 24 * (nf + nr), cpu_ms, rows_in=nf + nr,
+                            rows_out=mu, oracle_sample="bounded sample of both inputs, time scaled")
+    for h_ in live:
+        tb.tid_set_free(h_)
+    live.clear()
+
+    # a9: the 48 plans (star, chain, union, filter) through tid_exec
+    plans = synth.university_plans(st)
+    lat = []
+    for name, plan in plans:  # warm-up
+        h_ = tb.tid_exec(ctx, store, plan)
+        rows_of(h_)
+        tb.tid_set_free(h_)
+    for r in range(reps):
+        for name, plan in plans:
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            h_ = tb.tid_exec(ctx, store, plan)
+            rows_of(h_)
+            lat.append((time.perf_counter() - t) * 1e3)
+            tb.tid_set_free(h_)
+    lat = np.array(lat)
+    cpu_ms = None
+    sample_names = ("filter5", "union3", "star11")
+    if orc:
+        t = time.perf_counter()
+        for name, plan in plans:
+            if name in sample_names:
+                orc.execute(st.s, st.p, st.o, plan)
+        cpu_ms = (time.perf_counter() - t) * 1e3 / len(sample_names)
+    out["a9_exec"] = {"plans": len(plans), "queries_per_s": round(len(lat) / (lat.sum() / 1e3), 1),
+                      "latency_ms_p50": round(float(np.percentile(lat, 50)), 3),
+                      "latency_ms_p99": round(float(np.percentile(lat, 99)), 3),
+                      "oracle_ms_per_plan": None if cpu_ms is None else round(cpu_ms, 1),
+                      "oracle_sample": f"plans {', '.join(sample_names)}, full store"}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -289,6 +458,10 @@ def run_ours(args, rank, world, local):
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(store_np, synth.university_queries(store_np))
+    rows = None
+    if not args.no_rows:
+        rows = measure_rows(tb, ctx, store, store_np, stream, _peaks()[0],
+                            with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     tb.tid_store_free(store)
     tb.tid_ctx_destroy(ctx)
@@ -315,6 +488,7 @@ def run_ours(args, rank, world, local):
             "gpu_launches": nq * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": base,
+            "rows": rows,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -328,6 +502,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the other rows of the path")
     ap.add_argument("--triples", type=int, default=N_TRIPLES,
                     help="store size (default: the full 200M workload; smaller only for profiling)")
     args = ap.parse_args()

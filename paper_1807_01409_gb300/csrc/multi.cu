@@ -6,12 +6,18 @@
 // second union example).  Here the marks become one ascending index list per
 // pattern, built in the same pass, with the structure of K1:
 //  * each CTA streams one contiguous chunk per segment, loading the union of
-//    the patterns' bound columns once, and keeps one shared-memory hit bitmap
-//    per pattern (64 KB in all, so chunks shrink as patterns are added);
-//  * every pattern has one look-back chain over (segment, chunk) in store
-//    order; warp w resolves the chains of patterns w and w + 8;
-//  * each warp expands a contiguous run of 128-triple cells per pattern and
-//    writes ascending indices contiguously.
+//    the patterns' bound columns once per step and testing every pattern on
+//    the loaded values (latency is hidden by resident warps rather than by
+//    holding a second step in registers, whose pattern loop is long); each pattern keeps a triple-ordered 1-bit-per-triple
+//    bitmap in shared memory (8 lanes merge 4-bit masks with three
+//    xor-shuffles), 48 KB in all when one column is loaded, 96 KB otherwise, so
+//    chunks shrink as patterns are added;
+//  * pattern j's chunk count is a popc over its bitmap; it has one look-back
+//    chain over (segment, chunk) in store order; warp w resolves the chains of
+//    patterns w and w + 8;
+//  * per pattern, each warp expands a contiguous run of bitmap words, 32 at a
+//    time: popc, a warp prefix sum, and each lane writes the indices of its set
+//    bits.
 // A launch walks all segments of the store (segment = resident CTAs x chunk).
 // Bytes per launch: 4 * |union of bound columns| * n read + 4 * sum of hits written.
 
@@ -25,9 +31,20 @@ namespace {
 
 constexpr int K2_THREADS = 256;
 constexpr int K2_WARPS = K2_THREADS / 32;
-constexpr int K2_G = 4;                          // 16-byte loads per column per thread per step
-constexpr int K2_STEP = K2_THREADS * 4 * K2_G;   // 4096 triples
-constexpr int K2_BITMAP_BYTES = 64 * 1024;       // all patterns' bitmaps per CTA
+constexpr int K2_G = 8;                          // 16-byte loads per column per thread per step
+constexpr int K2_STEP = K2_THREADS * 4 * K2_G;   // 8192 triples per step (256 bitmap words)
+
+// resident CTAs per SM the register budget is shaped for: loaded data is 32
+// registers per bound column
+template <int U>
+constexpr int k2_min_blocks() {
+    return ((U & 1) + ((U >> 1) & 1) + ((U >> 2) & 1)) == 1 ? 3 : (((U & 1) + ((U >> 1) & 1) + ((U >> 2) & 1)) == 2 ? 2 : 1);
+}
+
+template <int U>
+constexpr int k2_bitmap_bytes() {
+    return ((U & 1) + ((U >> 1) & 1) + ((U >> 2) & 1)) == 1 ? 48 * 1024 : 96 * 1024;
+}
 
 struct MultiArgs {
     int m;
@@ -71,16 +88,19 @@ __device__ __forceinline__ unsigned eq4w(int4 v, int32_t k) {
 }
 
 template <int U, bool VEC>
-__global__ void __launch_bounds__(K2_THREADS)
+__global__ void __launch_bounds__(K2_THREADS, k2_min_blocks<U>())
 k2_match_multi(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int32_t *__restrict__ O,
                int64_t n, int64_t chunk_len, int n_seg, MultiArgs args, Lookback lb) {
-    extern __shared__ uint32_t s_bits[];  // pattern j: words [j * wpp, (j+1) * wpp)
+    // pattern j's bitmap: words [j * wpp, (j+1) * wpp); bit b of word W is triple
+    // c0 + 32 W + b; step st, load group g, warp w, lanes 8k..8k+7 -> word
+    // st*256 + (g*8 + w)*4 + k (as in K1)
+    extern __shared__ uint32_t s_bits[];
     __shared__ unsigned s_tile;
-    __shared__ unsigned s_cnt[TID_MAX_MULTI][K2_WARPS];
+    __shared__ unsigned s_wsum[K2_WARPS];
     __shared__ long long s_prefix[TID_MAX_MULTI];
 
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
+    const unsigned sub = lane & 7u;
     const int m = args.m;
     const unsigned G = lb.num_tiles;  // chunks per segment (= grid)
     const int wpp = (int)(chunk_len / 32);
@@ -91,12 +111,22 @@ k2_match_multi(const int32_t *__restrict__ S, const int32_t *__restrict__ P, con
     bool dead = false;
     int4 vs[K2_G], vp[K2_G], vo[K2_G];
     auto issue = [&](int64_t base) {
+        const int64_t t0 = base + threadIdx.x * 4;
+        if (VEC && base + K2_STEP <= n) {
 #pragma unroll
-        for (int g = 0; g < K2_G; ++g) {
-            const int64_t e0 = base + g * (K2_THREADS * 4) + threadIdx.x * 4;
-            if (U & 1) vs[g] = load4<VEC>(S, e0, n);
-            if (U & 2) vp[g] = load4<VEC>(P, e0, n);
-            if (U & 4) vo[g] = load4<VEC>(O, e0, n);
+            for (int g = 0; g < K2_G; ++g) {
+                if (U & 1) vs[g] = ld_stream_v4(S + t0 + g * (K2_THREADS * 4));
+                if (U & 2) vp[g] = ld_stream_v4(P + t0 + g * (K2_THREADS * 4));
+                if (U & 4) vo[g] = ld_stream_v4(O + t0 + g * (K2_THREADS * 4));
+            }
+        } else {
+#pragma unroll
+            for (int g = 0; g < K2_G; ++g) {
+                const int64_t e0 = t0 + g * (K2_THREADS * 4);
+                if (U & 1) vs[g] = load4<VEC>(S, e0, n);
+                if (U & 2) vp[g] = load4<VEC>(P, e0, n);
+                if (U & 4) vo[g] = load4<VEC>(O, e0, n);
+            }
         }
     };
 
@@ -104,61 +134,48 @@ k2_match_multi(const int32_t *__restrict__ S, const int32_t *__restrict__ P, con
         const int64_t c0 = ((int64_t)sg * G + t) * chunk_len;
         const int64_t c1 = min(c0 + chunk_len, n);
         const int steps = (!dead && c1 > c0) ? (int)ceil_div(c1 - c0, K2_STEP) : 0;
-        unsigned cnt[TID_MAX_MULTI];
-#pragma unroll
-        for (int j = 0; j < TID_MAX_MULTI; ++j) cnt[j] = 0;
 
-        // ---- stream the chunk: one bitmap per pattern
+        // ---- stream the chunk: the loaded columns are tested against every pattern
         if (steps > 0) issue(c0);
         for (int st = 0; st < steps; ++st) {
             const int64_t base = c0 + (int64_t)st * K2_STEP;
-            unsigned valid = 0;
-#pragma unroll
-            for (int g = 0; g < K2_G; ++g) {
-                const int64_t left = c1 - (base + g * (K2_THREADS * 4) + threadIdx.x * 4);
-                const unsigned vm = left <= 0 ? 0u : (left >= 4 ? 0xFu : ((1u << left) - 1u));
-                valid |= vm << (4 * g);
-            }
-            uint16_t hm[TID_MAX_MULTI];
-#pragma unroll
-            for (int j = 0; j < TID_MAX_MULTI; ++j) {
-                unsigned bits = 0;
-                if (j < m) {
-#pragma unroll
-                    for (int g = 0; g < K2_G; ++g) {
-                        unsigned mm = 0xFu;
-                        if (U & 1) mm &= eq4w(vs[g], args.key[j][0]);
-                        if (U & 2) mm &= eq4w(vp[g], args.key[j][1]);
-                        if (U & 4) mm &= eq4w(vo[g], args.key[j][2]);
-                        bits |= mm << (4 * g);
-                    }
-                }
-                hm[j] = (uint16_t)(bits & valid);
-            }
-            if (st + 1 < steps) issue(base + K2_STEP);
-#pragma unroll
-            for (int j = 0; j < TID_MAX_MULTI; ++j) {
-                if (j >= m) break;
+            unsigned valid = 0xFFFFFFFFu;  // bit 4g+e: element of load group g is inside the chunk
+            if (base + K2_STEP > c1) {
+                valid = 0;
 #pragma unroll
                 for (int g = 0; g < K2_G; ++g) {
-                    const int cell = (st * K2_G + g) * K2_WARPS + warp;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const unsigned word = __ballot_sync(0xffffffffu, (hm[j] >> (4 * g + e)) & 1u);
-                        if (lane == (unsigned)e) s_bits[j * wpp + cell * 4 + e] = word;
-                        cnt[j] += __popc(word);
-                    }
+                    const int64_t left = c1 - (base + g * (K2_THREADS * 4) + threadIdx.x * 4);
+                    const unsigned vm = left <= 0 ? 0u : (left >= 4 ? 0xFu : ((1u << left) - 1u));
+                    valid |= vm << (4 * g);
                 }
             }
+            for (int j = 0; j < m; ++j) {
+                const int32_t ks = args.key[j][0], kp = args.key[j][1], ko = args.key[j][2];
+                uint32_t *row = s_bits + (size_t)j * wpp + (size_t)st * K2_THREADS;
+#pragma unroll
+                for (int g = 0; g < K2_G; ++g) {
+                    unsigned mm = (valid >> (4 * g)) & 0xFu;
+                    if (U & 1) mm &= eq4w(vs[g], ks);
+                    if (U & 2) mm &= eq4w(vp[g], kp);
+                    if (U & 4) mm &= eq4w(vo[g], ko);
+                    unsigned v = mm << (4 * sub);
+                    v |= __shfl_xor_sync(0xffffffffu, v, 1);
+                    v |= __shfl_xor_sync(0xffffffffu, v, 2);
+                    v |= __shfl_xor_sync(0xffffffffu, v, 4);
+                    if (sub == (unsigned)g) row[(g * K2_WARPS + warp) * 4 + (lane >> 3)] = v;
+                }
+            }
+            if (st + 1 < steps) issue(base + K2_STEP);  // registers are free once all patterns are tested
         }
-        if (lane == 0)
-            for (int j = 0; j < m; ++j) s_cnt[j][warp] = cnt[j];
         __syncthreads();
 
         // ---- chunk offsets: chain of pattern j over (segment, chunk)
+        const int nwords = steps * K2_THREADS;
         const unsigned idx = (unsigned)sg * G + t;
         for (int j = (int)warp; j < m; j += K2_WARPS) {
-            unsigned tot = lane < K2_WARPS ? s_cnt[j][lane] : 0u;
+            const uint32_t *b = s_bits + (size_t)j * wpp;
+            unsigned tot = 0;
+            for (int i = (int)lane; i < nwords; i += 32) tot += __popc(b[i]);
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, d);
             Lookback lj = lb;
@@ -178,54 +195,47 @@ k2_match_multi(const int32_t *__restrict__ S, const int32_t *__restrict__ P, con
         __syncthreads();
         for (int j = 0; j < m; ++j) dead = dead || s_prefix[j] < 0;
 
-        // ---- expand: warp w owns cells [q0, q1) of every pattern
+        // ---- expand: per pattern, warp w owns words [w0, w1), 32 at a time
         if (!dead && steps > 0) {
-            const int ncells = steps * K2_G * K2_WARPS;
-            const int per = (ncells + K2_WARPS - 1) / K2_WARPS;
-            const int q0 = min(ncells, (int)warp * per), q1 = min(ncells, q0 + per);
-            unsigned blk[TID_MAX_MULTI];
-#pragma unroll
-            for (int j = 0; j < TID_MAX_MULTI; ++j) {
-                unsigned wt = 0;
-                if (j < m) {
-                    const uint32_t *b = s_bits + j * wpp;
-                    for (int q = q0 + (int)lane; q < q1; q += 32)
-                        wt += __popc(b[q * 4]) + __popc(b[q * 4 + 1]) + __popc(b[q * 4 + 2]) + __popc(b[q * 4 + 3]);
-#pragma unroll
-                    for (int d = 16; d > 0; d >>= 1) wt += __shfl_xor_sync(0xffffffffu, wt, d);
-                }
-                blk[j] = wt;
-            }
-            __syncthreads();  // s_cnt is reused
-            if (lane == 0)
-                for (int j = 0; j < m; ++j) s_cnt[j][warp] = blk[j];
-            __syncthreads();
+            const int per = (nwords / 32 + K2_WARPS - 1) / K2_WARPS * 32;
+            const int w0 = min(nwords, (int)warp * per), w1 = min(nwords, w0 + per);
             for (int j = 0; j < m; ++j) {
+                const uint32_t *b = s_bits + (size_t)j * wpp;
+                unsigned wt = 0;
+                for (int i = w0 + (int)lane; i < w1; i += 32) wt += __popc(b[i]);
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) wt += __shfl_xor_sync(0xffffffffu, wt, d);
+                __syncthreads();  // s_wsum is reused
+                if (lane == 0) s_wsum[warp] = wt;
+                __syncthreads();
                 long long run = s_prefix[j];
-                for (unsigned w = 0; w < warp; ++w) run += s_cnt[j][w];
-                const uint32_t *b = s_bits + j * wpp;
+                for (unsigned w = 0; w < warp; ++w) run += s_wsum[w];
                 int32_t *out = args.out[j];
                 const int64_t cap = args.cap[j];
-                for (int q = q0; q < q1; ++q) {
-                    const uint4 wd = *reinterpret_cast<const uint4 *>(b + q * 4);
-                    if ((wd.x | wd.y | wd.z | wd.w) == 0u) continue;
-                    const unsigned nib = ((wd.x >> lane) & 1u) | (((wd.y >> lane) & 1u) << 1) |
-                                         (((wd.z >> lane) & 1u) << 2) | (((wd.w >> lane) & 1u) << 3);
-                    long long pos = run + __popc(wd.x & lt) + __popc(wd.y & lt) + __popc(wd.z & lt) +
-                                    __popc(wd.w & lt);
-                    const int64_t elem = c0 + (int64_t)q * 128 + lane * 4;
+                for (int i0 = w0; i0 < w1; i0 += 32) {
+                    uint32_t word = b[i0 + lane];
+                    const unsigned c = __popc(word);
+                    unsigned x = c;
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if ((nib >> e) & 1u) {
-                            if (pos < cap) out[pos] = (int32_t)(elem + e);
-                            ++pos;
-                        }
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+                        if ((int)lane >= d) x += y;
                     }
-                    run += __popc(wd.x) + __popc(wd.y) + __popc(wd.z) + __popc(wd.w);
+                    const unsigned batch = __shfl_sync(0xffffffffu, x, 31);
+                    if (batch == 0) continue;
+                    long long pos = run + (x - c);
+                    const int64_t wbase = c0 + (int64_t)(i0 + (int)lane) * 32;
+                    while (word) {
+                        const int bit = __ffs(word) - 1;
+                        if ((unsigned long long)pos < (unsigned long long)cap) out[pos] = (int32_t)(wbase + bit);
+                        ++pos;
+                        word &= word - 1;
+                    }
+                    run += batch;
                 }
             }
         }
-        __syncthreads();  // bitmaps and counts are rewritten by the next segment
+        __syncthreads();  // bitmaps are rewritten by the next segment
     }
 }
 
@@ -244,9 +254,9 @@ template <int U, bool VEC>
 unsigned resident_k2() {
     static unsigned cached = 0;
     if (!cached) {
-        cudaFuncSetAttribute(k2_match_multi<U, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, K2_BITMAP_BYTES);
+        cudaFuncSetAttribute(k2_match_multi<U, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, k2_bitmap_bytes<U>());
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k2_match_multi<U, VEC>, K2_THREADS, K2_BITMAP_BYTES) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k2_match_multi<U, VEC>, K2_THREADS, k2_bitmap_bytes<U>()) !=
                 cudaSuccess || v <= 0)
             v = 1;
         cached = (unsigned)(v * sm_count_k2());
@@ -254,16 +264,17 @@ unsigned resident_k2() {
     return cached;
 }
 
-// chunk length for m patterns: all m bitmaps fit K2_BITMAP_BYTES
+// chunk length for m patterns: all m bitmaps fit the instance's bitmap bytes
+template <int U>
 int64_t k2_chunk_len(int m) {
-    const int64_t bits = (int64_t)K2_BITMAP_BYTES * 8 / m;
+    const int64_t bits = (int64_t)k2_bitmap_bytes<U>() * 8 / m;
     return std::max<int64_t>(K2_STEP, bits / K2_STEP * K2_STEP);
 }
 
 template <int U, bool VEC>
 int launch_u(tid_ctx *ctx, const int32_t *S, const int32_t *P, const int32_t *O, int64_t n, const MultiArgs &a) {
     const unsigned gmax = resident_k2<U, VEC>();
-    int64_t chunk = k2_chunk_len(a.m);
+    int64_t chunk = k2_chunk_len<U>(a.m);
     // fewer, longer chunks are never needed: shrink the grid for small stores
     int64_t chunks = std::min<int64_t>(gmax, ceil_div(n, chunk));
     if (chunks < (int64_t)gmax) chunk = ceil_div(ceil_div(n, chunks), K2_STEP) * K2_STEP;
