@@ -93,6 +93,21 @@ struct UniqueRow {  // rows in perm order; keep the first of each run of equal r
     }
 };
 
+template <typename K>
+struct PackedUniqueRow {  // sorted packed keys; keep the first of each run of equal keys
+    const K *keys;
+    PackSpec ps;
+    int k;
+    __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
+        const K key = keys[r];
+        for (int c = 0; c < k; ++c) {
+            const uint32_t f = ps.mask[c] ? (uint32_t)((key >> ps.shift[c]) & ps.mask[c]) : 0u;
+            v[c] = (int32_t)((f + ps.min[c]) ^ 0x80000000u);
+        }
+        return r == 0 || keys[r - 1] != key;
+    }
+};
+
 template <class Row>
 __global__ void __launch_bounds__(CP_THREADS)
 k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__restrict__ d_rows,
@@ -296,6 +311,18 @@ int compact_unique(tid_ctx *ctx, const int32_t *const *cols, int k, const int32_
     r.perm = perm;
     OutCols oc{};
     for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
+    return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev);
+}
+
+int compact_unique_packed(tid_ctx *ctx, const void *keys, bool wide, int k, int64_t n, const PackSpec &ps,
+                          tid_set *out) {
+    OutCols oc{};
+    for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
+    if (wide) {
+        PackedUniqueRow<unsigned long long> r{(const unsigned long long *)keys, ps, k};
+        return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev);
+    }
+    PackedUniqueRow<uint32_t> r{(const uint32_t *)keys, ps, k};
     return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev);
 }
 

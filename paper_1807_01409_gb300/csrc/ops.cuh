@@ -18,6 +18,16 @@ struct OutCols {
     int32_t *col[TID_MAX_COLS];
 };
 
+// Rows of k int32 columns packed into one unsigned key: field c holds
+// order_key(col_c) - min[c] (order_key flips the sign bit, so unsigned order is
+// int32 order) in bits [shift[c], shift[c] + width); column 0 is the most
+// significant field, so key order is row order.
+struct PackSpec {
+    uint32_t min[TID_MAX_COLS];
+    uint32_t shift[TID_MAX_COLS];
+    unsigned long long mask[TID_MAX_COLS];
+};
+
 // exclusive scan of n uint32 (out may alias in); *total_dev receives the sum
 int scan_exclusive_u32(tid_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
                        unsigned long long *total_dev);
@@ -28,6 +38,9 @@ int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, cons
 int compact_filter(tid_ctx *ctx, const tid_set *in, int64_t n, const Pred *preds, int n_preds, tid_set *out);
 int compact_unique(tid_ctx *ctx, const int32_t *const *cols, int k, const int32_t *perm, int64_t n,
                    tid_set *out);
+// sorted packed keys (64-bit if wide, else 32-bit) -> distinct rows of k columns
+int compact_unique_packed(tid_ctx *ctx, const void *keys, bool wide, int k, int64_t n, const PackSpec &ps,
+                          tid_set *out);
 
 // sorting (sort.cu)
 // perm receives the stable permutation that orders rows 0..n-1 lexicographically

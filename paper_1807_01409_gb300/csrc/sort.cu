@@ -2,17 +2,21 @@
 //
 // The paper sorts every result vector before joining and merges the final
 // results to keep distinct values (Section 4.3); it used a library mergesort.
-// Here rows are ordered by sorting a permutation: for each key column from the
-// last to the first, the (key, row) pairs are radix sorted stably, so the final
-// permutation orders rows lexicographically.  Per column only the bits that
-// vary are sorted: keys are rebased to (x - min) and the number of 8-bit digit
-// passes is taken from (max - min).
+// When the columns' value ranges fit 64 bits together (the usual case: entity
+// IDs need ~23 bits), each row is packed into one 32- or 64-bit key -- column
+// 0 most significant, each field rebased to (x - min) and as wide as
+// (max - min) needs -- and the keys alone are radix sorted, then unpacked (and
+// adjacent duplicates dropped) in one streaming pass.  Otherwise a row
+// permutation is sorted: for each key column from the last to the first, the
+// (key, row) pairs are radix sorted stably, so the final permutation orders
+// rows lexicographically; again only the bits that vary are sorted.
 //
 // One digit pass = upsweep (per-tile 256-bin histogram, warp-aggregated) +
 // exclusive scan of the (digit, tile) counts (look-back scan) + downsweep
 // (stable in-tile rank by warp match_any, staged in shared memory so the
 // scatter writes runs of equal digits contiguously).
-// Bytes per pass: 4n (upsweep) + 8n read + 8n written (downsweep).
+// Bytes per pass: w n (upsweep) + w n read + w n written (downsweep), w = key
+// bytes (4 or 8; 4 + 4 with the permutation).
 
 #include <algorithm>
 
@@ -35,6 +39,7 @@ struct ColPtrs {
 struct MutColPtrs {
     int32_t *c[TID_MAX_COLS];
 };
+
 
 __device__ __forceinline__ uint32_t order_key(int32_t x) { return (uint32_t)x ^ 0x80000000u; }
 
@@ -81,8 +86,9 @@ __global__ void k_iota32(int32_t *__restrict__ out, int64_t n) {
         out[i] = (int32_t)i;
 }
 
+template <typename K>
 __global__ void __launch_bounds__(RS_THREADS)
-rs_upsweep(const uint32_t *__restrict__ keys, int64_t n, int shift, uint32_t *__restrict__ hist, uint32_t tiles) {
+rs_upsweep(const K *__restrict__ keys, int64_t n, int shift, uint32_t *__restrict__ hist, uint32_t tiles) {
     __shared__ uint32_t cnt[RS_BINS];
     cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -92,7 +98,7 @@ rs_upsweep(const uint32_t *__restrict__ keys, int64_t n, int shift, uint32_t *__
     for (int j = 0; j < RS_ITEMS; ++j) {
         const int64_t i = base + j * RS_THREADS + threadIdx.x;
         const bool valid = i < n;
-        const unsigned d = valid ? (keys[i] >> shift) & 0xFFu : 0x100u;
+        const unsigned d = valid ? (unsigned)(keys[i] >> shift) & 0xFFu : 0x100u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
     }
@@ -100,15 +106,19 @@ rs_upsweep(const uint32_t *__restrict__ keys, int64_t n, int shift, uint32_t *__
     hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// Stable scatter of one digit pass; keys (and, with HAS_VAL, a 32-bit value
+// per key) are staged in shared memory so runs of equal digits are written
+// contiguously.
+template <typename K, bool HAS_VAL>
 __global__ void __launch_bounds__(RS_THREADS)
-rs_downsweep(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+rs_downsweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__restrict__ kout,
              int32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ offs, uint32_t tiles) {
     __shared__ uint32_t s_wcnt[RS_WARPS][RS_BINS];
     __shared__ uint32_t s_tdig[RS_BINS];
     __shared__ uint32_t s_gbase[RS_BINS];
     __shared__ uint32_t s_wsum[RS_WARPS];
-    __shared__ uint32_t s_k[RS_TILE];
-    __shared__ int32_t s_v[RS_TILE];
+    __shared__ K s_k[RS_TILE];
+    __shared__ int32_t s_v[HAS_VAL ? RS_TILE : 1];
 
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -116,21 +126,22 @@ rs_downsweep(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin, 
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
     const int64_t wbase = base + (int64_t)warp * (RS_ITEMS * 32);
-    uint32_t k[RS_ITEMS], r[RS_ITEMS];
-    int32_t v[RS_ITEMS];
+    K k[RS_ITEMS];
+    uint32_t r[RS_ITEMS];
+    int32_t v[HAS_VAL ? RS_ITEMS : 1];
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
         const int64_t i = wbase + j * 32 + lane;
         const bool valid = i < n;
-        k[j] = valid ? kin[i] : 0u;
-        v[j] = valid ? vin[i] : 0;
+        k[j] = valid ? kin[i] : (K)0;
+        if (HAS_VAL) v[j] = valid ? vin[i] : 0;
     }
     // stable rank among this warp's rows with the same digit, in row order
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
         const int64_t i = wbase + j * 32 + lane;
         const bool valid = i < n;
-        const unsigned d = valid ? (k[j] >> shift) & 0xFFu : 0x100u;
+        const unsigned d = valid ? (unsigned)(k[j] >> shift) & 0xFFu : 0x100u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t b = 0;
         if (valid) b = s_wcnt[warp][d];
@@ -176,20 +187,44 @@ rs_downsweep(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin, 
     for (int j = 0; j < RS_ITEMS; ++j) {
         const int64_t i = wbase + j * 32 + lane;
         if (i < n) {
-            const unsigned d = (k[j] >> shift) & 0xFFu;
+            const unsigned d = (unsigned)(k[j] >> shift) & 0xFFu;
             const uint32_t lp = s_tdig[d] + s_wcnt[warp][d] + r[j];
             s_k[lp] = k[j];
-            s_v[lp] = v[j];
+            if (HAS_VAL) s_v[lp] = v[j];
         }
     }
     __syncthreads();
     const int cnt = (int)(n - base < RS_TILE ? n - base : RS_TILE);
     for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
-        const uint32_t kk = s_k[i];
-        const unsigned d = (kk >> shift) & 0xFFu;
+        const K kk = s_k[i];
+        const unsigned d = (unsigned)(kk >> shift) & 0xFFu;
         const uint32_t gp = s_gbase[d] + ((uint32_t)i - s_tdig[d]);
         kout[gp] = kk;
-        vout[gp] = s_v[i];
+        if (HAS_VAL) vout[gp] = s_v[i];
+    }
+}
+
+// packed key of a row: column 0 most significant; field c holds
+// order_key(col_c) - min_c in bits [shift_c, shift_c + bits_c)
+template <typename K>
+__global__ void k_pack(ColPtrs cols, int k, int64_t n, PackSpec ps, K *__restrict__ keys) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        K key = 0;
+        for (int c = 0; c < k; ++c)  // a constant column (mask 0) has no field
+            if (ps.mask[c]) key |= (K)(order_key(cols.c[c][i]) - ps.min[c]) << ps.shift[c];
+        keys[i] = key;
+    }
+}
+
+// sorted packed keys -> k columns (no duplicate removal)
+template <typename K>
+__global__ void k_unpack(const K *__restrict__ keys, int k, int64_t n, PackSpec ps, MutColPtrs out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const K key = keys[i];
+        for (int c = 0; c < k; ++c) {
+            const uint32_t f = ps.mask[c] ? (uint32_t)((key >> ps.shift[c]) & ps.mask[c]) : 0u;
+            out.c[c][i] = (int32_t)((f + ps.min[c]) ^ 0x80000000u);
+        }
     }
 }
 
@@ -235,37 +270,42 @@ int set_rows_const(tid_set *set, int64_t n) {
     return launch_check("k_set_rows");
 }
 
-int sort_perm(tid_ctx *ctx, const int32_t *const *keys, int nk, int64_t n, int32_t *perm) {
-    if (n <= 0) return TID_OK;
-    if (nk < 0 || nk > TID_MAX_COLS) return fail(TID_ERR_ARG, "sort: %d key columns", nk);
+// Per-column [min, max] in sort order (one kernel, one synchronisation).
+static int column_ranges(tid_ctx *ctx, const int32_t *const *cols, int k, int64_t n, uint32_t *hmin, uint32_t *hmax) {
     cudaStream_t st = ctx->stream;
     Scratch s(ctx);
     uint32_t *mm = nullptr;
     TID_TRY(s.get(&mm, 2 * TID_MAX_COLS));
-    uint32_t hmin[TID_MAX_COLS], hmax[TID_MAX_COLS];
-    if (nk > 0) {
-        ColPtrs cp{};
-        for (int c = 0; c < nk; ++c) cp.c[c] = keys[c];
-        TID_TRY_CUDA(cudaMemsetAsync(mm, 0xFF, TID_MAX_COLS * 4, st), "memset");
-        TID_TRY_CUDA(cudaMemsetAsync(mm + TID_MAX_COLS, 0, TID_MAX_COLS * 4, st), "memset");
-        k_minmax<<<grid_for(n, 256), 256, 0, st>>>(cp, nk, n, mm, mm + TID_MAX_COLS);
-        TID_TRY(launch_check("k_minmax"));
-        uint32_t both[2 * TID_MAX_COLS];
-        TID_TRY_CUDA(cudaMemcpyAsync(both, mm, sizeof both, cudaMemcpyDeviceToHost, st), "copy min/max");
-        TID_TRY_CUDA(cudaStreamSynchronize(st), "sync min/max");
-        for (int c = 0; c < nk; ++c) {
-            hmin[c] = both[c];
-            hmax[c] = both[TID_MAX_COLS + c];
-        }
+    ColPtrs cp{};
+    for (int c = 0; c < k; ++c) cp.c[c] = cols[c];
+    TID_TRY_CUDA(cudaMemsetAsync(mm, 0xFF, TID_MAX_COLS * 4, st), "memset");
+    TID_TRY_CUDA(cudaMemsetAsync(mm + TID_MAX_COLS, 0, TID_MAX_COLS * 4, st), "memset");
+    k_minmax<<<grid_for(n, 256), 256, 0, st>>>(cp, k, n, mm, mm + TID_MAX_COLS);
+    TID_TRY(launch_check("k_minmax"));
+    uint32_t both[2 * TID_MAX_COLS];
+    TID_TRY_CUDA(cudaMemcpyAsync(both, mm, sizeof both, cudaMemcpyDeviceToHost, st), "copy min/max");
+    TID_TRY_CUDA(cudaStreamSynchronize(st), "sync min/max");
+    for (int c = 0; c < k; ++c) {
+        hmin[c] = both[c];
+        hmax[c] = both[TID_MAX_COLS + c];
     }
+    return TID_OK;
+}
+
+static int range_bits(uint32_t lo, uint32_t hi) { return hi == lo ? 0 : 32 - __builtin_clz(hi - lo); }
+
+// Stable LSD sort of a row permutation by key columns, given their ranges.
+static int sort_perm_ranges(tid_ctx *ctx, const int32_t *const *keys, int nk, int64_t n, const uint32_t *hmin,
+                            const uint32_t *hmax, int32_t *perm) {
+    cudaStream_t st = ctx->stream;
+    Scratch s(ctx);
     const unsigned tiles = (unsigned)ceil_div(n, RS_TILE);
     uint32_t *ka = nullptr, *kb = nullptr, *hist = nullptr;
     int32_t *pa = nullptr, *pb = nullptr;
     bool have_perm = false;  // pa holds the current permutation
     for (int c = nk - 1; c >= 0; --c) {
-        const uint32_t range = hmax[c] - hmin[c];
-        if (range == 0) continue;  // constant column: order unchanged
-        int bits = 32 - __builtin_clz(range);
+        const int bits = range_bits(hmin[c], hmax[c]);
+        if (bits == 0) continue;  // constant column: order unchanged
         const int passes = (bits + 7) / 8;
         if (!ka) {
             TID_TRY(s.get(&ka, n));
@@ -278,10 +318,10 @@ int sort_perm(tid_ctx *ctx, const int32_t *const *keys, int nk, int64_t n, int32
         TID_TRY(launch_check("k_prep"));
         for (int p = 0; p < passes; ++p) {
             const int shift = 8 * p;
-            rs_upsweep<<<tiles, RS_THREADS, 0, st>>>(ka, n, shift, hist, tiles);
+            rs_upsweep<uint32_t><<<tiles, RS_THREADS, 0, st>>>(ka, n, shift, hist, tiles);
             TID_TRY(launch_check("rs_upsweep"));
             TID_TRY(scan_exclusive_u32(ctx, hist, hist, (int64_t)RS_BINS * tiles, nullptr));
-            rs_downsweep<<<tiles, RS_THREADS, 0, st>>>(ka, pa, kb, pb, n, shift, hist, tiles);
+            rs_downsweep<uint32_t, true><<<tiles, RS_THREADS, 0, st>>>(ka, pa, kb, pb, n, shift, hist, tiles);
             TID_TRY(launch_check("rs_downsweep"));
             std::swap(ka, kb);
             std::swap(pa, pb);
@@ -295,6 +335,49 @@ int sort_perm(tid_ctx *ctx, const int32_t *const *keys, int nk, int64_t n, int32
         TID_TRY(launch_check("k_iota32"));
     }
     return TID_OK;
+}
+
+int sort_perm(tid_ctx *ctx, const int32_t *const *keys, int nk, int64_t n, int32_t *perm) {
+    if (n <= 0) return TID_OK;
+    if (nk < 0 || nk > TID_MAX_COLS) return fail(TID_ERR_ARG, "sort: %d key columns", nk);
+    uint32_t hmin[TID_MAX_COLS] = {0}, hmax[TID_MAX_COLS] = {0};
+    if (nk > 0) TID_TRY(column_ranges(ctx, keys, nk, n, hmin, hmax));
+    return sort_perm_ranges(ctx, keys, nk, n, hmin, hmax, perm);
+}
+
+// Canonical form by sorting packed keys (all fields fit K): pack, keys-only
+// digit passes over the occupied bits, then unpack (with distinct rows kept).
+template <typename K>
+static int canonical_packed(tid_ctx *ctx, const int32_t *const *cols, int k, int64_t n, bool dedupe,
+                            const PackSpec &ps, int total_bits, tid_set *set) {
+    cudaStream_t st = ctx->stream;
+    Scratch s(ctx);
+    const unsigned tiles = (unsigned)ceil_div(n, RS_TILE);
+    K *ka = nullptr, *kb = nullptr;
+    uint32_t *hist = nullptr;
+    TID_TRY(s.get(&ka, n));
+    TID_TRY(s.get(&kb, n));
+    TID_TRY(s.get(&hist, (size_t)RS_BINS * tiles));
+    ColPtrs cp{};
+    for (int c = 0; c < k; ++c) cp.c[c] = cols[c];
+    k_pack<K><<<grid_for(n, 256), 256, 0, st>>>(cp, k, n, ps, ka);
+    TID_TRY(launch_check("k_pack"));
+    const int passes = (total_bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        rs_upsweep<K><<<tiles, RS_THREADS, 0, st>>>(ka, n, shift, hist, tiles);
+        TID_TRY(launch_check("rs_upsweep"));
+        TID_TRY(scan_exclusive_u32(ctx, hist, hist, (int64_t)RS_BINS * tiles, nullptr));
+        rs_downsweep<K, false><<<tiles, RS_THREADS, 0, st>>>(ka, nullptr, kb, nullptr, n, shift, hist, tiles);
+        TID_TRY(launch_check("rs_downsweep"));
+        std::swap(ka, kb);
+    }
+    if (dedupe) return compact_unique_packed(ctx, ka, sizeof(K) == 8, k, n, ps, set);
+    MutColPtrs op{};
+    for (int c = 0; c < k; ++c) op.c[c] = set->col[c];
+    k_unpack<K><<<grid_for(n, 256), 256, 0, st>>>(ka, k, n, ps, op);
+    TID_TRY(launch_check("k_unpack"));
+    return set_rows_const(set, n);
 }
 
 int gather_cols(tid_ctx *ctx, const int32_t *const *in, int k, const int32_t *perm, int64_t n,
@@ -319,18 +402,37 @@ int canonicalize(tid_ctx *ctx, const int32_t *const *cols, int k, const int8_t *
     if (n == 0) {
         rc = set_rows_const(set, 0);
     } else {
-        int32_t *perm = nullptr;
-        rc = dev_alloc(ctx, (void **)&perm, (size_t)n * 4);
-        if (rc == TID_OK) rc = sort_perm(ctx, cols, k, n, perm);
+        uint32_t hmin[TID_MAX_COLS], hmax[TID_MAX_COLS];
+        rc = column_ranges(ctx, cols, k, n, hmin, hmax);
+        int total = 0;
+        PackSpec ps{};
         if (rc == TID_OK) {
-            if (dedupe) {
-                rc = compact_unique(ctx, cols, k, perm, n, set);
-            } else {
-                rc = gather_cols(ctx, cols, k, perm, n, set->col);
-                if (rc == TID_OK) rc = set_rows_const(set, n);
+            for (int c = k - 1; c >= 0; --c) {
+                const int bits = range_bits(hmin[c], hmax[c]);
+                ps.min[c] = hmin[c];
+                ps.shift[c] = (uint32_t)total;
+                ps.mask[c] = bits == 0 ? 0ull : ((1ull << bits) - 1ull);
+                total += bits;
             }
         }
-        if (perm) dev_free(ctx, perm);
+        if (rc == TID_OK && total <= 32) {
+            rc = canonical_packed<uint32_t>(ctx, cols, k, n, dedupe, ps, total, set);
+        } else if (rc == TID_OK && total <= 64) {
+            rc = canonical_packed<unsigned long long>(ctx, cols, k, n, dedupe, ps, total, set);
+        } else if (rc == TID_OK) {
+            int32_t *perm = nullptr;
+            rc = dev_alloc(ctx, (void **)&perm, (size_t)n * 4);
+            if (rc == TID_OK) rc = sort_perm_ranges(ctx, cols, k, n, hmin, hmax, perm);
+            if (rc == TID_OK) {
+                if (dedupe) {
+                    rc = compact_unique(ctx, cols, k, perm, n, set);
+                } else {
+                    rc = gather_cols(ctx, cols, k, perm, n, set->col);
+                    if (rc == TID_OK) rc = set_rows_const(set, n);
+                }
+            }
+            if (perm) dev_free(ctx, perm);
+        }
     }
     if (rc == TID_OK) rc = set_ready(set);
     if (rc != TID_OK) {
