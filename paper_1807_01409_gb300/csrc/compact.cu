@@ -42,10 +42,29 @@ __device__ __forceinline__ bool pred_ok(const Pred &p, int32_t x) {
 
 // ---- row sources -----------------------------------------------------------
 
+// Row sources write v[0..k) and say whether the row is kept.  Column loops run
+// to TID_MAX_COLS with a guard so v[] stays in registers.
+
+__device__ __forceinline__ bool preds_ok(const Pred *preds, int n_preds, const int32_t *v) {
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < MAX_PREDS; ++q) {
+        if (q < n_preds) {
+            int32_t x = v[0];
+#pragma unroll
+            for (int c = 1; c < TID_MAX_COLS; ++c)
+                if (preds[q].col == c) x = v[c];
+            ok = ok && pred_ok(preds[q], x);
+        }
+    }
+    return ok;
+}
+
 struct BindRow {  // triple index -> variable values
     const int32_t *S, *P, *O;
     const int32_t *idx;
     int k;
+    int need;                   // slots (bit 0 s, 1 p, 2 o) that carry a variable
     int8_t src[TID_MAX_COLS];   // slot (0,1,2) giving output column c
     int8_t eq_a[3], eq_b[3];    // pairs of slots that must be equal
     int n_eq;
@@ -53,15 +72,23 @@ struct BindRow {  // triple index -> variable values
     int n_preds;
     __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
         const int64_t t = idx[r];
-        int32_t term[3];
-        term[0] = S[t];
-        term[1] = P[t];
-        term[2] = O[t];
+        // only the variable slots are read: a bound slot holds the key itself
+        const int32_t t0 = (need & 1) ? S[t] : 0;
+        const int32_t t1 = (need & 2) ? P[t] : 0;
+        const int32_t t2 = (need & 4) ? O[t] : 0;
         bool ok = true;
-        for (int e = 0; e < n_eq; ++e) ok = ok && term[eq_a[e]] == term[eq_b[e]];
-        for (int c = 0; c < k; ++c) v[c] = term[src[c]];
-        for (int q = 0; q < n_preds; ++q) ok = ok && pred_ok(preds[q], v[preds[q].col]);
-        return ok;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            if (e < n_eq) {
+                const int32_t a = eq_a[e] == 0 ? t0 : (eq_a[e] == 1 ? t1 : t2);
+                const int32_t b = eq_b[e] == 0 ? t0 : (eq_b[e] == 1 ? t1 : t2);
+                ok = ok && a == b;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < k) v[c] = src[c] == 0 ? t0 : (src[c] == 1 ? t1 : t2);
+        return ok && preds_ok(preds, n_preds, v);
     }
 };
 
@@ -71,10 +98,10 @@ struct FilterRow {
     Pred preds[MAX_PREDS];
     int n_preds;
     __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
-        for (int c = 0; c < k; ++c) v[c] = col[c][r];
-        bool ok = true;
-        for (int q = 0; q < n_preds; ++q) ok = ok && pred_ok(preds[q], v[preds[q].col]);
-        return ok;
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < k) v[c] = col[c][r];
+        return preds_ok(preds, n_preds, v);
     }
 };
 
@@ -84,11 +111,15 @@ struct UniqueRow {  // rows in perm order; keep the first of each run of equal r
     int k;
     __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
         const int64_t a = perm ? perm[r] : r;
-        for (int c = 0; c < k; ++c) v[c] = col[c][a];
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < k) v[c] = col[c][a];
         if (r == 0) return true;
         const int64_t b = perm ? perm[r - 1] : r - 1;
         bool same = true;
-        for (int c = 0; c < k; ++c) same = same && col[c][b] == v[c];
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < k) same = same && col[c][b] == v[c];
         return !same;
     }
 };
@@ -100,9 +131,12 @@ struct PackedUniqueRow {  // sorted packed keys; keep the first of each run of e
     int k;
     __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
         const K key = keys[r];
-        for (int c = 0; c < k; ++c) {
-            const uint32_t f = ps.mask[c] ? (uint32_t)((key >> ps.shift[c]) & ps.mask[c]) : 0u;
-            v[c] = (int32_t)((f + ps.min[c]) ^ 0x80000000u);
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c) {
+            if (c < k) {
+                const uint32_t f = ps.mask[c] ? (uint32_t)((key >> ps.shift[c]) & ps.mask[c]) : 0u;
+                v[c] = (int32_t)((f + ps.min[c]) ^ 0x80000000u);
+            }
         }
         return r == 0 || keys[r - 1] != key;
     }
@@ -111,7 +145,7 @@ struct PackedUniqueRow {  // sorted packed keys; keep the first of each run of e
 template <class Row>
 __global__ void __launch_bounds__(CP_THREADS)
 k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__restrict__ d_rows,
-          int64_t *__restrict__ h_rows, Lookback lb) {
+          int64_t *__restrict__ h_rows, Lookback lb, uint32_t *__restrict__ mm) {
     __shared__ unsigned s_tile;
     __shared__ unsigned s_off[CP_ITEMS * CP_WARPS];
     __shared__ long long s_prefix;
@@ -160,6 +194,12 @@ k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__re
     __syncthreads();
     const long long prefix = s_prefix;
     if (prefix < 0) return;
+    uint32_t lo[TID_MAX_COLS], hi[TID_MAX_COLS];
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        lo[c] = 0xFFFFFFFFu;
+        hi[c] = 0u;
+    }
 #pragma unroll
     for (int j = 0; j < CP_ITEMS; ++j) {
         if (!((keep >> j) & 1u)) continue;
@@ -167,14 +207,38 @@ k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__re
         int32_t v[TID_MAX_COLS];
         row.load(r, v);  // second read of a kept row (cached in L1/L2)
         const long long pos = prefix + s_off[j * CP_WARPS + warp] + wpre[j];
-        if (pos < cap)
-            for (int c = 0; c < k_out; ++c) out.col[c][pos] = v[c];
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c) {
+            if (c < k_out) {
+                if (pos < cap) out.col[c][pos] = v[c];
+                const uint32_t u = (uint32_t)v[c] ^ 0x80000000u;
+                lo[c] = min(lo[c], u);
+                hi[c] = max(hi[c], u);
+            }
+        }
+    }
+    if (mm) {  // column bounds of the kept rows
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c) {
+            if (c < k_out) {
+                uint32_t a = lo[c], b = hi[c];
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) {
+                    a = min(a, __shfl_xor_sync(0xffffffffu, a, d));
+                    b = max(b, __shfl_xor_sync(0xffffffffu, b, d));
+                }
+                if (lane == 0 && a <= b) {
+                    atomicMin(mm + c, a);
+                    atomicMax(mm + TID_MAX_COLS + c, b);
+                }
+            }
+        }
     }
 }
 
 template <class Row>
 int launch_compact(tid_ctx *ctx, const Row &row, int64_t n, int k_out, const OutCols &out, int64_t cap,
-                   int64_t *d_rows, int64_t *h_rows_dev) {
+                   int64_t *d_rows, int64_t *h_rows_dev, uint32_t *mm = nullptr) {
     if (n == 0) {
         TID_TRY_CUDA(cudaMemsetAsync(d_rows, 0, sizeof(int64_t), ctx->stream), "memset rows");
         TID_TRY_CUDA(cudaMemsetAsync(h_rows_dev, 0, sizeof(int64_t), ctx->stream), "memset rows");
@@ -183,7 +247,7 @@ int launch_compact(tid_ctx *ctx, const Row &row, int64_t n, int k_out, const Out
     const unsigned tiles = (unsigned)ceil_div(n, CP_TILE);
     Lookback lb{};
     TID_TRY(lookback_scratch(ctx, tiles, &lb));
-    k_compact<Row><<<tiles, CP_THREADS, 0, ctx->stream>>>(row, n, k_out, out, cap, d_rows, h_rows_dev, lb);
+    k_compact<Row><<<tiles, CP_THREADS, 0, ctx->stream>>>(row, n, k_out, out, cap, d_rows, h_rows_dev, lb, mm);
     return launch_check("k_compact");
 }
 
@@ -261,7 +325,7 @@ int scan_exclusive_u32(tid_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t 
 }
 
 int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, const int32_t *idx, int64_t n,
-                 const Pred *preds, int n_preds, tid_set *out) {
+                 const Pred *preds, int n_preds, tid_set *out, uint32_t *mm) {
     BindRow r{};
     r.S = st->s;
     r.P = st->p;
@@ -269,6 +333,7 @@ int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, cons
     r.idx = idx;
     r.k = out->k;
     const int8_t var[3] = {pat.var[0], pat.var[1], pat.var[2]};
+    r.need = (var[0] >= 0 ? 1 : 0) | (var[1] >= 0 ? 2 : 0) | (var[2] >= 0 ? 4 : 0);
     for (int c = 0; c < out->k; ++c) {
         r.src[c] = -1;
         for (int j = 0; j < 3; ++j)
@@ -289,7 +354,7 @@ int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, cons
     for (int q = 0; q < n_preds; ++q) r.preds[q] = preds[q];
     OutCols oc{};
     for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
-    return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev);
+    return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev, mm);
 }
 
 int compact_filter(tid_ctx *ctx, const tid_set *in, int64_t n, const Pred *preds, int n_preds, tid_set *out) {

@@ -435,7 +435,17 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
     }
     const int32_t *ocols[TID_MAX_COLS];
     for (int c = 0; c < kout; ++c) ocols[c] = oc.c[c];
-    return canonicalize(ctx, ocols, kout, ovars, (int64_t)total, false, out);
+    Bounds b{};  // output columns keep their input's bounds
+    for (int c = 0; c < L->k; ++c) {
+        b.lo[c] = L->lo[c];
+        b.hi[c] = L->hi[c];
+    }
+    for (int c = 0; c < nrest; ++c) {
+        b.lo[L->k + c] = R->lo[rrest[c]];
+        b.hi[L->k + c] = R->hi[rrest[c]];
+    }
+    return canonicalize(ctx, ocols, kout, ovars, (int64_t)total, false, (L->bounded && R->bounded) ? &b : nullptr,
+                        out);
 }
 
 }  // namespace tid

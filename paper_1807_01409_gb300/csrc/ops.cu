@@ -3,6 +3,8 @@
 // imported from host memory.
 #include <string.h>
 
+#include <algorithm>
+
 #include <vector>
 
 #include "ops.cuh"
@@ -86,16 +88,34 @@ int bind_set(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, const ti
     if (n == 0) return empty_set(ctx, k, vars, out);
     tid_set *tmp = nullptr;
     TID_TRY(set_alloc(ctx, k, vars, n, &tmp));
-    int rc = compact_bind(ctx, st, pat, idx->col[0], n, pr, n_preds, tmp);
+    uint32_t *mm = nullptr;  // column bounds of the extracted rows, for the sort
+    int rc = dev_alloc(ctx, (void **)&mm, 2 * TID_MAX_COLS * sizeof(uint32_t));
+    if (rc == TID_OK) {
+        cudaError_t e = cudaMemsetAsync(mm, 0xFF, TID_MAX_COLS * sizeof(uint32_t), ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(mm + TID_MAX_COLS, 0, TID_MAX_COLS * sizeof(uint32_t), ctx->stream);
+        if (e != cudaSuccess) rc = fail_cuda(e, "tid_bind");
+    }
+    if (rc == TID_OK) rc = compact_bind(ctx, st, pat, idx->col[0], n, pr, n_preds, tmp, mm);
+    uint32_t hb[2 * TID_MAX_COLS];
+    if (rc == TID_OK) {
+        cudaError_t e = cudaMemcpyAsync(hb, mm, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) rc = fail_cuda(e, "tid_bind bounds");
+    }
     if (rc == TID_OK) rc = set_ready(tmp);
     int64_t m = 0;
     if (rc == TID_OK) rc = set_rows_host(tmp, &m);
     if (rc == TID_OK) {
         const int32_t *cols[TID_MAX_COLS];
-        for (int c = 0; c < k; ++c) cols[c] = tmp->col[c];
+        Bounds b{};
+        for (int c = 0; c < k; ++c) {
+            cols[c] = tmp->col[c];
+            b.lo[c] = hb[c];
+            b.hi[c] = hb[TID_MAX_COLS + c];
+        }
         // distinct triples give distinct rows unless a "?" slot is anonymous
-        rc = canonicalize(ctx, cols, k, vars, m, anon, out);
+        rc = canonicalize(ctx, cols, k, vars, m, anon, &b, out);
     }
+    if (mm) dev_free(ctx, mm);
     tid_set_free(tmp);
     return rc;
 }
@@ -109,6 +129,13 @@ int filter_set(tid_ctx *ctx, const tid_set *in, const tid_pred *preds, int n_pre
     TID_TRY(set_alloc(ctx, in->k, in->vars, n, &o));
     int rc = compact_filter(ctx, in, n, pr, n_preds, o);
     if (rc == TID_OK) rc = set_ready(o);
+    if (rc == TID_OK && in->bounded) {  // a subset keeps its input's bounds
+        o->bounded = true;
+        for (int c = 0; c < in->k; ++c) {
+            o->lo[c] = in->lo[c];
+            o->hi[c] = in->hi[c];
+        }
+    }
     if (rc != TID_OK) {
         tid_set_free(o);
         return rc;
@@ -156,7 +183,28 @@ int union_sets(tid_ctx *ctx, const tid_set *const *in, int k, tid_set **out) {
         }
         at += rows[i];
     }
-    if (rc == TID_OK) rc = canonicalize(ctx, cols, nu, uv, total, true, out);
+    // bounds of the union: each input's bounds, or the padding value 0
+    Bounds b{};
+    bool known = true;
+    for (int u = 0; u < nu; ++u) {
+        b.lo[u] = 0xFFFFFFFFu;
+        b.hi[u] = 0u;
+    }
+    for (int i = 0; i < k && known; ++i) {
+        if (rows[i] == 0) continue;
+        if (!in[i]->bounded) {
+            known = false;
+            break;
+        }
+        for (int u = 0; u < nu; ++u) {
+            const int c = find_col(in[i], uv[u]);
+            const uint32_t lo = c >= 0 ? in[i]->lo[c] : 0x80000000u;
+            const uint32_t hi = c >= 0 ? in[i]->hi[c] : 0x80000000u;
+            b.lo[u] = std::min(b.lo[u], lo);
+            b.hi[u] = std::max(b.hi[u], hi);
+        }
+    }
+    if (rc == TID_OK) rc = canonicalize(ctx, cols, nu, uv, total, true, known && total > 0 ? &b : nullptr, out);
     dev_free(ctx, block);
     return rc;
 }
@@ -176,7 +224,13 @@ int project_set(tid_ctx *ctx, const tid_set *in, const int8_t *vars, int n_vars,
     // keeping all columns in order of a canonical input is the identity
     bool identity = n_vars == in->k;
     for (int i = 0; i < n_vars && identity; ++i) identity = in->vars[i] == vars[i];
-    return canonicalize(ctx, cols, n_vars, vars, n, !identity, out);
+    Bounds b{};
+    for (int i = 0; i < n_vars; ++i) {
+        const int c = find_col(in, vars[i]);
+        b.lo[i] = in->lo[c];
+        b.hi[i] = in->hi[c];
+    }
+    return canonicalize(ctx, cols, n_vars, vars, n, !identity, in->bounded ? &b : nullptr, out);
 }
 
 }  // namespace tid
@@ -264,7 +318,7 @@ extern "C" int tid_set_from_host(tid_ctx *ctx, const int32_t *buf, int64_t rows,
     if (rc == TID_OK) {
         const int32_t *cp[TID_MAX_COLS];
         for (int c = 0; c < cols; ++c) cp[c] = (const int32_t *)block + (size_t)c * rows;
-        rc = canonicalize(ctx, cp, cols, vars, rows, true, out);
+        rc = canonicalize(ctx, cp, cols, vars, rows, true, nullptr, out);
         if (rc == TID_OK) rc = set_rows_host(*out, &rows);  // colbuf must outlive the copy
     }
     dev_free(ctx, block);

@@ -28,13 +28,21 @@ struct PackSpec {
     unsigned long long mask[TID_MAX_COLS];
 };
 
+// Column value bounds in sort order (int32 ^ 0x80000000); any valid bounds
+// serve the packed sort, exact ones make its keys narrowest.
+struct Bounds {
+    uint32_t lo[TID_MAX_COLS], hi[TID_MAX_COLS];
+};
+
 // exclusive scan of n uint32 (out may alias in); *total_dev receives the sum
 int scan_exclusive_u32(tid_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
                        unsigned long long *total_dev);
 
 // single-pass compactions (compact.cu); `out` must have capacity >= n
+// bind; if mm is not null, mm[c] / mm[8 + c] receive (atomic min / max) the
+// sort-order bounds of output column c over the kept rows (caller presets them)
 int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, const int32_t *idx, int64_t n,
-                 const Pred *preds, int n_preds, tid_set *out);
+                 const Pred *preds, int n_preds, tid_set *out, uint32_t *mm);
 int compact_filter(tid_ctx *ctx, const tid_set *in, int64_t n, const Pred *preds, int n_preds, tid_set *out);
 int compact_unique(tid_ctx *ctx, const int32_t *const *cols, int k, const int32_t *perm, int64_t n,
                    tid_set *out);
@@ -49,9 +57,11 @@ int sort_perm(tid_ctx *ctx, const int32_t *const *keys, int nk, int64_t n, int32
 // out[c][i] = in[c][perm[i]] for c < k, i < n
 int gather_cols(tid_ctx *ctx, const int32_t *const *in, int k, const int32_t *perm, int64_t n,
                 int32_t *const *out);
-// canonical form (rows sorted in column order; duplicates dropped if dedupe)
+// canonical form (rows sorted in column order; duplicates dropped if dedupe);
+// bounds of the input columns if known (else they are computed); the output
+// set records the bounds used
 int canonicalize(tid_ctx *ctx, const int32_t *const *cols, int k, const int8_t *vars, int64_t n,
-                 bool dedupe, tid_set **out);
+                 bool dedupe, const Bounds *bounds, tid_set **out);
 
 // write a known row count into a set (device count and host mirror)
 int set_rows_const(tid_set *set, int64_t n);

@@ -394,7 +394,7 @@ int gather_cols(tid_ctx *ctx, const int32_t *const *in, int k, const int32_t *pe
 }
 
 int canonicalize(tid_ctx *ctx, const int32_t *const *cols, int k, const int8_t *vars, int64_t n, bool dedupe,
-                 tid_set **out) {
+                 const Bounds *bounds, tid_set **out) {
     *out = nullptr;
     tid_set *set = nullptr;
     TID_TRY(set_alloc(ctx, k, vars, n, &set));
@@ -403,7 +403,21 @@ int canonicalize(tid_ctx *ctx, const int32_t *const *cols, int k, const int8_t *
         rc = set_rows_const(set, 0);
     } else {
         uint32_t hmin[TID_MAX_COLS], hmax[TID_MAX_COLS];
-        rc = column_ranges(ctx, cols, k, n, hmin, hmax);
+        if (bounds) {
+            for (int c = 0; c < k; ++c) {
+                hmin[c] = bounds->lo[c];
+                hmax[c] = bounds->hi[c];
+            }
+        } else {
+            rc = column_ranges(ctx, cols, k, n, hmin, hmax);
+        }
+        if (rc == TID_OK) {
+            set->bounded = true;
+            for (int c = 0; c < k; ++c) {
+                set->lo[c] = hmin[c];
+                set->hi[c] = hmax[c];
+            }
+        }
         int total = 0;
         PackSpec ps{};
         if (rc == TID_OK) {

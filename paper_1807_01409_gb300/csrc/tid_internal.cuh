@@ -118,6 +118,10 @@ struct tid_set {
     cudaEvent_t ready = nullptr; // recorded after the producing work
     int64_t rows_known = -1;
     void *block = nullptr;       // allocation holding the columns and d_rows
+    // Valid bounds of each column's values in sort order (int32 ^ 0x80000000),
+    // when known: lo[c] <= every value of column c <= hi[c].
+    bool bounded = false;
+    uint32_t lo[TID_MAX_COLS] = {0}, hi[TID_MAX_COLS] = {0};
 };
 
 namespace tid {
