@@ -495,6 +495,27 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_rows_only(args, local):
+    """One pass of measure_rows on the university store (no oracle), for launch-list captures."""
+    import torch
+
+    from paper_1807_01409_gb300 import binding as tb
+    from paper_1807_01409_gb300 import build as tbuild
+    torch.cuda.set_device(local)
+    tbuild.build()
+    st = synth.university_store(args.triples)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = tb.tid_ctx_create(local, stream.cuda_stream)
+    cols = [torch.from_numpy(c).cuda() for c in (st.s, st.p, st.o)]
+    torch.cuda.synchronize()
+    store = tb.tid_load(ctx, *cols, copy=0)
+    rows = measure_rows(tb, ctx, store, st, stream, _peaks()[0], with_oracle=False, reps=1)
+    tb.tid_store_free(store)
+    tb.tid_ctx_destroy(ctx)
+    print(json.dumps({"rows": rows, "n_triples": st.n}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -503,12 +524,16 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the other rows of the path")
+    ap.add_argument("--rows-only", action="store_true",
+                    help="profiling aid: one pass of the other rows only (no oracle), printed as JSON")
     ap.add_argument("--triples", type=int, default=N_TRIPLES,
                     help="store size (default: the full 200M workload; smaller only for profiling)")
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.rows_only:
+        run_rows_only(args, local)
     else:
         run_ours(args, rank, world, local)
 
