@@ -133,6 +133,23 @@ int tid_match(tid_ctx *ctx, const tid_store *st, tid_pattern pat, tid_set **out)
 int tid_match_multi(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, int m,
                     tid_set **outs);
 
+/* Any number of patterns in two passes over the store per TID_BATCH_KEYS
+ * distinct patterns: the multi-key search of Section 4.1 and of the
+ * entailment steps of Section 5, grown to thousands of keys.  Every triple is
+ * looked up, once per bound-position mask present, in a perfect-hash table of
+ * the batch's keys held in shared memory, instead of being compared with
+ * every key.  outs[j] receives the ascending index list of pats[j], exactly
+ * as tid_match(pats[j]) would; equal patterns are scanned once and receive
+ * views of one list; a pattern with no bound position goes through tid_match.
+ * The union of the patterns' bound columns is read twice (a count pass sizes
+ * every list, one synchronisation, a write pass fills them in order); the
+ * lists of one sub-batch share one allocation, freed with the last of its
+ * sets.  q >= 0; on error every outs[j] is NULL.  Errors: TID_ERR_ID if a
+ * pattern value is negative.  Synchronises once per sub-batch. */
+#define TID_BATCH_KEYS 2048
+int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, int q,
+                    tid_set **outs);
+
 /* A variant of tid_match that allocates nothing, for callers that may not
  * allocate device memory when they scan (for example a server that gave all
  * free device memory to its own pool at start-up, or a latency-critical loop

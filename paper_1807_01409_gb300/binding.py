@@ -19,6 +19,7 @@ TID_OK, TID_ERR_ARG, TID_ERR_ID, TID_ERR_OOM, TID_ERR_CAPACITY, TID_ERR_TIMEOUT,
 TID_HOST, TID_DEVICE = 0, 1
 TID_MAX_COLS = 8
 TID_MAX_MULTI = 16
+TID_BATCH_KEYS = 2048
 ERR_NAMES = {0: "TID_OK", 1: "TID_ERR_ARG", 2: "TID_ERR_ID", 3: "TID_ERR_OOM",
              4: "TID_ERR_CAPACITY", 5: "TID_ERR_TIMEOUT", 6: "TID_ERR_CUDA"}
 
@@ -96,6 +97,7 @@ def lib():
         "tid_set_to_host": (C.c_int, [_vp, _vp, C.c_int64, i64p]),
         "tid_set_free": (C.c_int, [_vp]),
         "tid_match_multi": (C.c_int, [_vp, _vp, C.POINTER(tid_pattern), C.c_int, C.POINTER(_vp)]),
+        "tid_match_batch": (C.c_int, [_vp, _vp, C.POINTER(tid_pattern), C.c_int, C.POINTER(_vp)]),
         "tid_bind": (C.c_int, [_vp, _vp, tid_pattern, _vp, C.POINTER(tid_pred), C.c_int, C.POINTER(_vp)]),
         "tid_filter": (C.c_int, [_vp, _vp, C.POINTER(tid_pred), C.c_int, C.POINTER(_vp)]),
         "tid_join": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(_vp)]),
@@ -254,6 +256,36 @@ def tid_match_multi(ctx, st, patterns):
     outs = (_vp * len(pats))()
     _check(lib().tid_match_multi(ctx, st, arr, len(pats), outs), "tid_match_multi")
     return [_vp(outs[i]) for i in range(len(pats))]
+
+
+PATTERN_DTYPE = np.dtype([("s", "<i4"), ("p", "<i4"), ("o", "<i4"), ("var", "i1", (3,)), ("reserved", "i1")])
+
+
+def pattern_array(patterns):
+    """Patterns as a packed tid_pattern array (numpy): from an (q, 3) integer array
+    of keys (anonymous variables), or from a list of anything as_pattern takes."""
+    if isinstance(patterns, np.ndarray) and patterns.dtype == PATTERN_DTYPE:
+        return patterns
+    if isinstance(patterns, np.ndarray) and patterns.ndim == 2 and patterns.shape[1] == 3:
+        arr = np.zeros(patterns.shape[0], PATTERN_DTYPE)
+        arr["s"], arr["p"], arr["o"] = patterns[:, 0], patterns[:, 1], patterns[:, 2]
+        arr["var"] = -1
+        return arr
+    arr = np.zeros(len(patterns), PATTERN_DTYPE)
+    for i, x in enumerate(patterns):
+        t = as_pattern(x)
+        arr[i] = (t.s, t.p, t.o, tuple(t.var), 0)
+    return arr
+
+
+def tid_match_batch(ctx, st, patterns):
+    """Index lists of many patterns (see tid.h); `patterns` as pattern_array takes."""
+    arr = pattern_array(patterns)
+    q = int(arr.shape[0])
+    outs = (_vp * max(1, q))()
+    ptr = arr.ctypes.data_as(C.POINTER(tid_pattern)) if q else None
+    _check(lib().tid_match_batch(ctx, st, ptr, q, outs), "tid_match_batch")
+    return [_vp(outs[i]) for i in range(q)]
 
 
 def tid_bind(ctx, st, pattern, idx, preds=()):

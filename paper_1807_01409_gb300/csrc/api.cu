@@ -193,14 +193,35 @@ int set_alloc(tid_ctx *ctx, int k, const int8_t *vars, int64_t cap, tid_set **ou
         }
     }
     if (rc != TID_OK) {
-        tid_set_free(s);
+        set_free(s);
         return rc;
     }
     *out = s;
     return TID_OK;
 }
 
+int set_view(tid_ctx *ctx, SharedBlock *sb, int32_t *col, int64_t *d_rows, int64_t rows, tid_set **out) {
+    *out = nullptr;
+    tid_set *s = new (std::nothrow) tid_set();
+    if (!s) return fail(TID_ERR_OOM, "host allocation");
+    s->ctx = ctx;
+    s->k = 1;
+    s->vars[0] = -1;
+    s->cap = rows;
+    s->col[0] = col;
+    s->d_rows = d_rows;
+    s->rows_known = rows;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        s->shared = sb;
+        ++sb->refs;
+    }
+    *out = s;
+    return TID_OK;
+}
+
 int set_ready(tid_set *set) {
+    if (!set->ready) return TID_OK;  // a view: its producer is waited for through the stream
     TID_TRY_CUDA(cudaEventRecord(set->ready, set->ctx->stream), "event record");
     return TID_OK;
 }
@@ -451,12 +472,26 @@ extern "C" int tid_set_to_host(tid_set *set, int32_t *buf, int64_t cap_rows, int
     return check_ctx_error(ctx);
 }
 
-extern "C" int tid_set_free(tid_set *set) {
-    clear_error();
-    if (!set) return TID_OK;
+namespace tid {
+// frees a set without touching the error message (used on error paths too)
+void set_free(tid_set *set) {
+    if (!set) return;
     tid_ctx *ctx = set->ctx;
     DeviceGuard g(ctx->device);
     if (set->block) dev_free(ctx, set->block);
+    if (set->shared) {
+        SharedBlock *sb = set->shared;
+        bool last;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            last = --sb->refs == 0;
+        }
+        if (last) {
+            for (void *p : sb->ptr)
+                if (p) dev_free(ctx, p);
+            delete sb;
+        }
+    }
     if (set->slot.slab >= 0) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         if (set->ready) {
@@ -469,5 +504,11 @@ extern "C" int tid_set_free(tid_set *set) {
     }
     if (set->ready) cudaEventDestroy(set->ready);
     delete set;
+}
+}  // namespace tid
+
+extern "C" int tid_set_free(tid_set *set) {
+    clear_error();
+    tid::set_free(set);
     return TID_OK;
 }

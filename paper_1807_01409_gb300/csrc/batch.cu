@@ -1,0 +1,505 @@
+// Batched single-pattern search: thousands of patterns in two scans of the
+// store, each pattern's matches returned exactly as tid_match would (an
+// ascending index list).
+//
+// The paper searches several subqueries in one pass through its key array
+// (Section 4.1) and, for entailment, turns the distinct keys found by one search
+// into a multi-key search (Section 5).  For a large batch the per-triple test
+// against every key is replaced by lookups: for every bound-position mask
+// present in the batch, the triple's own values under that mask form the only
+// key of that mask it can answer, and one lookup in a table of the batch's
+// distinct (mask, key) pairs -- "key ids" -- finds it.  The table is a
+// hash-and-displace perfect hash built on the host (Belazzougui, Botelho and
+// Dietzfelbinger, "Hash, displace, and compress", ESA 2009): a key's bucket
+// gives a displacement, bucket and displacement give its slot, so a lookup is
+// two shared-memory reads and one comparison, with no probe loop.
+//
+//  * pass 1 (count): warp w owns a contiguous slice of the store and counts the
+//    hits of every key id in a warp-private shared-memory array (one add per
+//    group of lanes that hit the same key id in a 32-triple slot, grouped with
+//    match_any); the counts go to counts[w][kid];
+//  * a per-key exclusive scan over the warps gives every (warp, key id) its
+//    first output position, and each key id's total (one synchronisation sizes
+//    all outputs exactly; the lists share one allocation);
+//  * pass 2 (write): the same traversal; a hit's position is the warp's running
+//    cursor for its key id plus its rank among the lanes of the slot that hit the
+//    same key id, so every list is written in ascending order, without atomics
+//    or a sort.
+// Sub-batches of at most TID_BATCH_KEYS key ids keep table and counters in
+// shared memory.
+// Bytes per sub-batch: 2 x 4 * |union of bound columns| * n read + 4 * hits
+// written (+ 3 x 4 * key ids * warps for counts and bases).
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "ops.cuh"
+
+namespace tid {
+
+namespace {
+
+constexpr int KB_THREADS = 256;
+constexpr int KB_WARPS = KB_THREADS / 32;
+constexpr int KB_MAX_KIDS = TID_BATCH_KEYS;  // key ids per sub-batch
+constexpr int KB_UNROLL = 8;                 // 32-triple slots loaded per iteration
+
+struct __align__(16) Entry {  // one table slot: key values under its mask, mask and key id
+    int32_t s, p, o;
+    int32_t mask_kid;  // mask in bits [30:28], key id in [27:0]; -1 = empty
+};
+
+// Hash of (mask, key under the mask): a multiply-add chain over the bound
+// columns with odd multipliers drawn from the table's seed; the same on host and
+// device.  Bucket and slot take the high bits of products (range reduction by
+// multiply-high), which depend on every bit of the key.
+struct HashParams {
+    uint32_t base, k1, k2, k3, k4;
+};
+
+inline HashParams hash_params(uint32_t seed) {
+    HashParams hp;
+    uint64_t z = seed;
+    uint32_t v[5];
+    for (int i = 0; i < 5; ++i) {  // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014)
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t x = z;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        v[i] = (uint32_t)((x ^ (x >> 31)) >> 32);
+    }
+    hp.base = v[0];
+    hp.k1 = v[1] | 1u;
+    hp.k2 = v[2] | 1u;
+    hp.k3 = v[3] | 1u;
+    hp.k4 = v[4] | 1u;
+    return hp;
+}
+
+__host__ __device__ __forceinline__ uint32_t kb_hash(const HashParams &hp, int mask, uint32_t s, uint32_t p,
+                                                     uint32_t o) {
+    uint32_t x = hp.base ^ ((uint32_t)mask * 0x9E3779B1u);
+    if (mask & 1) x = (x + s) * hp.k1;
+    if (mask & 2) x = (x + p) * hp.k2;
+    if (mask & 4) x = (x + o) * hp.k3;
+    return x;
+}
+
+__host__ __device__ __forceinline__ uint32_t kb_range(uint32_t x, uint32_t n) {  // floor(x * n / 2^32)
+#ifdef __CUDA_ARCH__
+    return __umulhi(x, n);
+#else
+    return (uint32_t)(((uint64_t)x * n) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ uint32_t kb_bucket(uint32_t h, uint32_t nb) { return kb_range(h, nb); }
+
+__host__ __device__ __forceinline__ uint32_t kb_slot(const HashParams &hp, uint32_t h, uint32_t d, uint32_t ns) {
+    return kb_range((h ^ (d * 0x9E3779B9u)) * hp.k4, ns);
+}
+
+struct BatchArgs {
+    const int32_t *S, *P, *O;
+    int64_t n;
+    int64_t slice;           // triples per warp slice (multiple of 32 * KB_UNROLL)
+    int kids;                // key ids in this sub-batch
+    HashParams hp;           // hash multipliers
+    uint32_t nb, ns;         // buckets, slots
+    const Entry *table;      // ns slots
+    const uint16_t *disp;    // nb displacements
+    uint32_t *counts;        // [warp][kid]: pass 1 writes counts, the scan turns them into bases
+    int32_t *arena;          // the lists, list k at arena + off[k]
+    const int64_t *off;
+};
+
+__host__ __device__ __forceinline__ size_t kb_disp_bytes(uint32_t nb) { return (sizeof(uint16_t) * nb + 15) / 16 * 16; }
+
+size_t kb_smem_bytes(int kids, uint32_t ns, uint32_t nb) {
+    return sizeof(Entry) * ns + kb_disp_bytes(nb) + sizeof(uint32_t) * KB_WARPS * kids;
+}
+
+template <int U, bool WRITE>
+__global__ void __launch_bounds__(KB_THREADS) k_batch(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char kb_smem[];
+    Entry *s_tab = (Entry *)kb_smem;
+    uint16_t *s_disp = (uint16_t *)(s_tab + a.ns);
+    uint32_t *s_cnt = (uint32_t *)(kb_smem + sizeof(Entry) * a.ns + kb_disp_bytes(a.nb));
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (uint32_t i = threadIdx.x; i < a.ns; i += KB_THREADS) s_tab[i] = a.table[i];
+    for (uint32_t i = threadIdx.x; i < a.nb; i += KB_THREADS) s_disp[i] = a.disp[i];
+    const int64_t gw = (int64_t)blockIdx.x * KB_WARPS + warp;
+    uint32_t *cnt = s_cnt + warp * a.kids;
+    uint32_t *row = a.counts + gw * a.kids;
+    for (int k = lane; k < a.kids; k += 32) cnt[k] = WRITE ? row[k] : 0u;
+    __syncthreads();
+    const int64_t lo = gw * a.slice, hi = min(lo + a.slice, a.n);
+    for (int64_t b0 = lo; b0 < hi; b0 += 32 * KB_UNROLL) {
+        int32_t vs[KB_UNROLL], vp[KB_UNROLL], vo[KB_UNROLL];
+#pragma unroll
+        for (int u = 0; u < KB_UNROLL; ++u) {
+            const int64_t i = b0 + u * 32 + lane;
+            const bool in = i < hi;
+            vs[u] = (U & 1) && in ? __ldcs(a.S + i) : 0;
+            vp[u] = (U & 2) && in ? __ldcs(a.P + i) : 0;
+            vo[u] = (U & 4) && in ? __ldcs(a.O + i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < KB_UNROLL; ++u) {
+            const int64_t i = b0 + u * 32 + lane;
+            const bool in = i < hi;
+            // every mask's lookup first (independent chains), then the hits
+            int kid[7];
+#pragma unroll
+            for (int m = 1; m < 8; ++m) {
+                kid[m - 1] = -1;
+                if (m & ~U) continue;
+                const uint32_t h = kb_hash(a.hp, m, vs[u], vp[u], vo[u]);
+                const Entry e = s_tab[kb_slot(a.hp, h, s_disp[kb_bucket(h, a.nb)], a.ns)];
+                const bool hit = in && (e.mask_kid >> 28) == m && (!(m & 1) || e.s == vs[u]) &&
+                                 (!(m & 2) || e.p == vp[u]) && (!(m & 4) || e.o == vo[u]);
+                kid[m - 1] = hit ? (e.mask_kid & 0x0FFFFFFF) : -1;
+            }
+#pragma unroll
+            for (int m = 1; m < 8; ++m) {
+                if (m & ~U) continue;
+                const int k = kid[m - 1];
+                if (!__any_sync(0xffffffffu, k >= 0)) continue;
+                const unsigned peers = __match_any_sync(0xffffffffu, k);
+                if (k >= 0) {
+                    const uint32_t c = cnt[k];
+                    if (WRITE) a.arena[a.off[k] + c + __popc(peers & lt)] = (int32_t)i;
+                    __syncwarp(peers);
+                    if (lane == (unsigned)(__ffs(peers) - 1)) cnt[k] = c + __popc(peers);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncwarp();
+    if (!WRITE)
+        for (int k = lane; k < a.kids; k += 32) row[k] = cnt[k];
+}
+
+// counts[w][k] -> exclusive prefix over w for each k; rows[k] = total of k.
+// Block: 32 key ids (lanes) x 8 ranges of warps (the block's warps).
+__global__ void __launch_bounds__(256) k_batch_scan(uint32_t *counts, int64_t GW, int kids, int64_t *rows) {
+    __shared__ uint32_t s_sum[8][32];
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + lane;
+    const int64_t per = (GW + 7) / 8;
+    const int64_t b = min((int64_t)w * per, GW), e = min(b + per, GW);
+    uint32_t sum = 0;
+    if (k < kids)
+        for (int64_t g = b; g < e; ++g) sum += counts[g * kids + k];
+    s_sum[w][lane] = sum;
+    __syncthreads();
+    uint32_t run = 0;
+    for (unsigned v = 0; v < w; ++v) run += s_sum[v][lane];
+    if (k < kids) {
+        for (int64_t g = b; g < e; ++g) {
+            const uint32_t c = counts[g * kids + k];
+            counts[g * kids + k] = run;
+            run += c;
+        }
+        if (w == 7) rows[k] = run;
+    }
+}
+
+int sm_count_kb() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        cached = v;
+    }
+    return cached;
+}
+
+// resident CTAs of both passes with `smem` bytes of dynamic shared memory
+template <int U>
+int kb_grid(size_t smem, unsigned *grid) {
+    static bool opted = false;
+    if (!opted) {
+        int optin = 0, dev = 0;
+        cudaGetDevice(&dev);
+        TID_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
+        TID_TRY_CUDA(cudaFuncSetAttribute(k_batch<U, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                     "k_batch smem");
+        TID_TRY_CUDA(cudaFuncSetAttribute(k_batch<U, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                     "k_batch smem");
+        opted = true;
+    }
+    int v = 0, w = 0;
+    TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<U, true>, KB_THREADS, smem), "occupancy");
+    TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, k_batch<U, false>, KB_THREADS, smem), "occupancy");
+    if (std::min(v, w) < 1) return fail(TID_ERR_CAPACITY, "tid_match_batch: %zu bytes of shared memory per CTA", smem);
+    *grid = (unsigned)(std::min(v, w) * sm_count_kb());
+    return TID_OK;
+}
+
+template <int U>
+int run_pass(cudaStream_t st, bool write, unsigned grid, size_t smem, const BatchArgs &a) {
+    if (write) k_batch<U, true><<<grid, KB_THREADS, smem, st>>>(a);
+    else k_batch<U, false><<<grid, KB_THREADS, smem, st>>>(a);
+    return launch_check("k_batch");
+}
+
+#define KB_DISPATCH(U, call)                              \
+    switch (U) {                                          \
+        case 1: { constexpr int u_ = 1; return call; }    \
+        case 2: { constexpr int u_ = 2; return call; }    \
+        case 3: { constexpr int u_ = 3; return call; }    \
+        case 4: { constexpr int u_ = 4; return call; }    \
+        case 5: { constexpr int u_ = 5; return call; }    \
+        case 6: { constexpr int u_ = 6; return call; }    \
+        default: { constexpr int u_ = 7; return call; }   \
+    }
+
+int grid_of(int U, size_t smem, unsigned *grid) { KB_DISPATCH(U, kb_grid<u_>(smem, grid)) }
+
+int pass_of(int U, cudaStream_t st, bool write, unsigned grid, size_t smem, const BatchArgs &a) {
+    KB_DISPATCH(U, run_pass<u_>(st, write, grid, smem, a))
+}
+
+using Key = std::tuple<int, int32_t, int32_t, int32_t>;  // mask, s, p, o (0 where unbound)
+
+// Hash-and-displace table of `keys` (key id = position): buckets in decreasing
+// size each take the first displacement that puts all their keys on free
+// slots.  Returns false if some bucket finds none (the caller changes seed).
+bool build_table(const std::vector<Key> &keys, const HashParams &hp, uint32_t nb, uint32_t ns, std::vector<Entry> &tab,
+                 std::vector<uint16_t> &disp) {
+    const int K = (int)keys.size();
+    std::vector<uint32_t> h(K);
+    std::vector<std::vector<int>> bucket(nb);
+    for (int k = 0; k < K; ++k) {
+        int m;
+        int32_t s, p, o;
+        std::tie(m, s, p, o) = keys[k];
+        h[k] = kb_hash(hp, m, (uint32_t)s, (uint32_t)p, (uint32_t)o);
+        bucket[kb_bucket(h[k], nb)].push_back(k);
+    }
+    std::vector<uint32_t> order(nb);
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return bucket[x].size() > bucket[y].size(); });
+    tab.assign(ns, Entry{0, 0, 0, -1});
+    disp.assign(nb, 0);
+    std::vector<char> used(ns, 0);
+    std::vector<uint32_t> pos;
+    for (uint32_t b : order) {
+        const auto &ks = bucket[b];
+        if (ks.empty()) break;
+        bool placed = false;
+        for (uint32_t d = 0; d < 65536 && !placed; ++d) {
+            pos.clear();
+            bool ok = true;
+            for (int k : ks) {
+                const uint32_t sl = kb_slot(hp, h[k], d, ns);
+                if (used[sl] || std::find(pos.begin(), pos.end(), sl) != pos.end()) {
+                    ok = false;
+                    break;
+                }
+                pos.push_back(sl);
+            }
+            if (!ok) continue;
+            for (size_t j = 0; j < ks.size(); ++j) {
+                int m;
+                int32_t s, p, o;
+                std::tie(m, s, p, o) = keys[ks[j]];
+                used[pos[j]] = 1;
+                tab[pos[j]] = Entry{s, p, o, (m << 28) | ks[j]};
+            }
+            disp[b] = (uint16_t)d;
+            placed = true;
+        }
+        if (!placed) return false;
+    }
+    return true;
+}
+
+struct Scratch {
+    tid_ctx *ctx;
+    std::vector<void *> ptrs;
+    explicit Scratch(tid_ctx *c) : ctx(c) {}
+    ~Scratch() {
+        for (void *p : ptrs) dev_free(ctx, p);
+    }
+    template <class T>
+    int get(T **p, size_t count) {
+        void *q = nullptr;
+        TID_TRY(dev_alloc(ctx, &q, count * sizeof(T) + 16));
+        ptrs.push_back(q);
+        *p = (T *)q;
+        return TID_OK;
+    }
+};
+
+// One sub-batch: key ids 0..K-1; sets[k] receives key id k's list.
+int run_sub_batch(tid_ctx *ctx, const tid_store *st, const std::vector<Key> &keys, std::vector<tid_set *> &sets) {
+    cudaStream_t stream = ctx->stream;
+    const int kids = (int)keys.size();
+    int U = 0;
+    for (auto &k : keys) U |= std::get<0>(k);
+    const uint32_t nb = (uint32_t)std::max(1, (kids + 1) / 2);
+    uint32_t ns = (uint32_t)(kids + kids / 4 + 8);
+    std::vector<Entry> tab;
+    std::vector<uint16_t> disp;
+    HashParams hp{};
+    for (uint32_t attempt = 0;; ++attempt) {
+        hp = hash_params(0x243F6A88u + attempt);
+        if (build_table(keys, hp, nb, ns, tab, disp)) break;
+        if (attempt == 64) return fail(TID_ERR_CAPACITY, "tid_match_batch: no key table for %d keys", kids);
+        if (attempt % 8 == 7) ns += ns / 8;
+    }
+    const size_t smem = kb_smem_bytes(kids, ns, nb);
+    unsigned grid = 0;
+    TID_TRY(grid_of(U, smem, &grid));
+    const int64_t GW = (int64_t)grid * KB_WARPS;
+    const int64_t gran = 32 * KB_UNROLL;
+    const int64_t slice = std::max<int64_t>(gran, ceil_div(ceil_div(st->n, GW), gran) * gran);
+
+    SharedBlock *sb = new (std::nothrow) SharedBlock();
+    if (!sb) return fail(TID_ERR_OOM, "host allocation");
+    // the row counts live as long as the lists: both are the sets' shared block
+    int rc = dev_alloc(ctx, &sb->ptr[0], sizeof(int64_t) * kids);
+    if (rc != TID_OK) {
+        delete sb;
+        return rc;
+    }
+    int64_t *d_rows = (int64_t *)sb->ptr[0];
+    auto give_up = [&](int code) {
+        dev_free(ctx, sb->ptr[0]);
+        if (sb->ptr[1]) dev_free(ctx, sb->ptr[1]);
+        delete sb;
+        return code;
+    };
+    Scratch s(ctx);
+    Entry *d_tab = nullptr;
+    uint16_t *d_disp = nullptr;
+    uint32_t *counts = nullptr;
+    int64_t *d_off = nullptr;
+    if ((rc = s.get(&d_tab, ns)) != TID_OK || (rc = s.get(&d_disp, nb)) != TID_OK ||
+        (rc = s.get(&counts, (size_t)kids * GW)) != TID_OK || (rc = s.get(&d_off, kids)) != TID_OK)
+        return give_up(rc);
+    cudaError_t ce = cudaMemcpyAsync(d_tab, tab.data(), sizeof(Entry) * ns, cudaMemcpyHostToDevice, stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_disp, disp.data(), sizeof(uint16_t) * nb, cudaMemcpyHostToDevice, stream);
+    if (ce != cudaSuccess) return give_up(fail_cuda(ce, "batch table"));
+    BatchArgs a{};
+    a.S = st->s;
+    a.P = st->p;
+    a.O = st->o;
+    a.n = st->n;
+    a.slice = slice;
+    a.kids = kids;
+    a.hp = hp;
+    a.nb = nb;
+    a.ns = ns;
+    a.table = d_tab;
+    a.disp = d_disp;
+    a.counts = counts;
+    if ((rc = pass_of(U, stream, false, grid, smem, a)) != TID_OK) return give_up(rc);
+    k_batch_scan<<<(unsigned)ceil_div(kids, 32), 256, 0, stream>>>(counts, GW, kids, d_rows);
+    if ((rc = launch_check("k_batch_scan")) != TID_OK) return give_up(rc);
+    std::vector<int64_t> tot(kids), off(kids);
+    ce = cudaMemcpyAsync(tot.data(), d_rows, sizeof(int64_t) * kids, cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    if (ce != cudaSuccess) return give_up(fail_cuda(ce, "batch totals"));
+    if ((rc = check_ctx_error(ctx)) != TID_OK) return give_up(rc);
+    int64_t total = 0;
+    for (int k = 0; k < kids; ++k) {  // lists start on 64-byte boundaries
+        off[k] = total;
+        total += (tot[k] + 15) / 16 * 16;
+    }
+    if ((rc = dev_alloc(ctx, &sb->ptr[1], sizeof(int32_t) * std::max<int64_t>(total, 16))) != TID_OK)
+        return give_up(rc);
+    int32_t *arena = (int32_t *)sb->ptr[1];
+    ce = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * kids, cudaMemcpyHostToDevice, stream);
+    if (ce != cudaSuccess) return give_up(fail_cuda(ce, "batch offsets"));
+    a.arena = arena;
+    a.off = d_off;
+    if ((rc = pass_of(U, stream, true, grid, smem, a)) != TID_OK) return give_up(rc);
+    for (int k = 0; k < kids; ++k) {
+        rc = set_view(ctx, sb, arena + off[k], d_rows + k, tot[k], &sets[k]);
+        if (rc != TID_OK) {
+            if (k == 0) return give_up(rc);
+            for (int j = 0; j < k; ++j) {  // the last of these frees the shared block
+                set_free(sets[j]);
+                sets[j] = nullptr;
+            }
+            return rc;
+        }
+    }
+    return TID_OK;
+}
+
+}  // namespace
+}  // namespace tid
+
+using namespace tid;
+
+extern "C" int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, int q, tid_set **outs) {
+    clear_error();
+    if (!ctx || !st || (q > 0 && (!pats || !outs))) return fail(TID_ERR_ARG, "tid_match_batch: null argument");
+    if (q < 0) return fail(TID_ERR_ARG, "tid_match_batch: q = %d", q);
+    if (st->ctx != ctx) return fail(TID_ERR_ARG, "tid_match_batch: store belongs to another context");
+    for (int i = 0; i < q; ++i) outs[i] = nullptr;
+    for (int i = 0; i < q; ++i)
+        if (pats[i].s < 0 || pats[i].p < 0 || pats[i].o < 0)
+            return fail(TID_ERR_ID, "tid_match_batch: negative ID in pattern %d", i);
+    DeviceGuard g(ctx->device);
+    // distinct (mask, key) -> key id; (?,?,?) and an empty store go through tid_match
+    std::map<Key, int> id_of;
+    std::vector<Key> keys;
+    std::vector<int> kid_of(q, -1);
+    for (int i = 0; i < q; ++i) {
+        const int m = (pats[i].s != 0) | ((pats[i].p != 0) << 1) | ((pats[i].o != 0) << 2);
+        if (m == 0 || st->n == 0) continue;
+        const Key key = std::make_tuple(m, pats[i].s, pats[i].p, pats[i].o);
+        auto it = id_of.find(key);
+        if (it == id_of.end()) {
+            it = id_of.emplace(key, (int)keys.size()).first;
+            keys.push_back(key);
+        }
+        kid_of[i] = it->second;
+    }
+    int rc = TID_OK;
+    std::vector<tid_set *> by_kid(keys.size(), nullptr);
+    for (size_t b = 0; b < keys.size() && rc == TID_OK; b += KB_MAX_KIDS) {
+        const size_t e = std::min(keys.size(), b + (size_t)KB_MAX_KIDS);
+        std::vector<Key> sub(keys.begin() + b, keys.begin() + e);
+        std::vector<tid_set *> sets(sub.size(), nullptr);
+        rc = run_sub_batch(ctx, st, sub, sets);
+        for (size_t k = 0; k < sets.size(); ++k) by_kid[b + k] = sets[k];
+    }
+    // the first pattern of a key id takes its set, equal patterns get views of the same list
+    std::vector<bool> taken(keys.size(), false);
+    for (int i = 0; i < q && rc == TID_OK; ++i) {
+        const int k = kid_of[i];
+        if (k < 0) {
+            rc = tid_match(ctx, st, pats[i], &outs[i]);
+        } else if (!taken[k]) {
+            outs[i] = by_kid[k];
+            taken[k] = true;
+        } else {
+            const tid_set *src = by_kid[k];
+            rc = set_view(ctx, src->shared, src->col[0], src->d_rows, src->rows_known, &outs[i]);
+        }
+    }
+    if (rc != TID_OK) {
+        for (int i = 0; i < q; ++i) {
+            if (outs[i] && (kid_of[i] < 0 || outs[i] != by_kid[kid_of[i]])) set_free(outs[i]);
+            outs[i] = nullptr;
+        }
+        for (size_t k = 0; k < by_kid.size(); ++k) set_free(by_kid[k]);
+        return rc;
+    }
+    return TID_OK;
+}

@@ -110,7 +110,7 @@ extern "C" int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *
 
     auto release = [&](int i) {
         if (--readers[i] == 0 && res[i]) {
-            tid_set_free(res[i]);
+            set_free(res[i]);
             res[i] = nullptr;
         }
     };
@@ -121,7 +121,7 @@ extern "C" int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *
         switch (nd.op) {
             case TID_OP_MATCH:
                 rc = bind_set(ctx, st, nd.pattern, idx[i], fused[i].data(), (int)fused[i].size(), &res[i]);
-                tid_set_free(idx[i]);
+                set_free(idx[i]);
                 idx[i] = nullptr;
                 break;
             case TID_OP_FILTER:
@@ -161,8 +161,8 @@ extern "C" int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *
         res[n_nodes - 1] = nullptr;
     }
     for (int i = 0; i < n_nodes; ++i) {
-        if (res[i]) tid_set_free(res[i]);
-        if (idx[i]) tid_set_free(idx[i]);
+        if (res[i]) set_free(res[i]);
+        if (idx[i]) set_free(idx[i]);
     }
     return rc;
 }

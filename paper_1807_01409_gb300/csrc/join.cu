@@ -309,7 +309,7 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         int rc = set_rows_const(e, 0);
         if (rc == TID_OK) rc = set_ready(e);
         if (rc != TID_OK) {
-            tid_set_free(e);
+            set_free(e);
             return rc;
         }
         *out = e;

@@ -362,7 +362,7 @@ extern "C" int tid_match(tid_ctx *ctx, const tid_store *st, tid_pattern pat, tid
                           set->col[0], set->cap, set->d_rows, set->slot.dev, sc);
     if (rc == TID_OK) rc = set_ready(set);
     if (rc != TID_OK) {
-        tid_set_free(set);
+        set_free(set);
         return rc;
     }
     *out = set;

@@ -353,7 +353,7 @@ extern "C" int tid_match_multi(tid_ctx *ctx, const tid_store *st, const tid_patt
     for (int j = 0; j < m && rc == TID_OK; ++j) rc = set_ready(outs[j]);
     if (rc != TID_OK) {
         for (int j = 0; j < m; ++j) {
-            tid_set_free(outs[j]);
+            set_free(outs[j]);
             outs[j] = nullptr;
         }
     }

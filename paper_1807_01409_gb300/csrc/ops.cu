@@ -44,7 +44,7 @@ int empty_set(tid_ctx *ctx, int k, const int8_t *vars, tid_set **out) {
     int rc = set_rows_const(e, 0);
     if (rc == TID_OK) rc = set_ready(e);
     if (rc != TID_OK) {
-        tid_set_free(e);
+        set_free(e);
         return rc;
     }
     *out = e;
@@ -116,7 +116,7 @@ int bind_set(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, const ti
         rc = canonicalize(ctx, cols, k, vars, m, anon, &b, out);
     }
     if (mm) dev_free(ctx, mm);
-    tid_set_free(tmp);
+    set_free(tmp);
     return rc;
 }
 
@@ -137,7 +137,7 @@ int filter_set(tid_ctx *ctx, const tid_set *in, const tid_pred *preds, int n_pre
         }
     }
     if (rc != TID_OK) {
-        tid_set_free(o);
+        set_free(o);
         return rc;
     }
     *out = o;

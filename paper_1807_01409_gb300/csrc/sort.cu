@@ -450,7 +450,7 @@ int canonicalize(tid_ctx *ctx, const int32_t *const *cols, int k, const int8_t *
     }
     if (rc == TID_OK) rc = set_ready(set);
     if (rc != TID_OK) {
-        tid_set_free(set);
+        set_free(set);
         return rc;
     }
     *out = set;

@@ -76,6 +76,11 @@ struct PendingSlot {  // a freed set's slot, reusable once its producer event co
     cudaEvent_t ev;
 };
 
+struct SharedBlock {  // device allocations shared by several sets (freed with the last)
+    void *ptr[2] = {nullptr, nullptr};
+    int refs = 0;
+};
+
 }  // namespace tid
 
 struct tid_ctx {
@@ -118,6 +123,7 @@ struct tid_set {
     cudaEvent_t ready = nullptr; // recorded after the producing work
     int64_t rows_known = -1;
     void *block = nullptr;       // allocation holding the columns and d_rows
+    tid::SharedBlock *shared = nullptr;  // or: a view into allocations shared with other sets
     // Valid bounds of each column's values in sort order (int32 ^ 0x80000000),
     // when known: lo[c] <= every value of column c <= hi[c].
     bool bounded = false;
@@ -139,6 +145,10 @@ int ctx_scratch(tid_ctx *ctx, size_t words, LbScratch *sc);    // the context's 
 int make_lookback(const LbScratch &sc, unsigned int num_tiles, Lookback *lb);  // next epoch
 int set_alloc(tid_ctx *ctx, int k, const int8_t *vars, int64_t cap, tid_set **out);
 int set_ready(tid_set *set);      // record the producer event
+void set_free(tid_set *set);      // tid_set_free without clearing the error message
+// A one-column set labelled -1 viewing `col` (rows known on the host, count in
+// *d_rows on the device) inside sb's allocations; takes one reference on sb.
+int set_view(tid_ctx *ctx, tid::SharedBlock *sb, int32_t *col, int64_t *d_rows, int64_t rows, tid_set **out);
 int check_ctx_error(tid_ctx *ctx); // reads and clears the kernel error word
 int launch_check(const char *what);
 

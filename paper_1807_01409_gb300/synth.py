@@ -474,3 +474,155 @@ def university_plans(store: Store, seed: int = QUERY_SEED, n_star: int = 16, n_c
             nodes.append({"op": "join", "inputs": [1, 2], "algo": "auto"})
         plans.append((f"filter{i}", nodes))
     return plans
+
+
+# ----------------------------------------------------------------------------
+# large stores drawn on a device (batched and served workloads: 500M, 1B)
+# ----------------------------------------------------------------------------
+#
+# The same university recipe as university_store, drawn with torch on a device
+# (seconds at 500M, where the host recipe takes minutes).  The values differ from
+# university_store's (another random stream); the recipe, the ID layout and the
+# set property are the same.  Inputs only: no matching, joining or compaction.
+
+
+def university_store_torch(n: int, seed: int = STORE_SEED, device="cuda"):
+    """(s, p, o) int32 tensors on `device`: n distinct triples of the university
+    recipe in a seeded random order."""
+    import torch
+    dev = torch.device(device)
+    subjects = uni_subjects(n)
+    lay = uni_layout(subjects)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    hrng = np.random.default_rng(seed)
+    sizes = torch.as_tensor(lay["sizes"], dtype=torch.int64, device=dev)
+    starts = torch.as_tensor(lay["starts"], dtype=torch.int64, device=dev)
+    cdf_sub = torch.as_tensor(zipf_cdf(0.5, SUBCLASSES), device=dev)
+    ccdf = {}
+
+    def zipf(m, cdf):
+        u = torch.rand(m, generator=g, device=dev, dtype=torch.float64)
+        return torch.searchsorted(cdf, u, right=True).clamp_(max=cdf.shape[0] - 1) + 1
+
+    def pick(m, classes):
+        cls = torch.as_tensor(sorted(classes), dtype=torch.int64, device=dev)
+        w = torch.cumsum(sizes[cls].double(), 0)
+        u = torch.rand(m, generator=g, device=dev, dtype=torch.float64) * w[-1]
+        return cls[torch.searchsorted(w, u, right=True).clamp_(max=cls.shape[0] - 1)]
+
+    def draw(m):
+        counts = hrng.multinomial(m, PRED_FREQ)
+        parts = []
+        for j, (kind, dom, r) in enumerate(PRED_KIND):
+            mj = int(counts[j])
+            if mj == 0:
+                continue
+            cls = pick(mj, dom)
+            off = (torch.rand(mj, generator=g, device=dev, dtype=torch.float64) * sizes[cls]).long()
+            s = starts[cls] + off
+            if kind == "type":
+                o = lay["class_base"] + cls * SUBCLASSES + (zipf(mj, cdf_sub) - 1)
+            elif kind == "lit":
+                o = LIT_BASE + torch.randint(0, 10 ** r, (mj,), generator=g, device=dev)
+            else:
+                rc = pick(mj, r)
+                o = torch.empty(mj, dtype=torch.int64, device=dev)
+                for c in sorted(set(r)):
+                    sel = rc == c
+                    k = int(sel.sum())
+                    if k:
+                        if c not in ccdf:
+                            ccdf[c] = torch.as_tensor(zipf_cdf(1.1, int(lay["sizes"][c])), device=dev)
+                        o[sel] = int(lay["starts"][c]) + zipf(k, ccdf[c]) - 1
+            parts.append((s << _S_SHIFT) | (j << _P_SHIFT) | o)
+        return torch.cat(parts)
+
+    keys = torch.unique(draw(int(n * 1.08) + 1024))
+    while keys.shape[0] < n:
+        keys = torch.unique(torch.cat([keys, draw(int((n - keys.shape[0]) * 1.5) + 1024)]))
+    keys = keys[torch.randperm(keys.shape[0], generator=g, device=dev)[:n]]
+    s = ((keys >> _S_SHIFT) & ((1 << 26) - 1)).int()
+    pidx = (keys >> _P_SHIFT) & 127
+    o = (keys & ((1 << 31) - 1)).int()
+    del keys
+    p = torch.as_tensor(lay["pred_ids"], dtype=torch.int64, device=dev)[pidx].int()
+    return s.contiguous(), p.contiguous(), o.contiguous()
+
+
+# (mask, shape name, var labels) of the single-pattern shapes a batch draws from
+BATCH_SHAPES = [(2, "?p?", (0, -1, 1)), (6, "?po", (0, -1, -1)), (4, "??o", (0, 1, -1)),
+                (1, "s??", (-1, 0, 1)), (3, "sp?", (-1, -1, 0)), (5, "s?o", (-1, 0, -1)),
+                (7, "spo", (-1, -1, -1))]
+
+
+def batch_queries(s, p, o, m: int = 4096, seed: int = QUERY_SEED, lo: float = 1.0, hi: float = 1e7,
+                  window: float = 1.5):
+    """m single-pattern queries whose result sizes are log-uniform on [lo, hi] as far as
+    the store allows.  For each target size t a shape is drawn among those having
+    patterns whose size lies within a factor `window` of t, then one such pattern at
+    random (so a batch holds many distinct keys of every size); if no shape has one,
+    the pattern whose size is closest to t.  Sizes come from value tallies of the
+    store's columns (torch tensors, any device); they choose constants only.
+    Returns a list of (Pattern, target size, tally size)."""
+    import torch
+    rng = np.random.default_rng(seed + 4096)
+    s64, p64, o64 = s.long(), p.long(), o.long()
+    cols = {1: s64, 2: p64, 4: o64}
+    targets = np.exp(rng.uniform(np.log(lo), np.log(hi), size=m))
+    tt = torch.as_tensor(targets, device=s.device)
+    shapes = []
+    for mask, name, var in BATCH_SHAPES:
+        bound = [b for b in (1, 2, 4) if mask & b]
+        if len(bound) == 3:  # (s, p, o): every stored triple is a size-1 pattern
+            vals, cnt = None, None
+        else:
+            key = cols[bound[0]] if len(bound) == 1 else cols[bound[0]] * (1 << 32) + cols[bound[1]]
+            vals, cnt = torch.unique(key, return_counts=True)
+            del key
+            order = torch.argsort(cnt)
+            vals, cnt = vals[order], cnt[order]
+        shapes.append((mask, var, bound, vals, cnt))
+    n = s.shape[0]
+    lo_t, hi_t = (tt / window).ceil(), (tt * window).floor()
+    choice = []
+    for mask, var, bound, vals, cnt in shapes:
+        if cnt is None:
+            a = torch.zeros(m, dtype=torch.int64, device=s.device)
+            b = torch.where((lo_t <= 1) & (hi_t >= 1), torch.full_like(a, n), a)
+        else:
+            a = torch.searchsorted(cnt, lo_t.long())
+            b = torch.searchsorted(cnt, hi_t.long(), right=True)
+        choice.append((a.cpu().numpy(), b.cpu().numpy()))
+    out = []
+    for i, t in enumerate(targets):
+        ok = [k for k in range(len(shapes)) if choice[k][1][i] > choice[k][0][i]]
+        if ok:
+            k = int(rng.choice(ok))
+            j = int(rng.integers(choice[k][0][i], choice[k][1][i]))
+        else:  # closest size over all shapes
+            best = None
+            for k2, (_, _, _, vals, cnt) in enumerate(shapes):
+                if cnt is None:
+                    continue
+                q = int(torch.searchsorted(cnt, torch.as_tensor([int(t)], device=cnt.device)).clamp(max=cnt.shape[0] - 1))
+                for jj in (max(0, q - 1), q):
+                    d = abs(np.log(float(cnt[jj])) - np.log(t))
+                    if best is None or d < best[0]:
+                        best = (d, k2, jj)
+            _, k, j = best
+        mask, var, bound, vals, cnt = shapes[k]
+        if vals is None:
+            r = j
+            key = {1: int(s[r]), 2: int(p[r]), 4: int(o[r])}
+            size = 1
+        else:
+            v = int(vals[j])
+            if len(bound) == 1:
+                key = {bound[0]: v}
+            else:
+                key = {bound[0]: v >> 32, bound[1]: v & 0xFFFFFFFF}
+            size = int(cnt[j])
+        pat = Pattern(key.get(1, 0), key.get(2, 0), key.get(4, 0), var=var)
+        out.append((pat, float(t), size))
+    return out

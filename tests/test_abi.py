@@ -56,3 +56,17 @@ def test_product_never_imports_oracle():
     for f in glob.glob(os.path.join(ROOT, "paper_1807_01409_gb300", "**", "*.*"), recursive=True):
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             assert not pat.search(open(f).read()), f
+
+
+def test_pattern_array_matches_the_c_struct():
+    import ctypes
+    import numpy as np
+    from paper_1807_01409_gb300 import binding as tb
+    from paper_1807_01409_gb300.synth import Pattern
+    assert tb.PATTERN_DTYPE.itemsize == ctypes.sizeof(tb.tid_pattern) == 16
+    a = tb.pattern_array(np.array([[1, 2, 3], [0, 5, 0]]))
+    b = tb.pattern_array([(1, 2, 3), Pattern(0, 5, 0)])
+    assert a.tobytes() == b.tobytes()
+    c = tb.pattern_array([Pattern(0, 5, 0, var=(0, -1, 1))])
+    t = tb.tid_pattern.from_buffer_copy(c.tobytes())
+    assert (t.s, t.p, t.o, tuple(t.var)) == (0, 5, 0, (0, -1, 1))
