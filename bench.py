@@ -8,6 +8,11 @@ with the scan kernel's achieved HBM bandwidth against the measured peak.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Beside the headline, "rows" times every other row of the path (multi-pattern
+scan, bind+filter, sort, joins, union, filter, plan execution) on the same
+store, and "batch" times 4096 single-pattern queries on a 500M-triple store
+batched (tid_match_batch) against one launch per query on the same GPU.
+
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
 of the workload (weak scaling: fixed work per GPU); the step time is the max
 over ranks.  --impl reference times the CPU oracle (the plain nested-loop
@@ -36,6 +41,10 @@ UNIT = "Gtriples/s"
 N_TRIPLES = synth.UNI_FULL
 WORKLOAD = ("university-200M: 200M triples (int32 SoA, resident), 64 single-pattern "
             "queries, selectivity 1e-6..0.3")
+BATCH_TRIPLES = 500_000_000
+BATCH_QUERIES = 4096
+BATCH_WORKLOAD = ("university-500M (drawn on the device): 500M triples (6 GB int32 SoA, resident), "
+                  "4096 single-pattern queries of all seven shapes, result sizes log-uniform 1..1e7")
 
 
 def _env_rank():
@@ -464,6 +473,12 @@ def run_ours(args, rank, world, local):
                             with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     tb.tid_store_free(store)
+    del cols
+    torch.cuda.empty_cache()
+    batch = None
+    if not args.no_batch:
+        batch = measure_batch(tb, ctx, stream, _peaks()[0],
+                              with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     tb.tid_ctx_destroy(ctx)
 
     if rank == 0:
@@ -489,10 +504,132 @@ def run_ours(args, rank, world, local):
             "clocks": clk.summary(),
             "cpu_baseline": base,
             "rows": rows,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _pct(x, q):
+    return float(np.percentile(np.asarray(x, np.float64), q))
+
+
+def measure_batch(tb, ctx, stream, peak, n=BATCH_TRIPLES, m=BATCH_QUERIES, with_oracle=True, reps=3):
+    """Batched search against one launch per query on the same GPU: 4096 patterns
+    over a 500M-triple store.  Batched: one tid_match_batch call (every query is
+    answered when it returns).  Plain: one tid_match per query in submission order
+    (a query's latency is the time from the start to its own scan's completion).
+    Both from the same start, all queries submitted at once."""
+    import torch
+
+    s, p, o = synth.university_store_torch(n, device="cuda")
+    qs = synth.batch_queries(s, p, o, m=m)
+    keys = np.array([q.key() for q, _, _ in qs], np.int64)
+    pats = tb.pattern_array(keys)
+    sizes = np.array([sz for _, _, sz in qs], np.int64)
+    distinct = {}
+    for pat, _, sz in qs:
+        distinct[pat.key()] = sz
+    dk = list(distinct)
+    alg_bytes = 0
+    for b in range(0, len(dk), tb.TID_BATCH_KEYS):  # per sub-batch: two passes over its columns
+        cols = 0
+        for k in dk[b:b + tb.TID_BATCH_KEYS]:
+            cols |= sum(1 << j for j in range(3) if k[j])
+        alg_bytes += 2 * 4 * bin(cols).count("1") * n
+    alg_bytes += 4 * sum(distinct.values())
+    torch.cuda.synchronize()
+    store = tb.tid_load(ctx, s, p, o, copy=0)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    for h in tb.tid_match_batch(ctx, store, pats):
+        tb.tid_set_free(h)
+    batch_ms, hits_ok = [], True
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        hs = tb.tid_match_batch(ctx, store, pats)
+        e1.record(stream)
+        e1.synchronize()
+        batch_ms.append(e0.elapsed_time(e1))
+        got = np.array([tb.tid_set_rows(h) for h in hs], np.int64)
+        hits_ok = hits_ok and bool(np.array_equal(got, sizes))
+        for h in hs:
+            tb.tid_set_free(h)
+
+    plist = [tb.as_pattern(tuple(int(x) for x in k)) for k in keys]
+    for q in plist[:64]:
+        tb.tid_set_free(tb.tid_match(ctx, store, q))
+    torch.cuda.synchronize()
+    done = [ev() for _ in plist]
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for q, e in zip(plist, done):
+        h = tb.tid_match(ctx, store, q)
+        e.record(stream)
+        tb.tid_set_free(h)
+    e1.record(stream)
+    e1.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    plain_lat = [e0.elapsed_time(e) for e in done]
+    tb.tid_store_free(store)
+
+    oracle = None
+    if with_oracle:
+        from oracle import oracle as orc
+        orc.build()
+        hs_, hp_, ho_ = (t.cpu().numpy() for t in (s, p, o))
+        t0, cnt = time.perf_counter(), 0
+        for k in keys[:: max(1, m // 64)]:
+            orc.match(hs_, hp_, ho_, tuple(int(x) for x in k))
+            cnt += 1
+            if time.perf_counter() - t0 > 10.0:
+                break
+        dt = time.perf_counter() - t0
+        oracle = {"value": cnt / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                  "sample": f"{cnt} of the {m} queries (every {max(1, m // 64)}th), each a full "
+                            f"single-threaded C oracle scan of the {n}-triple store ({dt:.1f} s)"}
+        del hs_, hp_, ho_
+    del s, p, o
+    torch.cuda.empty_cache()
+    bms = statistics.median(batch_ms)
+    return {
+        "workload": BATCH_WORKLOAD, "n_triples": n, "queries": m, "distinct_keys": len(dk),
+        "sub_batches": (len(dk) + tb.TID_BATCH_KEYS - 1) // tb.TID_BATCH_KEYS,
+        "result_rows": int(sizes.sum()), "result_rows_distinct_keys": int(sum(distinct.values())),
+        "results_match_tallies": hits_ok,
+        "batched": {"ms": bms, "ms_all": batch_ms, "queries_per_s": m / (bms / 1e3),
+                    "p50_ms": bms, "p99_ms": bms},
+        "plain": {"ms": plain_ms, "queries_per_s": m / (plain_ms / 1e3),
+                  "p50_ms": _pct(plain_lat, 50), "p99_ms": _pct(plain_lat, 99)},
+        "speedup_queries_per_s": plain_ms / bms,
+        "p99_ratio_plain_over_batched": _pct(plain_lat, 99) / bms,
+        "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / (bms / 1e3) / 1e9,
+                "frac_of_peak": alg_bytes / (bms / 1e3) / 1e9 / peak,
+                "note": "whole call: both passes of every sub-batch, the scans of counts, the "
+                        "host synchronisation between passes and set creation"},
+        "cpu_baseline": oracle,
+    }
+
+
+def run_batch_only(args, local):
+    """One batched-versus-plain measurement (no oracle), for launch-list captures."""
+    import torch
+
+    from paper_1807_01409_gb300 import binding as tb
+    from paper_1807_01409_gb300 import build as tbuild
+    torch.cuda.set_device(local)
+    tbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = tb.tid_ctx_create(local, stream.cuda_stream)
+    res = measure_batch(tb, ctx, stream, _peaks()[0], with_oracle=False, reps=1)
+    tb.tid_ctx_destroy(ctx)
+    print(json.dumps({"batch": res}), flush=True)
 
 
 def run_rows_only(args, local):
@@ -526,6 +663,9 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the other rows of the path")
     ap.add_argument("--rows-only", action="store_true",
                     help="profiling aid: one pass of the other rows only (no oracle), printed as JSON")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-queries row")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="profiling aid: one batched-versus-plain measurement only, printed as JSON")
     ap.add_argument("--triples", type=int, default=N_TRIPLES,
                     help="store size (default: the full 200M workload; smaller only for profiling)")
     args = ap.parse_args()
@@ -534,6 +674,8 @@ def main():
         run_reference(args, rank, world)
     elif args.rows_only:
         run_rows_only(args, local)
+    elif args.batch_only:
+        run_batch_only(args, local)
     else:
         run_ours(args, rank, world, local)
 
