@@ -11,7 +11,10 @@ with the scan kernel's achieved HBM bandwidth against the measured peak.
 Beside the headline, "rows" times every other row of the path (multi-pattern
 scan, bind+filter, sort, joins, union, filter, plan execution) on the same
 store, and "batch" times 4096 single-pattern queries on a 500M-triple store
-batched (tid_match_batch) against one launch per query on the same GPU.
+batched (tid_match_batch) against one launch per query on the same GPU, and
+"serve" runs a Poisson request stream through the request server (continuous
+batching, admission by estimated bytes) against the same server taking one
+request at a time with one search launch per request.
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
 of the workload (weak scaling: fixed work per GPU); the step time is the max
@@ -480,6 +483,9 @@ def run_ours(args, rank, world, local):
         batch = measure_batch(tb, ctx, stream, _peaks()[0],
                               with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     tb.tid_ctx_destroy(ctx)
+    serve = None
+    if not args.no_serve:
+        serve = measure_serve(tb, with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     if rank == 0:
         line = {
@@ -505,6 +511,7 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": base,
             "rows": rows,
             "batch": batch,
+            "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -616,6 +623,98 @@ def measure_batch(tb, ctx, stream, peak, n=BATCH_TRIPLES, m=BATCH_QUERIES, with_
     }
 
 
+SERVE_TRIPLES = 1_000_000_000
+SERVE_REQUESTS = 4000
+SERVE_RATE = 20000.0
+SERVE_BUDGET = 60 << 30
+SERVE_WORKLOAD = ("university-1B (drawn on the device): 1B triples (12 GB int32 SoA, resident), Poisson "
+                  "arrivals at 20k requests/s: 70% index lookups (result sizes log-uniform 1..1e5), 15% "
+                  "two-pattern star joins, 15% unions / literal-range filters; 60 GB admission budget")
+
+
+def _serve_stream(tb, srv, prepared, arrivals):
+    """Submit every request at its arrival time (open loop), wait for all; latencies
+    run from the scheduled arrival."""
+    t0 = tb.Server.now_ns() + 20_000_000
+    due = (t0 + np.asarray(arrivals) * 1e9).astype(np.int64)
+    ids, i, m = [], 0, len(prepared)
+    while i < m:
+        now = tb.Server.now_ns()
+        while i < m and due[i] <= now:
+            ids.append(srv.submit(prepared[i], int(due[i])))
+            i += 1
+        if i < m:
+            time.sleep(max(0.0, min(1e-3, (due[i] - tb.Server.now_ns()) / 1e9)))
+    lat, fin, bad = [], [], 0
+    for rid, d in zip(ids, due):
+        srv.wait(rid)
+        st, _, rows, ln = srv.result(rid)
+        bad += st != tb.TID_OK
+        lat.append(ln / 1e6)
+        fin.append(int(d) + ln)
+    span = (max(fin) - t0) / 1e9
+    return {"requests": m, "seconds": span, "queries_per_s": m / span, "p50_ms": _pct(lat, 50),
+            "p99_ms": _pct(lat, 99), "max_ms": max(lat), "failed": int(bad)}
+
+
+def measure_serve(tb, n=SERVE_TRIPLES, m=SERVE_REQUESTS, rate=SERVE_RATE, with_oracle=True):
+    """The request server against the same server run one request at a time with one
+    search launch per request, on the same Poisson stream."""
+    import torch
+
+    s, p, o = synth.university_store_torch(n, device="cuda")
+    kinds, payloads, arrivals = synth.serving_requests(s, p, o, m=m, rate=rate)
+    prepared = [tb.Server.request(k, x) for k, x in zip(kinds, payloads)]
+    torch.cuda.synchronize()
+    out = {"workload": SERVE_WORKLOAD, "n_triples": n, "offered_queries_per_s": rate,
+           "mix": {k: kinds.count(k) for k in set(kinds)}}
+    for name, kw in (("served", dict(workers=2, max_wave=4096, batch_scans=True, budget_bytes=SERVE_BUDGET)),
+                     ("plain", dict(workers=1, max_wave=1, batch_scans=False, budget_bytes=SERVE_BUDGET))):
+        with tb.Server(s, p, o, **kw) as srv:
+            warm = [srv.submit(x) for x in prepared[:32]]
+            for rid in warm:
+                srv.wait(rid)
+                srv.release(rid)
+            res = _serve_stream(tb, srv, prepared, arrivals)
+            res["stats"] = srv.stats()
+            res["config"] = kw
+        out[name] = res
+    out["speedup_queries_per_s"] = out["served"]["queries_per_s"] / out["plain"]["queries_per_s"]
+    out["p99_ratio_plain_over_served"] = out["plain"]["p99_ms"] / out["served"]["p99_ms"]
+    if with_oracle:
+        from oracle import oracle as orc
+        orc.build()
+        hs_, hp_, ho_ = (t.cpu().numpy() for t in (s, p, o))
+        t0, cnt = time.perf_counter(), 0
+        for k, x in zip(kinds, payloads):
+            if k == "index":
+                orc.match(hs_, hp_, ho_, x.key())
+            else:
+                orc.execute(hs_, hp_, ho_, x)
+            cnt += 1
+            if time.perf_counter() - t0 > 10.0:
+                break
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": cnt / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                               "sample": f"the first {cnt} requests of the stream, one after another, "
+                                         f"single-threaded oracle on the {n}-triple store ({dt:.1f} s)"}
+        del hs_, hp_, ho_
+    del s, p, o
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve_only(args, local):
+    """One served-versus-plain measurement (no oracle), for launch-list captures."""
+    import torch
+
+    from paper_1807_01409_gb300 import binding as tb
+    from paper_1807_01409_gb300 import build as tbuild
+    torch.cuda.set_device(local)
+    tbuild.build()
+    print(json.dumps({"serve": measure_serve(tb, with_oracle=False)}), flush=True)
+
+
 def run_batch_only(args, local):
     """One batched-versus-plain measurement (no oracle), for launch-list captures."""
     import torch
@@ -666,6 +765,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-queries row")
     ap.add_argument("--batch-only", action="store_true",
                     help="profiling aid: one batched-versus-plain measurement only, printed as JSON")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-requests row")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="profiling aid: one served-versus-plain measurement only, printed as JSON")
     ap.add_argument("--triples", type=int, default=N_TRIPLES,
                     help="store size (default: the full 200M workload; smaller only for profiling)")
     args = ap.parse_args()
@@ -676,6 +778,8 @@ def main():
         run_rows_only(args, local)
     elif args.batch_only:
         run_batch_only(args, local)
+    elif args.serve_only:
+        run_serve_only(args, local)
     else:
         run_ours(args, rank, world, local)
 

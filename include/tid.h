@@ -307,6 +307,91 @@ int tid_set_to_host(tid_set *set, int32_t *buf, int64_t cap_rows, int64_t *rows_
 
 int tid_set_free(tid_set *set);
 
+/* ------------------------------------------------------------------------ */
+/* serving: a request loop over a resident store                             */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper answers one query at a time (Section 4.3: split into subqueries,
+ * search, extract, join).  A server keeps the store resident and answers a
+ * stream of requests with continuous batching; the paper has no counterpart.
+ *
+ *  - Requests wait in one first-come-first-served queue.  A worker admits the
+ *    requests at the head of the queue while their estimated device bytes fit
+ *    in what is left of the budget (the head is always admitted when nothing
+ *    else is admitted), up to max_wave of them: a wave.  Requests that arrive
+ *    while a wave runs join the next wave of the first free worker.
+ *  - Estimated bytes: a pattern's rows are estimated from value counts of a
+ *    strided sample of the store (the least frequent bound value wins); a
+ *    plan's bytes are the sum over its nodes of estimated rows x 4 bytes x
+ *    (columns + 1), joins estimated as their larger input, unions as the sum.
+ *  - With batch_scans = 1, every MATCH node of every request of a wave is
+ *    searched by one tid_match_batch call; each request then runs the rest of
+ *    its plan.  With batch_scans = 0 each request searches alone (tid_match
+ *    for an index request, tid_exec for a plan): with max_wave = 1 and one
+ *    worker this is one launch per query, the server's own baseline.
+ *  - Workers run on their own contexts and streams, so one wave's operators
+ *    overlap the next wave's scan on the GPU.
+ *  - A request's result is copied to host memory owned by the server until
+ *    tid_server_release.  Its latency runs from its arrival time (given at
+ *    submission on the tid_server_now_ns clock, or the submission time) to the
+ *    moment its result is in host memory.
+ *  - A result does not depend on what else is in the wave: every path returns
+ *    the canonical set (index lists: the ascending list).
+ */
+typedef struct tid_server tid_server;
+
+typedef struct {
+    int32_t workers;       /* worker threads, each with its own context and stream (1..16) */
+    int32_t max_wave;      /* requests per wave (>= 1) */
+    int32_t batch_scans;   /* 1: a wave shares one batched search; 0: each request searches alone */
+    int32_t reserved;      /* set to 0 */
+    int64_t budget_bytes;  /* estimated device bytes of admitted requests; 0 = unlimited */
+} tid_server_config;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t waves;               /* waves run */
+    int64_t max_wave_seen;       /* largest wave */
+    int64_t peak_admitted_bytes; /* largest sum of estimates admitted at once */
+    int64_t scan_patterns;       /* MATCH nodes searched */
+} tid_server_stats;
+
+#define TID_REQ_INDEX 1  /* nodes = one MATCH node; result: its ascending index list (one column, -1) */
+#define TID_REQ_PLAN  2  /* result: the plan's canonical tuple set (as tid_exec)                      */
+
+/* Server on CUDA device `device` over the store s/p/o (n int32 each, device
+ * memory, borrowed: unchanged and valid until tid_server_destroy).  Starts the
+ * workers.  Errors: TID_ERR_ARG (bad configuration), TID_ERR_OOM, TID_ERR_CUDA. */
+int tid_server_create(int device, const int32_t *s, const int32_t *p, const int32_t *o, int64_t n,
+                      const tid_server_config *cfg, tid_server **out);
+
+/* Nanoseconds on the server clock (steady, process-wide). */
+int64_t tid_server_now_ns(void);
+
+/* Queue a request (nodes are copied); *id receives its id.  arrival_ns <= 0
+ * means now.  The plan is checked here: TID_ERR_ARG / TID_ERR_ID as tid_exec. */
+int tid_server_submit(tid_server *srv, int kind, const tid_plan_node *nodes, int n_nodes, int64_t arrival_ns,
+                      int64_t *id);
+
+/* Wait up to timeout_ms (< 0: forever) for request id: TID_OK once it has
+ * finished (successfully or not), TID_ERR_TIMEOUT if it has not yet. */
+int tid_server_wait(tid_server *srv, int64_t id, int64_t timeout_ms);
+
+/* A finished request: its status (TID_OK or the error of its evaluation),
+ * columns, variable ids (up to TID_MAX_COLS), rows, host data (rows x cols
+ * int32, row-major; owned by the server until tid_server_release) and latency.
+ * Any output pointer may be NULL.  TID_ERR_ARG if id is unknown or unfinished. */
+int tid_server_result(tid_server *srv, int64_t id, int *status, int *cols, int8_t *vars, int64_t *rows,
+                      const int32_t **data, int64_t *latency_ns);
+
+/* Forget a finished request and its host data. */
+int tid_server_release(tid_server *srv, int64_t id);
+
+int tid_server_get_stats(tid_server *srv, tid_server_stats *out);
+
+/* Finish every queued request, stop the workers and free the server. */
+int tid_server_destroy(tid_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

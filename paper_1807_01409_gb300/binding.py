@@ -35,6 +35,19 @@ class tid_pattern(C.Structure):
                 ("var", C.c_int8 * 3), ("reserved", C.c_int8)]
 
 
+class tid_server_config(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("max_wave", C.c_int32), ("batch_scans", C.c_int32),
+                ("reserved", C.c_int32), ("budget_bytes", C.c_int64)]
+
+
+class tid_server_stats(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in ("submitted", "completed", "failed", "waves", "max_wave_seen",
+                                         "peak_admitted_bytes", "scan_patterns")]
+
+
+TID_REQ_INDEX, TID_REQ_PLAN = 1, 2
+
+
 class tid_pred(C.Structure):
     _fields_ = [("var", C.c_int32), ("op", C.c_int32), ("a", C.c_int32), ("b", C.c_int32)]
 
@@ -107,6 +120,16 @@ def lib():
         "tid_exec": (C.c_int, [_vp, _vp, C.POINTER(tid_plan_node), C.c_int, C.POINTER(_vp)]),
         "tid_match_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, C.c_int64, tid_pattern, _vp, C.c_int64,
                                         _vp]),
+        "tid_server_create": (C.c_int, [C.c_int, _vp, _vp, _vp, C.c_int64, C.POINTER(tid_server_config),
+                                        C.POINTER(_vp)]),
+        "tid_server_now_ns": (C.c_int64, []),
+        "tid_server_submit": (C.c_int, [_vp, C.c_int, C.POINTER(tid_plan_node), C.c_int, C.c_int64, i64p]),
+        "tid_server_wait": (C.c_int, [_vp, C.c_int64, C.c_int64]),
+        "tid_server_result": (C.c_int, [_vp, C.c_int64, C.POINTER(C.c_int), C.POINTER(C.c_int), i8p, i64p,
+                                        C.POINTER(i32p), i64p]),
+        "tid_server_release": (C.c_int, [_vp, C.c_int64]),
+        "tid_server_get_stats": (C.c_int, [_vp, C.POINTER(tid_server_stats)]),
+        "tid_server_destroy": (C.c_int, [_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -396,6 +419,91 @@ class Context:
         self._owned = []
         if self.h:
             tid_ctx_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """A tid_server over device columns s, p, o (kept referenced while it lives).
+    Requests: submit_index(pattern) -> ascending index list; submit_plan(plan)
+    -> canonical tuple set (rows x vars).  See tid.h for the scheduling rules."""
+
+    def __init__(self, s, p, o, device=0, workers=2, max_wave=4096, batch_scans=True, budget_bytes=60 << 30):
+        self._cols = (s, p, o)
+        cfg = tid_server_config(int(workers), int(max_wave), 1 if batch_scans else 0, 0, int(budget_bytes))
+        h = _vp()
+        n = int(s.shape[0])
+        _check(lib().tid_server_create(int(device), _ptr(s), _ptr(p), _ptr(o), n, C.byref(cfg), C.byref(h)),
+               "tid_server_create")
+        self.h = h
+
+    @staticmethod
+    def now_ns() -> int:
+        return int(lib().tid_server_now_ns())
+
+    def _submit(self, kind, nodes, arrival_ns):
+        rid = C.c_int64()
+        _check(lib().tid_server_submit(self.h, kind, nodes, len(nodes), int(arrival_ns), C.byref(rid)),
+               "tid_server_submit")
+        return rid.value
+
+    @staticmethod
+    def request(kind, x):
+        """(kind code, node array) of an index request (x: a pattern) or a plan request
+        (x: a plan), prepared ahead of submission."""
+        if kind == "index":
+            nodes = (tid_plan_node * 1)()
+            nodes[0].op = OP["match"]
+            nodes[0].pattern = as_pattern(x)
+            return TID_REQ_INDEX, nodes
+        return TID_REQ_PLAN, plan_nodes(x)
+
+    def submit(self, prepared, arrival_ns=0):
+        return self._submit(prepared[0], prepared[1], arrival_ns)
+
+    def submit_index(self, pattern, arrival_ns=0):
+        return self.submit(self.request("index", pattern), arrival_ns)
+
+    def submit_plan(self, plan, arrival_ns=0):
+        return self.submit(self.request("plan", plan), arrival_ns)
+
+    def wait(self, rid, timeout_ms=-1) -> bool:
+        rc = lib().tid_server_wait(self.h, int(rid), int(timeout_ms))
+        if rc == TID_ERR_TIMEOUT:
+            return False
+        _check(rc, "tid_server_wait")
+        return True
+
+    def result(self, rid, release=True):
+        """(status, vars, rows array (rows x cols int32, a copy), latency in ns)."""
+        st, k, rows, lat = C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+        vars_ = (C.c_int8 * TID_MAX_COLS)()
+        data = C.POINTER(C.c_int32)()
+        _check(lib().tid_server_result(self.h, int(rid), C.byref(st), C.byref(k), vars_, C.byref(rows),
+                                       C.byref(data), C.byref(lat)), "tid_server_result")
+        n = rows.value * k.value
+        arr = np.ctypeslib.as_array(data, shape=(n,)).copy() if n else np.zeros(0, np.int32)
+        out = (st.value, tuple(vars_[:k.value]), arr.reshape(rows.value, max(1, k.value)), lat.value)
+        if release:
+            self.release(rid)
+        return out
+
+    def release(self, rid):
+        _check(lib().tid_server_release(self.h, int(rid)), "tid_server_release")
+
+    def stats(self) -> dict:
+        st = tid_server_stats()
+        _check(lib().tid_server_get_stats(self.h, C.byref(st)), "tid_server_get_stats")
+        return {f: getattr(st, f) for f, _ in tid_server_stats._fields_}
+
+    def close(self):
+        if self.h:
+            lib().tid_server_destroy(self.h)
             self.h = None
 
     def __enter__(self):

@@ -51,14 +51,26 @@ int validate(const tid_plan_node *nodes, int n) {
 
 }  // namespace
 
-extern "C" int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *nodes, int n_nodes, tid_set **out) {
-    clear_error();
-    if (!ctx || !st || !nodes || !out) return fail(TID_ERR_ARG, "tid_exec: null argument");
-    *out = nullptr;
+namespace tid {
+
+int validate_plan(const tid_plan_node *nodes, int n_nodes) {
     if (n_nodes < 1) return fail(TID_ERR_ARG, "tid_exec: empty plan");
-    if (st->ctx != ctx) return fail(TID_ERR_ARG, "tid_exec: store belongs to another context");
     TID_TRY(validate(nodes, n_nodes));
-    DeviceGuard g(ctx->device);
+    for (int i = 0; i < n_nodes; ++i)
+        if (nodes[i].op == TID_OP_MATCH) {
+            int8_t v[TID_MAX_COLS];
+            int k = 0;
+            bool anon = false;
+            TID_TRY(pattern_vars(nodes[i].pattern, v, &k, &anon));
+        }
+    return TID_OK;
+}
+
+// Evaluates a validated plan.  matched[i], for a MATCH node i, is its index list
+// when the caller searched it already (taken over and freed here), or null.
+int exec_plan(tid_ctx *ctx, const tid_store *st, const tid_plan_node *nodes, int n_nodes, tid_set **matched,
+              tid_set **out) {
+    *out = nullptr;
 
     std::vector<int> readers(n_nodes, 0);
     for (int i = 0; i < n_nodes; ++i)
@@ -86,23 +98,22 @@ extern "C" int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *
     std::vector<tid_set *> idx(n_nodes, nullptr);
     int rc = TID_OK;
 
-    // 1) search: all MATCH nodes, up to TID_MAX_MULTI per pass
+    // 1) search: all MATCH nodes not searched yet, up to TID_MAX_MULTI per pass
     std::vector<int> matches;
-    for (int i = 0; i < n_nodes; ++i)
-        if (nodes[i].op == TID_OP_MATCH) matches.push_back(i);
+    for (int i = 0; i < n_nodes; ++i) {
+        if (nodes[i].op != TID_OP_MATCH) continue;
+        if (matched && matched[i]) {
+            idx[i] = matched[i];
+            matched[i] = nullptr;
+        } else {
+            matches.push_back(i);
+        }
+    }
     for (size_t b = 0; b < matches.size() && rc == TID_OK; b += TID_MAX_MULTI) {
         const int m = (int)std::min<size_t>(TID_MAX_MULTI, matches.size() - b);
         tid_pattern pats[TID_MAX_MULTI];
         tid_set *outs[TID_MAX_MULTI];
-        for (int j = 0; j < m; ++j) {
-            pats[j] = nodes[matches[b + j]].pattern;
-            int8_t v[TID_MAX_COLS];
-            int k = 0;
-            bool anon = false;
-            rc = pattern_vars(pats[j], v, &k, &anon);
-            if (rc != TID_OK) break;
-        }
-        if (rc != TID_OK) break;
+        for (int j = 0; j < m; ++j) pats[j] = nodes[matches[b + j]].pattern;
         rc = m == 1 ? tid_match(ctx, st, pats[0], &outs[0]) : tid_match_multi(ctx, st, pats, m, outs);
         if (rc != TID_OK) break;
         for (int j = 0; j < m; ++j) idx[matches[b + j]] = outs[j];
@@ -163,6 +174,22 @@ extern "C" int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *
     for (int i = 0; i < n_nodes; ++i) {
         if (res[i]) set_free(res[i]);
         if (idx[i]) set_free(idx[i]);
+        if (matched && matched[i]) {
+            set_free(matched[i]);
+            matched[i] = nullptr;
+        }
     }
     return rc;
+}
+
+}  // namespace tid
+
+extern "C" int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *nodes, int n_nodes, tid_set **out) {
+    clear_error();
+    if (!ctx || !st || !nodes || !out) return fail(TID_ERR_ARG, "tid_exec: null argument");
+    *out = nullptr;
+    if (st->ctx != ctx) return fail(TID_ERR_ARG, "tid_exec: store belongs to another context");
+    TID_TRY(validate_plan(nodes, n_nodes));
+    DeviceGuard g(ctx->device);
+    return exec_plan(ctx, st, nodes, n_nodes, nullptr, out);
 }

@@ -73,4 +73,10 @@ int set_rows_host(const tid_set *set, int64_t *rows);
 // joins (join.cu)
 int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out);
 
+// plans (exec.cu): checks a plan's shape and patterns; evaluates a checked plan,
+// taking over matched[i] (an index list, or null to search it) for MATCH nodes
+int validate_plan(const tid_plan_node *nodes, int n_nodes);
+int exec_plan(tid_ctx *ctx, const tid_store *st, const tid_plan_node *nodes, int n_nodes, tid_set **matched,
+              tid_set **out);
+
 }  // namespace tid

@@ -626,3 +626,85 @@ def batch_queries(s, p, o, m: int = 4096, seed: int = QUERY_SEED, lo: float = 1.
         pat = Pattern(key.get(1, 0), key.get(2, 0), key.get(4, 0), var=var)
         out.append((pat, float(t), size))
     return out
+
+
+# ----------------------------------------------------------------------------
+# a served request stream: Poisson arrivals of three query classes
+# ----------------------------------------------------------------------------
+
+SERVE_MIX = (0.7, 0.15, 0.15)  # index lookups, two-pattern star joins, unions / filters
+
+
+def serving_requests(s, p, o, m: int = 4000, seed: int = QUERY_SEED, mix=SERVE_MIX, hi_index: float = 1e5,
+                     rate: float = 20000.0):
+    """m requests over a university store held as torch columns, with Poisson
+    arrival offsets (seconds, mean rate `rate`).  Returns (kinds, payloads,
+    arrivals): kind "index" carries a Pattern (the answer is its index list; result
+    sizes log-uniform on [1, hi_index] as batch_queries draws them); kind "plan"
+    carries a plan (list of node dicts):
+      * star: (?X p1 o1) JOIN (?X p2 o2), two triples of one random subject whose
+        predicates are entity-valued or fine-grained literals (both selective);
+      * union: (s p_j ?Y) for 2-4 predicates of one random subject, UNION;
+      * filter: (s ?P ?V) of one random subject, FILTER ?V in a literal range.
+    Inputs only: subjects and their triples are looked up by sorting the subject
+    column (no query evaluation)."""
+    import torch
+    rng = np.random.default_rng(seed + 20000)
+    kinds = rng.choice(3, size=m, p=np.asarray(mix) / np.sum(mix))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=m))
+    n = int(s.shape[0])
+    lay = uni_layout(uni_subjects(n))
+    pred_base = int(lay["pred_base"])
+    selective = set()
+    for j, (kind, _, r) in enumerate(PRED_KIND):
+        if kind == "ent" or (kind == "lit" and r >= 5):
+            selective.add(pred_base + j)
+    idx_q = iter(batch_queries(s, p, o, m=int((kinds == 0).sum()), seed=seed + 1, lo=1.0, hi=hi_index))
+    s_sorted, order = torch.sort(s)
+
+    def triples_of(s0):
+        a = int(torch.searchsorted(s_sorted, torch.tensor([s0], dtype=s_sorted.dtype, device=s.device)))
+        b = int(torch.searchsorted(s_sorted, torch.tensor([s0], dtype=s_sorted.dtype, device=s.device), right=True))
+        rows = order[a:b]
+        return p[rows].cpu().numpy(), o[rows].cpu().numpy()
+
+    def random_subject():
+        return int(s[int(rng.integers(0, n))])
+
+    payloads = []
+    for kd in kinds:
+        if kd == 0:
+            payloads.append(next(idx_q)[0])
+            continue
+        while True:
+            s0 = random_subject()
+            ps, os_ = triples_of(s0)
+            if kd == 1:
+                cand = [i for i in range(len(ps)) if int(ps[i]) in selective]
+                if len(cand) < 2:
+                    continue
+                i1, i2 = (int(x) for x in rng.choice(cand, size=2, replace=False))
+                plan = [{"op": "match", "pattern": Pattern(0, int(ps[i1]), int(os_[i1]), var=(X, -1, -1))},
+                        {"op": "match", "pattern": Pattern(0, int(ps[i2]), int(os_[i2]), var=(X, -1, -1))},
+                        {"op": "join", "inputs": [0, 1], "algo": "auto"}]
+            elif rng.random() < 0.5:
+                own = np.unique(ps)
+                if len(own) < 2:
+                    continue
+                k = int(rng.integers(2, min(4, len(own)) + 1))
+                plan = [{"op": "match", "pattern": Pattern(s0, int(pj), 0, var=(-1, -1, Y))}
+                        for pj in rng.choice(own, size=k, replace=False)]
+                plan.append({"op": "union", "inputs": list(range(k))})
+            else:
+                lit = os_[os_ >= LIT_BASE]
+                if len(lit) == 0:
+                    continue
+                v = int(rng.choice(lit)) - LIT_BASE
+                lo_, hi_ = max(0, v - int(rng.integers(0, 1000))), v + int(rng.integers(0, 1000))
+                plan = [{"op": "match", "pattern": Pattern(s0, 0, 0, var=(-1, Y, Z))},
+                        {"op": "filter", "input": 0, "var": Z, "cmp": "range",
+                         "a": LIT_BASE + lo_, "b": LIT_BASE + hi_}]
+            payloads.append(plan)
+            break
+    del s_sorted, order
+    return ["index" if k == 0 else "plan" for k in kinds], payloads, arrivals
