@@ -726,7 +726,7 @@ def run_batch_only(args, local):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = tb.tid_ctx_create(local, stream.cuda_stream)
-    res = measure_batch(tb, ctx, stream, _peaks()[0], with_oracle=False, reps=1)
+    res = measure_batch(tb, ctx, stream, _peaks()[0], n=args.batch_triples, with_oracle=False, reps=1)
     tb.tid_ctx_destroy(ctx)
     print(json.dumps({"batch": res}), flush=True)
 
@@ -765,6 +765,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-queries row")
     ap.add_argument("--batch-only", action="store_true",
                     help="profiling aid: one batched-versus-plain measurement only, printed as JSON")
+    ap.add_argument("--batch-triples", type=int, default=BATCH_TRIPLES,
+                    help="store size of --batch-only (default: the 500M workload; smaller only for profiling)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-requests row")
     ap.add_argument("--serve-only", action="store_true",
                     help="profiling aid: one served-versus-plain measurement only, printed as JSON")

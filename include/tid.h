@@ -146,7 +146,7 @@ int tid_match_multi(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, 
  * lists of one sub-batch share one allocation, freed with the last of its
  * sets.  q >= 0; on error every outs[j] is NULL.  Errors: TID_ERR_ID if a
  * pattern value is negative.  Synchronises once per sub-batch. */
-#define TID_BATCH_KEYS 2048
+#define TID_BATCH_KEYS 1920
 int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, int q,
                     tid_set **outs);
 

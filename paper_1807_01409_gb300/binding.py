@@ -19,7 +19,7 @@ TID_OK, TID_ERR_ARG, TID_ERR_ID, TID_ERR_OOM, TID_ERR_CAPACITY, TID_ERR_TIMEOUT,
 TID_HOST, TID_DEVICE = 0, 1
 TID_MAX_COLS = 8
 TID_MAX_MULTI = 16
-TID_BATCH_KEYS = 2048
+TID_BATCH_KEYS = 1920
 ERR_NAMES = {0: "TID_OK", 1: "TID_ERR_ARG", 2: "TID_ERR_ID", 3: "TID_ERR_OOM",
              4: "TID_ERR_CAPACITY", 5: "TID_ERR_TIMEOUT", 6: "TID_ERR_CUDA"}
 

@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <tuple>
@@ -47,6 +48,8 @@ constexpr int KB_THREADS = 256;
 constexpr int KB_WARPS = KB_THREADS / 32;
 constexpr int KB_MAX_KIDS = TID_BATCH_KEYS;  // key ids per sub-batch
 constexpr int KB_UNROLL = 8;                 // 32-triple slots loaded per iteration
+constexpr int KB_FILTER_LOG = 13;            // per-column prefilter: 2^13 four-bit entries
+constexpr int KB_FILTER_WORDS = (1 << KB_FILTER_LOG) / 8;
 
 struct __align__(16) Entry {  // one table slot: key values under its mask, mask and key id
     int32_t s, p, o;
@@ -59,13 +62,14 @@ struct __align__(16) Entry {  // one table slot: key values under its mask, mask
 // multiply-high), which depend on every bit of the key.
 struct HashParams {
     uint32_t base, k1, k2, k3, k4;
+    uint32_t f[3];  // prefilter multipliers of s, p, o
 };
 
 inline HashParams hash_params(uint32_t seed) {
     HashParams hp;
     uint64_t z = seed;
-    uint32_t v[5];
-    for (int i = 0; i < 5; ++i) {  // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014)
+    uint32_t v[8];
+    for (int i = 0; i < 8; ++i) {  // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014)
         z += 0x9E3779B97F4A7C15ull;
         uint64_t x = z;
         x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -77,7 +81,28 @@ inline HashParams hash_params(uint32_t seed) {
     hp.k2 = v[2] | 1u;
     hp.k3 = v[3] | 1u;
     hp.k4 = v[4] | 1u;
+    for (int c = 0; c < 3; ++c) hp.f[c] = v[5 + c] | 1u;
     return hp;
+}
+
+// Prefilter entry of a column value (multiplicative hashing, top 13 bits).  Each
+// entry holds one bit per mask that binds the column -- s: masks 1,3,5,7; p:
+// 2,3,6,7; o: 4,5,6,7 -- set when some key of that mask has a value with this
+// entry in the column.
+__host__ __device__ __forceinline__ uint32_t kb_fentry(const HashParams &hp, int c, uint32_t v) {
+    return (v * hp.f[c]) >> (32 - KB_FILTER_LOG);
+}
+
+__host__ __device__ __forceinline__ int kb_fbit(int c, int mask) {  // bit of `mask` in column c's entries
+    return c == 0 ? (mask >> 1) : c == 1 ? ((mask & 1) | ((mask >> 1) & 2)) : (mask & 3);
+}
+
+// masks (bit m) a triple may answer, from its three entries (4-bit each)
+__device__ __forceinline__ uint32_t kb_candidates(uint32_t es, uint32_t ep, uint32_t eo) {
+    const uint32_t cs = 0x55u | ((es & 1u) << 1) | ((es & 2u) << 2) | ((es & 4u) << 3) | ((es & 8u) << 4);
+    const uint32_t cp = 0x33u | ((ep & 3u) << 2) | ((ep & 12u) << 4);
+    const uint32_t co = 0x0Fu | (eo << 4);
+    return cs & cp & co;
 }
 
 __host__ __device__ __forceinline__ uint32_t kb_hash(const HashParams &hp, int mask, uint32_t s, uint32_t p,
@@ -112,31 +137,42 @@ struct BatchArgs {
     uint32_t nb, ns;         // buckets, slots
     const Entry *table;      // ns slots
     const uint16_t *disp;    // nb displacements
+    const uint32_t *filter;  // 3 x KB_FILTER_WORDS words (eight 4-bit entries each)
     uint32_t *counts;        // [warp][kid]: pass 1 writes counts, the scan turns them into bases
     int32_t *arena;          // the lists, list k at arena + off[k]
     const int64_t *off;
+    int abs32;               // the allocation holds < 2^32 rows
 };
 
 __host__ __device__ __forceinline__ size_t kb_disp_bytes(uint32_t nb) { return (sizeof(uint16_t) * nb + 15) / 16 * 16; }
 
 size_t kb_smem_bytes(int kids, uint32_t ns, uint32_t nb) {
-    return sizeof(Entry) * ns + kb_disp_bytes(nb) + sizeof(uint32_t) * KB_WARPS * kids;
+    return sizeof(Entry) * ns + kb_disp_bytes(nb) + sizeof(uint32_t) * 3 * KB_FILTER_WORDS +
+           sizeof(uint32_t) * KB_WARPS * kids;
 }
 
-template <int U, bool WRITE>
+// SKIP: a warp skips a mask's lookups when none of its lanes may answer it
+// (fewer instructions when candidates are rare; a branch per mask that breaks the
+// overlap of the seven lookups when they are common).  The autotuner picks it.
+template <int U, bool WRITE, bool SKIP>
 __global__ void __launch_bounds__(KB_THREADS) k_batch(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char kb_smem[];
     Entry *s_tab = (Entry *)kb_smem;
     uint16_t *s_disp = (uint16_t *)(s_tab + a.ns);
-    uint32_t *s_cnt = (uint32_t *)(kb_smem + sizeof(Entry) * a.ns + kb_disp_bytes(a.nb));
+    uint32_t *s_filt = (uint32_t *)(kb_smem + sizeof(Entry) * a.ns + kb_disp_bytes(a.nb));
+    uint32_t *s_cnt = s_filt + 3 * KB_FILTER_WORDS;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     for (uint32_t i = threadIdx.x; i < a.ns; i += KB_THREADS) s_tab[i] = a.table[i];
     for (uint32_t i = threadIdx.x; i < a.nb; i += KB_THREADS) s_disp[i] = a.disp[i];
+    for (uint32_t i = threadIdx.x; i < 3 * KB_FILTER_WORDS; i += KB_THREADS) s_filt[i] = a.filter[i];
     const int64_t gw = (int64_t)blockIdx.x * KB_WARPS + warp;
     uint32_t *cnt = s_cnt + warp * a.kids;
     uint32_t *row = a.counts + gw * a.kids;
-    for (int k = lane; k < a.kids; k += 32) cnt[k] = WRITE ? row[k] : 0u;
+    // pass 2 cursors: absolute positions in the lists' allocation when it holds
+    // fewer than 2^32 rows (no per-hit offset load), else positions in each list
+    for (int k = lane; k < a.kids; k += 32)
+        cnt[k] = WRITE ? row[k] + (a.abs32 ? (uint32_t)a.off[k] : 0u) : 0u;
     __syncthreads();
     const int64_t lo = gw * a.slice, hi = min(lo + a.slice, a.n);
     for (int64_t b0 = lo; b0 < hi; b0 += 32 * KB_UNROLL) {
@@ -152,28 +188,45 @@ __global__ void __launch_bounds__(KB_THREADS) k_batch(BatchArgs a) {
 #pragma unroll
         for (int u = 0; u < KB_UNROLL; ++u) {
             const int64_t i = b0 + u * 32 + lane;
-            const bool in = i < hi;
-            // every mask's lookup first (independent chains), then the hits
+            // masks this triple may answer (prefilter), and over the warp
+            uint32_t e3[3] = {0u, 0u, 0u};
+            const uint32_t v3[3] = {(uint32_t)vs[u], (uint32_t)vp[u], (uint32_t)vo[u]};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (!(U & (1 << c))) continue;
+                const uint32_t f = kb_fentry(a.hp, c, v3[c]);
+                e3[c] = (s_filt[c * KB_FILTER_WORDS + (f >> 3)] >> ((f & 7u) * 4u)) & 0xFu;
+            }
+            const uint32_t cand = i < hi ? kb_candidates(e3[0], e3[1], e3[2]) : 0u;
+            const uint32_t any = __reduce_or_sync(0xffffffffu, cand);
+            // every candidate mask's lookup first (independent chains), then the hits
             int kid[7];
 #pragma unroll
             for (int m = 1; m < 8; ++m) {
                 kid[m - 1] = -1;
-                if (m & ~U) continue;
+                if ((m & ~U) || (SKIP && !((any >> m) & 1))) continue;
+                // lanes that cannot answer m read slot 0 like the others (a broadcast,
+                // no extra shared-memory wavefront) and keep straight-line code
+                const bool cm = (cand >> m) & 1;
                 const uint32_t h = kb_hash(a.hp, m, vs[u], vp[u], vo[u]);
-                const Entry e = s_tab[kb_slot(a.hp, h, s_disp[kb_bucket(h, a.nb)], a.ns)];
-                const bool hit = in && (e.mask_kid >> 28) == m && (!(m & 1) || e.s == vs[u]) &&
+                const uint32_t d = s_disp[cm ? kb_bucket(h, a.nb) : 0u];
+                const Entry e = s_tab[cm ? kb_slot(a.hp, h, d, a.ns) : 0u];
+                const bool hit = cm && (e.mask_kid >> 28) == m && (!(m & 1) || e.s == vs[u]) &&
                                  (!(m & 2) || e.p == vp[u]) && (!(m & 4) || e.o == vo[u]);
                 kid[m - 1] = hit ? (e.mask_kid & 0x0FFFFFFF) : -1;
             }
 #pragma unroll
             for (int m = 1; m < 8; ++m) {
-                if (m & ~U) continue;
+                if ((m & ~U) || !((any >> m) & 1)) continue;
                 const int k = kid[m - 1];
                 if (!__any_sync(0xffffffffu, k >= 0)) continue;
                 const unsigned peers = __match_any_sync(0xffffffffu, k);
                 if (k >= 0) {
                     const uint32_t c = cnt[k];
-                    if (WRITE) a.arena[a.off[k] + c + __popc(peers & lt)] = (int32_t)i;
+                    if (WRITE) {
+                        const uint32_t r = c + __popc(peers & lt);
+                        a.arena[a.abs32 ? (int64_t)r : a.off[k] + r] = (int32_t)i;
+                    }
                     __syncwarp(peers);
                     if (lane == (unsigned)(__ffs(peers) - 1)) cnt[k] = c + __popc(peers);
                 }
@@ -223,31 +276,33 @@ int sm_count_kb() {
 }
 
 // resident CTAs of both passes with `smem` bytes of dynamic shared memory
-template <int U>
+template <int U, bool SKIP>
 int kb_grid(size_t smem, unsigned *grid) {
     static bool opted = false;
     if (!opted) {
         int optin = 0, dev = 0;
         cudaGetDevice(&dev);
         TID_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
-        TID_TRY_CUDA(cudaFuncSetAttribute(k_batch<U, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+        TID_TRY_CUDA(cudaFuncSetAttribute(k_batch<U, true, SKIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
                      "k_batch smem");
-        TID_TRY_CUDA(cudaFuncSetAttribute(k_batch<U, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+        TID_TRY_CUDA(cudaFuncSetAttribute(k_batch<U, false, SKIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
                      "k_batch smem");
         opted = true;
     }
     int v = 0, w = 0;
-    TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<U, true>, KB_THREADS, smem), "occupancy");
-    TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, k_batch<U, false>, KB_THREADS, smem), "occupancy");
+    TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<U, true, SKIP>, KB_THREADS, smem),
+                 "occupancy");
+    TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, k_batch<U, false, SKIP>, KB_THREADS, smem),
+                 "occupancy");
     if (std::min(v, w) < 1) return fail(TID_ERR_CAPACITY, "tid_match_batch: %zu bytes of shared memory per CTA", smem);
     *grid = (unsigned)(std::min(v, w) * sm_count_kb());
     return TID_OK;
 }
 
-template <int U>
+template <int U, bool SKIP>
 int run_pass(cudaStream_t st, bool write, unsigned grid, size_t smem, const BatchArgs &a) {
-    if (write) k_batch<U, true><<<grid, KB_THREADS, smem, st>>>(a);
-    else k_batch<U, false><<<grid, KB_THREADS, smem, st>>>(a);
+    if (write) k_batch<U, true, SKIP><<<grid, KB_THREADS, smem, st>>>(a);
+    else k_batch<U, false, SKIP><<<grid, KB_THREADS, smem, st>>>(a);
     return launch_check("k_batch");
 }
 
@@ -262,10 +317,80 @@ int run_pass(cudaStream_t st, bool write, unsigned grid, size_t smem, const Batc
         default: { constexpr int u_ = 7; return call; }   \
     }
 
-int grid_of(int U, size_t smem, unsigned *grid) { KB_DISPATCH(U, kb_grid<u_>(smem, grid)) }
+int grid_of(int U, bool skip, size_t smem, unsigned *grid) {
+    if (skip) KB_DISPATCH(U, (kb_grid<u_, true>(smem, grid)))
+    KB_DISPATCH(U, (kb_grid<u_, false>(smem, grid)))
+}
 
-int pass_of(int U, cudaStream_t st, bool write, unsigned grid, size_t smem, const BatchArgs &a) {
-    KB_DISPATCH(U, run_pass<u_>(st, write, grid, smem, a))
+int pass_of(int U, bool skip, cudaStream_t st, bool write, unsigned grid, size_t smem, const BatchArgs &a) {
+    if (skip) KB_DISPATCH(U, (run_pass<u_, true>(st, write, grid, smem, a)))
+    KB_DISPATCH(U, (run_pass<u_, false>(st, write, grid, smem, a)))
+}
+
+// Autotuner.  The two kernel shapes (SKIP) trade instructions against overlap
+// depending on how often lanes are candidates, which depends on the key set and
+// the store.  On the first sub-batch of each (columns read, log2 of key count),
+// the count pass of both shapes is timed on a prefix of the store (CUDA events,
+// best of two) and the faster one is kept for the process.
+struct TuneKey {
+    int device, U, kbits;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(device, U, kbits) < std::tie(o.device, o.U, o.kbits);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, bool> g_tuned;
+
+constexpr int64_t KB_TUNE_TRIPLES = 1 << 25;
+
+// (the passes run on `grid`, the grid the count matrix was sized for)
+int tune_skip(tid_ctx *ctx, int U, int kids, size_t smem, unsigned grid, const BatchArgs &full, bool *skip) {
+    int kbits = 0;
+    while ((1 << kbits) < kids) ++kbits;
+    const TuneKey key{ctx->device, U, kbits};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            *skip = it->second;
+            return TID_OK;
+        }
+    }
+    if (full.n < KB_TUNE_TRIPLES / 4) {  // too little store to tell: the shape for few candidates
+        *skip = true;
+        return TID_OK;
+    }
+    cudaStream_t st = ctx->stream;
+    cudaEvent_t ev[3];
+    for (auto &e : ev) TID_TRY_CUDA(cudaEventCreate(&e), "tuner events");
+    float best[2] = {1e30f, 1e30f};
+    int rc = TID_OK;
+    for (int rep = 0; rep < 2 && rc == TID_OK; ++rep)
+        for (int sk = 0; sk < 2 && rc == TID_OK; ++sk) {
+            unsigned g2 = 0;  // opts the shape into the shared memory it needs
+            rc = grid_of(U, sk == 1, smem, &g2);
+            if (rc != TID_OK) break;
+            BatchArgs a = full;
+            a.n = std::min<int64_t>(full.n, KB_TUNE_TRIPLES);
+            const int64_t GW = (int64_t)grid * KB_WARPS, gran = 32 * KB_UNROLL;
+            a.slice = std::max<int64_t>(gran, ceil_div(ceil_div(a.n, GW), gran) * gran);
+            cudaEventRecord(ev[0], st);
+            rc = pass_of(U, sk == 1, st, false, grid, smem, a);
+            cudaEventRecord(ev[1], st);
+            if (rc == TID_OK) {
+                cudaError_t e = cudaEventSynchronize(ev[1]);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+                if (e != cudaSuccess) rc = fail_cuda(e, "tuner timing");
+                best[sk] = std::min(best[sk], ms);
+            }
+        }
+    for (auto &e : ev) cudaEventDestroy(e);
+    TID_TRY(rc);
+    *skip = best[1] <= best[0];
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = *skip;
+    return TID_OK;
 }
 
 using Key = std::tuple<int, int32_t, int32_t, int32_t>;  // mask, s, p, o (0 where unbound)
@@ -348,9 +473,10 @@ int run_sub_batch(tid_ctx *ctx, const tid_store *st, const std::vector<Key> &key
     int U = 0;
     for (auto &k : keys) U |= std::get<0>(k);
     const uint32_t nb = (uint32_t)std::max(1, (kids + 1) / 2);
-    uint32_t ns = (uint32_t)(kids + kids / 4 + 8);
+    uint32_t ns = (uint32_t)(kids + kids / 8 + 8);
     std::vector<Entry> tab;
     std::vector<uint16_t> disp;
+    std::vector<uint32_t> filt(3 * KB_FILTER_WORDS, 0u);
     HashParams hp{};
     for (uint32_t attempt = 0;; ++attempt) {
         hp = hash_params(0x243F6A88u + attempt);
@@ -358,9 +484,19 @@ int run_sub_batch(tid_ctx *ctx, const tid_store *st, const std::vector<Key> &key
         if (attempt == 64) return fail(TID_ERR_CAPACITY, "tid_match_batch: no key table for %d keys", kids);
         if (attempt % 8 == 7) ns += ns / 8;
     }
+    for (auto &k : keys) {
+        int m;
+        int32_t kv[3];
+        std::tie(m, kv[0], kv[1], kv[2]) = k;
+        for (int c = 0; c < 3; ++c)
+            if (m & (1 << c)) {
+                const uint32_t f = kb_fentry(hp, c, (uint32_t)kv[c]);
+                filt[c * KB_FILTER_WORDS + (f >> 3)] |= (1u << kb_fbit(c, m)) << ((f & 7u) * 4u);
+            }
+    }
     const size_t smem = kb_smem_bytes(kids, ns, nb);
     unsigned grid = 0;
-    TID_TRY(grid_of(U, smem, &grid));
+    TID_TRY(grid_of(U, true, smem, &grid));
     const int64_t GW = (int64_t)grid * KB_WARPS;
     const int64_t gran = 32 * KB_UNROLL;
     const int64_t slice = std::max<int64_t>(gran, ceil_div(ceil_div(st->n, GW), gran) * gran);
@@ -383,14 +519,19 @@ int run_sub_batch(tid_ctx *ctx, const tid_store *st, const std::vector<Key> &key
     Scratch s(ctx);
     Entry *d_tab = nullptr;
     uint16_t *d_disp = nullptr;
+    uint32_t *d_filt = nullptr;
     uint32_t *counts = nullptr;
     int64_t *d_off = nullptr;
     if ((rc = s.get(&d_tab, ns)) != TID_OK || (rc = s.get(&d_disp, nb)) != TID_OK ||
+        (rc = s.get(&d_filt, 3 * KB_FILTER_WORDS)) != TID_OK ||
         (rc = s.get(&counts, (size_t)kids * GW)) != TID_OK || (rc = s.get(&d_off, kids)) != TID_OK)
         return give_up(rc);
     cudaError_t ce = cudaMemcpyAsync(d_tab, tab.data(), sizeof(Entry) * ns, cudaMemcpyHostToDevice, stream);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(d_disp, disp.data(), sizeof(uint16_t) * nb, cudaMemcpyHostToDevice, stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_filt, filt.data(), sizeof(uint32_t) * 3 * KB_FILTER_WORDS, cudaMemcpyHostToDevice,
+                             stream);
     if (ce != cudaSuccess) return give_up(fail_cuda(ce, "batch table"));
     BatchArgs a{};
     a.S = st->s;
@@ -404,8 +545,11 @@ int run_sub_batch(tid_ctx *ctx, const tid_store *st, const std::vector<Key> &key
     a.ns = ns;
     a.table = d_tab;
     a.disp = d_disp;
+    a.filter = d_filt;
     a.counts = counts;
-    if ((rc = pass_of(U, stream, false, grid, smem, a)) != TID_OK) return give_up(rc);
+    bool skip = true;
+    if ((rc = tune_skip(ctx, U, kids, smem, grid, a, &skip)) != TID_OK) return give_up(rc);
+    if ((rc = pass_of(U, skip, stream, false, grid, smem, a)) != TID_OK) return give_up(rc);
     k_batch_scan<<<(unsigned)ceil_div(kids, 32), 256, 0, stream>>>(counts, GW, kids, d_rows);
     if ((rc = launch_check("k_batch_scan")) != TID_OK) return give_up(rc);
     std::vector<int64_t> tot(kids), off(kids);
@@ -425,7 +569,8 @@ int run_sub_batch(tid_ctx *ctx, const tid_store *st, const std::vector<Key> &key
     if (ce != cudaSuccess) return give_up(fail_cuda(ce, "batch offsets"));
     a.arena = arena;
     a.off = d_off;
-    if ((rc = pass_of(U, stream, true, grid, smem, a)) != TID_OK) return give_up(rc);
+    a.abs32 = total < ((int64_t)1 << 32) ? 1 : 0;
+    if ((rc = pass_of(U, skip, stream, true, grid, smem, a)) != TID_OK) return give_up(rc);
     for (int k = 0; k < kids; ++k) {
         rc = set_view(ctx, sb, arena + off[k], d_rows + k, tot[k], &sets[k]);
         if (rc != TID_OK) {
