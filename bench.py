@@ -605,7 +605,9 @@ def measure_batch(tb, ctx, stream, peak, n=BATCH_TRIPLES, m=BATCH_QUERIES, with_
     torch.cuda.empty_cache()
     bms = statistics.median(batch_ms)
     return {
-        "workload": BATCH_WORKLOAD, "n_triples": n, "queries": m, "distinct_keys": len(dk),
+        "workload": BATCH_WORKLOAD if n == BATCH_TRIPLES else f"university-{n}: profiling size, not the "
+                                                              f"batched workload",
+        "n_triples": n, "queries": m, "distinct_keys": len(dk),
         "sub_batches": (len(dk) + tb.TID_BATCH_KEYS - 1) // tb.TID_BATCH_KEYS,
         "result_rows": int(sizes.sum()), "result_rows_distinct_keys": int(sum(distinct.values())),
         "results_match_tallies": hits_ok,
