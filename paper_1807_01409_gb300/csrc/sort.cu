@@ -228,6 +228,86 @@ __global__ void k_unpack(const K *__restrict__ keys, int k, int64_t n, PackSpec 
     }
 }
 
+// Small sets (n <= SMALL_N rows) in one CTA: pack, bitonic sort in shared memory
+// (padded to a power of two with the largest key), drop adjacent duplicates if
+// asked (flags + block scan), unpack, and write the row count -- one launch
+// instead of the passes of the device-wide sort.
+constexpr int SMALL_N = 4096;
+constexpr int SMALL_THREADS = 1024;
+
+template <typename K>
+__global__ void __launch_bounds__(SMALL_THREADS) k_small_canonical(ColPtrs cols, int k, int n, PackSpec ps,
+                                                                   int dedupe, MutColPtrs out,
+                                                                   int64_t *__restrict__ d_rows,
+                                                                   int64_t *__restrict__ h_rows) {
+    __shared__ K sk[SMALL_N];
+    __shared__ uint32_t s_warp[SMALL_THREADS / 32];
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += SMALL_THREADS) {
+        K key = ~(K)0;
+        if (i < n) {
+            key = 0;
+            for (int c = 0; c < k; ++c)
+                if (ps.mask[c]) key |= (K)(order_key(cols.c[c][i]) - ps.min[c]) << ps.shift[c];
+        }
+        sk[i] = key;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < P / 2; t += SMALL_THREADS) {
+                const int i = 2 * t - (t & (stride - 1));  // lower index of the pair
+                const int j = i + stride;
+                const bool up = (i & size) == 0;
+                const K a = sk[i], b = sk[j];
+                if ((a > b) == up) {
+                    sk[i] = b;
+                    sk[j] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // each thread owns up to SMALL_N / SMALL_THREADS consecutive sorted rows
+    constexpr int PER = SMALL_N / SMALL_THREADS;
+    const int b = threadIdx.x * PER;
+    bool keep[PER];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = b + q;
+        keep[q] = i < n && (!dedupe || i == 0 || sk[i] != sk[i - 1]);
+        cnt += keep[q];
+    }
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if ((int)lane >= d) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t base = 0;
+    for (unsigned w = 0; w < warp; ++w) base += s_warp[w];
+    uint32_t pos = base + x - cnt;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        if (!keep[q]) continue;
+        const K key = sk[b + q];
+        for (int c = 0; c < k; ++c) {
+            const uint32_t f = ps.mask[c] ? (uint32_t)((key >> ps.shift[c]) & ps.mask[c]) : 0u;
+            out.c[c][pos] = (int32_t)((f + ps.min[c]) ^ 0x80000000u);
+        }
+        ++pos;
+    }
+    if (threadIdx.x == SMALL_THREADS - 1) {
+        *d_rows = pos;
+        *h_rows = pos;
+    }
+}
+
 __global__ void k_gather(ColPtrs in, int k, const int32_t *__restrict__ perm, int64_t n, MutColPtrs out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = perm[i];
@@ -351,6 +431,19 @@ template <typename K>
 static int canonical_packed(tid_ctx *ctx, const int32_t *const *cols, int k, int64_t n, bool dedupe,
                             const PackSpec &ps, int total_bits, tid_set *set) {
     cudaStream_t st = ctx->stream;
+    if (n <= SMALL_N) {
+        ColPtrs cp{};
+        MutColPtrs op{};
+        for (int c = 0; c < k; ++c) {
+            cp.c[c] = cols[c];
+            op.c[c] = set->col[c];
+        }
+        k_small_canonical<K><<<1, SMALL_THREADS, 0, st>>>(cp, k, (int)n, ps, dedupe ? 1 : 0, op, set->d_rows,
+                                                          set->slot.dev);
+        TID_TRY(launch_check("k_small_canonical"));
+        if (!dedupe) set->rows_known = n;
+        return TID_OK;
+    }
     Scratch s(ctx);
     const unsigned tiles = (unsigned)ceil_div(n, RS_TILE);
     K *ka = nullptr, *kb = nullptr;
