@@ -568,6 +568,8 @@ def measure_batch(tb, ctx, stream, peak, n=BATCH_TRIPLES, m=BATCH_QUERIES, with_
         for h in hs:
             tb.tid_set_free(h)
 
+    two = _two_pattern_batch(tb, s, p, o)
+
     plist = [tb.as_pattern(tuple(int(x) for x in k)) for k in keys]
     for q in plist[:64]:
         tb.tid_set_free(tb.tid_match(ctx, store, q))
@@ -622,7 +624,33 @@ def measure_batch(tb, ctx, stream, peak, n=BATCH_TRIPLES, m=BATCH_QUERIES, with_
                 "note": "whole call: both passes of every sub-batch, the scans of counts, the "
                         "host synchronisation between passes and set creation"},
         "cpu_baseline": oracle,
+        "two_pattern": two,
     }
+
+
+def _two_pattern_batch(tb, s, p, o, m=1024):
+    """Two-pattern queries (star joins of two bound (predicate, object) pairs of one
+    subject), all arriving at once, through the request server: batched (one search
+    for the wave, then each join) against one request at a time, each searching alone."""
+    kinds, plans, _ = synth.serving_requests(s, p, o, m=m, seed=synth.QUERY_SEED + 4096, mix=(0.0, 1.0, 0.0))
+    prepared = [tb.Server.request(k, x) for k, x in zip(kinds, plans)]
+    out = {"queries": m, "shape": "(?x p1 o1) JOIN (?x p2 o2)"}
+    for name, kw in (("batched", dict(workers=2, max_wave=4096, batch_scans=True)),
+                     ("plain", dict(workers=1, max_wave=1, batch_scans=False))):
+        with tb.Server(s, p, o, budget_bytes=SERVE_BUDGET, **kw) as srv:
+            for rid in [srv.submit(x) for x in prepared[:16]]:
+                srv.wait(rid)
+                srv.release(rid)
+            t0 = tb.Server.now_ns()
+            ids = [srv.submit(x, t0) for x in prepared]
+            lat = []
+            for rid in ids:
+                srv.wait(rid)
+                lat.append(srv.result(rid)[3] / 1e6)
+            span = max(lat) / 1e3
+        out[name] = {"ms": span * 1e3, "queries_per_s": m / span, "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99)}
+    out["speedup_queries_per_s"] = out["batched"]["queries_per_s"] / out["plain"]["queries_per_s"]
+    return out
 
 
 SERVE_TRIPLES = 1_000_000_000

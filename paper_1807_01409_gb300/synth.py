@@ -659,7 +659,8 @@ def serving_requests(s, p, o, m: int = 4000, seed: int = QUERY_SEED, mix=SERVE_M
     for j, (kind, _, r) in enumerate(PRED_KIND):
         if kind == "ent" or (kind == "lit" and r >= 5):
             selective.add(pred_base + j)
-    idx_q = iter(batch_queries(s, p, o, m=int((kinds == 0).sum()), seed=seed + 1, lo=1.0, hi=hi_index))
+    n_index = int((kinds == 0).sum())
+    idx_q = iter(batch_queries(s, p, o, m=n_index, seed=seed + 1, lo=1.0, hi=hi_index) if n_index else [])
     s_sorted, order = torch.sort(s)
 
     def triples_of(s0):
