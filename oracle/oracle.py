@@ -22,6 +22,12 @@ Paper passages followed (TripleID-Q, IEEE TPDS 2018):
 * ``execute``      -- Section 4.3 / Fig. "Integration of several operations": per
                       subquery search+extract (filter fused), joins left to right,
                       distinct results.
+* ``entail``       -- Section 5, Table "RDFS Entailment rules" (R2, R3, R5, R7, R9,
+                      R11) and the Rule-11 walk-through: search the schema premise,
+                      keep its distinct join terms, search the store for the triples
+                      whose term at the join position is one of them (the keysArray
+                      of the second GPUSearch), join the two result vectors on the
+                      shared term, keep the distinct conclusions.
 
 Readings where the paper is silent: 0 (unbound, e.g. union padding) never joins
 and never passes a filter; every result is a set in canonical order (rows
@@ -328,3 +334,72 @@ def execute(s, p, o, plan) -> TupleSet:
         return r
 
     return ev(len(plan) - 1)
+
+
+# ---------------------------------------------------------------------------
+# RDFS entailment (Section 5)
+# ---------------------------------------------------------------------------
+
+# The six two-premise rules of the table, written as premise patterns over
+# variable names and fixed vocabulary terms, the shared variable, and the
+# conclusion.  Premise 1 is the schema triple (searched first), premise 2 the
+# data triple (searched with the distinct values of the shared variable).
+ENTAIL_RULES = {
+    2: {"schema": ("p", "domain", "D"), "data": ("s", "p", "o"), "on": "p", "then": ("s", "type", "D")},
+    3: {"schema": ("p", "range", "R"), "data": ("s", "p", "o"), "on": "p", "then": ("o", "type", "R")},
+    5: {"schema": ("p", "subprop", "q"), "data": ("q", "subprop", "r"), "on": "q", "then": ("p", "subprop", "r")},
+    7: {"schema": ("p", "subprop", "q"), "data": ("s", "p", "o"), "on": "p", "then": ("s", "q", "o")},
+    9: {"schema": ("x", "subclass", "y"), "data": ("s", "type", "x"), "on": "x", "then": ("s", "type", "y")},
+    11: {"schema": ("x", "subclass", "y"), "data": ("y", "subclass", "z"), "on": "y", "then": ("x", "subclass", "z")},
+}
+VOCAB_TERMS = ("type", "domain", "range", "subprop", "subclass")
+
+
+def entail(s, p, o, rule: int, vocab: dict):
+    """Conclusions of one rule over the store, as a set of (s, p, o) rows (vars
+    0, 1, 2), plus the step counts of the paper's table: res1 (matches of the
+    schema premise), dist1 (its distinct join terms), res2 (store triples found
+    by the second search), dist2 (their distinct join terms), all (conclusions)."""
+    s, p, o = _col(s), _col(p), _col(o)
+    r = ENTAIL_RULES[rule]
+    names = {}
+
+    def pattern(tpl):
+        key, var = [], []
+        for j, t in enumerate(tpl):
+            if t in VOCAB_TERMS:
+                key.append(int(vocab[t]))
+                var.append(-1)
+            else:
+                names.setdefault(t, len(names))
+                key.append(0)
+                var.append(names[t])
+        return key, var
+
+    k1, v1 = pattern(r["schema"])
+    k2, v2 = pattern(r["data"])
+    on = names[r["on"]]
+    # step 1: the schema premise; its distinct join terms become the keys of step 2
+    idx1 = match(s, p, o, k1)
+    t1 = bind(s, p, o, k1, v1, idx1)
+    keys = np.unique(t1.rows[:, t1.vars.index(on)]) if t1.n else np.zeros(0, np.int32)
+    # step 2: the triples of premise 2 whose term at the join slot is one of the keys
+    slot = r["data"].index(r["on"])
+    cand = match(s, p, o, k2)
+    col = (s, p, o)[slot]
+    idx2 = cand[np.isin(col[cand], keys)] if cand.shape[0] else cand
+    t2 = bind(s, p, o, k2, v2, idx2)
+    dist2 = int(np.unique(t2.rows[:, t2.vars.index(on)]).shape[0]) if t2.n else 0
+    # combine: join on the shared term, the conclusion's terms, distinct
+    j = join(t1, t2)
+    cols = []
+    for t in r["then"]:
+        if t in VOCAB_TERMS:
+            cols.append(np.full(j.n, int(vocab[t]), np.int32))
+        else:
+            cols.append(j.rows[:, j.vars.index(names[t])])
+    rows = np.stack(cols, axis=1) if j.n else np.zeros((0, 3), np.int32)
+    out = _set((0, 1, 2), rows)
+    stats = {"res1": int(idx1.shape[0]), "dist1": int(keys.shape[0]), "res2": int(idx2.shape[0]),
+             "dist2": dist2, "all": out.n}
+    return out, stats

@@ -286,6 +286,77 @@ def pin_project(o):
     assert pr.vars == (2, 0) and pr.rows.tolist() == [list(x) for x in want]
 
 
+# RDFS rules of the paper's entailment table (Section 5), for the brute force:
+# two premises and a conclusion over variable names and vocabulary terms
+_RULES_BF = {
+    2: ((("p", "domain", "D"), ("s", "p", "o")), ("s", "type", "D")),
+    3: ((("p", "range", "R"), ("s", "p", "o")), ("o", "type", "R")),
+    5: ((("p", "subprop", "q"), ("q", "subprop", "r")), ("p", "subprop", "r")),
+    7: ((("p", "subprop", "q"), ("s", "p", "o")), ("s", "q", "o")),
+    9: ((("x", "subclass", "y"), ("s", "type", "x")), ("s", "type", "y")),
+    11: ((("x", "subclass", "y"), ("y", "subclass", "z")), ("x", "subclass", "z")),
+}
+
+
+def _unify(tpl, triple, env, vocab):
+    env = dict(env)
+    for term, val in zip(tpl, triple):
+        if term in vocab:
+            if vocab[term] != val:
+                return None
+        elif term in env:
+            if env[term] != val:
+                return None
+        else:
+            env[term] = val
+    return env
+
+
+def entail_bruteforce(S, P, O, rule, vocab):
+    """Conclusions of a rule by trying every ordered pair of stored triples as
+    (premise 1, premise 2) instances."""
+    G = list(zip(S.tolist(), P.tolist(), O.tolist()))
+    (t1, t2), then = _RULES_BF[rule]
+    out = set()
+    for a in G:
+        e1 = _unify(t1, a, {}, vocab)
+        if e1 is None:
+            continue
+        for b in G:
+            e2 = _unify(t2, b, e1, vocab)
+            if e2 is not None:
+                out.add(tuple(vocab[t] if t in vocab else e2[t] for t in then))
+    return sorted(out)
+
+
+def pin_entail_golden(o):
+    """Section 5, Rule (11) walk-through through the rule evaluator: 4 schema
+    matches, 3 distinct terms (the three keys of the second search), 2 matches of
+    the second search, 2 conclusions (76, 84, 78) and (76, 84, 77)."""
+    g = json.load(open(os.path.join(GOLDEN, "rule11_worked_example.json")))
+    st = np.array(g["store"], np.int32)
+    vocab = {"type": 1, "domain": 2, "range": 3, "subprop": 4, "subclass": 84}
+    out, stats = o.entail(st[:, 0].copy(), st[:, 1].copy(), st[:, 2].copy(), 11, vocab)
+    assert out.vars == (0, 1, 2)
+    assert sorted(map(tuple, out.rows.tolist())) == sorted((x, 84, z) for x, z in g["result_xz"])
+    assert stats["res1"] == sum(g["step1"]["flags"]) and stats["dist1"] == len(g["step2"]["keys"])
+    assert stats["res2"] == sum(g["step2"]["flags"]) and stats["all"] == len(g["result_xz"])
+
+
+def pin_entail_bruteforce(o):
+    """Every rule on small random graphs whose IDs include the vocabulary terms:
+    the conclusions equal the pairwise brute force."""
+    vocab = {"type": 1, "domain": 2, "range": 3, "subprop": 4, "subclass": 5}
+    for seed in range(6):
+        S, P, O = tiny_graph(100 + seed, 90, ids=7)
+        for rule in _RULES_BF:
+            out, stats = o.entail(S, P, O, rule, vocab)
+            want = entail_bruteforce(S, P, O, rule, vocab)
+            assert out.rows.tolist() == [list(t) for t in want], (seed, rule)
+            assert stats["all"] == len(want)
+
+
 ALL_PINS = [pin_golden_rule11, pin_match_bruteforce, pin_match_tallies,
             pin_bind_join_bruteforce, pin_join_cross_product, pin_union_laws,
-            pin_filter_algebra, pin_canonical, pin_project]
+            pin_filter_algebra, pin_canonical, pin_project, pin_entail_golden,
+            pin_entail_bruteforce]

@@ -51,7 +51,7 @@ def test_pins_catch_planted_mistake(orc, mut, tmp_path):
         for pin in pins.ALL_PINS:
             try:
                 pin(orc)
-            except AssertionError:
+            except Exception:  # a pin that fails or breaks on the mutant has caught it
                 failed.append(pin.__name__)
     assert failed, f"no pin caught mutation {mut}: {new!r}"
 
@@ -100,3 +100,38 @@ def test_execute_plans_against_solution_mappings(orc):
     b = pins.solutions(S, P, O, [((0, 2, 0), (Y, -1, Z))], (Y, Z))
     want = sorted({(x, y, 0) for x, y in a} | {(0, y, z) for y, z in b})
     assert r.vars == (X, Y, Z) and r.rows.tolist() == [list(w) for w in want]
+
+
+# planted mistakes in the Python rule evaluator (oracle.py), caught by the entailment pins
+ENTAIL_MUTATIONS = [
+    ("keys = np.unique(t1.rows[:, t1.vars.index(on)])", "keys = np.unique(t1.rows[:, 0])"),  # wrong column
+    ("idx2 = cand[np.isin(col[cand], keys)] if cand.shape[0] else cand", "idx2 = cand"),  # no key restriction
+    ('slot = r["data"].index(r["on"])', "slot = 0"),                                         # wrong join slot
+    ('for t in r["then"]:', 'for t in reversed(r["then"]):'),                                # conclusion reversed
+]
+
+
+@pytest.mark.parametrize("mut", range(len(ENTAIL_MUTATIONS)))
+def test_entail_pins_catch_planted_mistake(orc, mut, tmp_path):
+    import importlib.util
+    old, new = ENTAIL_MUTATIONS[mut]
+    src = open(orc.__file__).read()
+    assert old in src, "mutation site vanished from oracle.py"
+    bad = tmp_path / "oracle_entail_mut.py"
+    bad.write_text(src.replace(old, new, 1))
+    import sys
+    spec = importlib.util.spec_from_file_location("oracle_entail_mut", bad)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules["oracle_entail_mut"] = mod
+    try:
+        spec.loader.exec_module(mod)
+    finally:
+        sys.modules.pop("oracle_entail_mut", None)
+    mod._SRC, mod._BUILD, mod._SO, mod._lib = orc._SRC, orc._BUILD, orc._SO, None
+    failed = []
+    for pin in (pins.pin_entail_golden, pins.pin_entail_bruteforce):
+        try:
+            pin(mod)
+        except Exception:
+            failed.append(pin.__name__)
+    assert failed, f"no pin caught entailment mutation {mut}: {new!r}"
