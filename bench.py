@@ -12,6 +12,7 @@ Beside the headline, "rows" times every other row of the path (multi-pattern
 scan, bind+filter, sort, joins, union, filter, plan execution) on the same
 store, and "batch" times 4096 single-pattern queries on a 500M-triple store
 batched (tid_match_batch) against one launch per query on the same GPU, and
+"entail" runs the six RDFS rules on the store plus its schema, and
 "serve" runs a Poisson request stream through the request server (continuous
 batching, admission by estimated bytes) against the same server taking one
 request at a time with one search launch per request.
@@ -478,6 +479,10 @@ def run_ours(args, rank, world, local):
     tb.tid_store_free(store)
     del cols
     torch.cuda.empty_cache()
+    entail = None
+    if not args.no_entail:
+        entail = measure_entail(tb, ctx, stream, store_np, _peaks()[0],
+                                with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     batch = None
     if not args.no_batch:
         batch = measure_batch(tb, ctx, stream, _peaks()[0],
@@ -510,6 +515,7 @@ def run_ours(args, rank, world, local):
             "clocks": clk.summary(),
             "cpu_baseline": base,
             "rows": rows,
+            "entail": entail,
             "batch": batch,
             "serve": serve,
         }
@@ -650,6 +656,65 @@ def _two_pattern_batch(tb, s, p, o, m=1024):
             span = max(lat) / 1e3
         out[name] = {"ms": span * 1e3, "queries_per_s": m / span, "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99)}
     out["speedup_queries_per_s"] = out["batched"]["queries_per_s"] / out["plain"]["queries_per_s"]
+    return out
+
+
+def measure_entail(tb, ctx, stream, store_np, peak, with_oracle=True, oracle_n=20_000_000):
+    """The six RDFS rules (tid_entail) on the university store plus its schema:
+    per rule the call's time (CUDA events; the call synchronises), the paper's step
+    counts, and the algorithmic bytes of its two store passes over that time: the
+    schema search reads P (4n), the keyed search reads P for every triple (the fixed
+    predicate or the key itself, 4n) and the other columns of the triples it keeps
+    (at most 8 bytes each of res2).  The oracle runs the same rules on a smaller store
+    of the same recipe, beside the GPU on that store."""
+    import torch
+
+    def run(st_np):
+        vocab = synth.rdfs_vocab(st_np.meta["subjects"])
+        cols = [torch.from_numpy(c).cuda() for c in (st_np.s, st_np.p, st_np.o)]
+        torch.cuda.synchronize()
+        st = tb.tid_load(ctx, *cols, copy=0)
+        res = {}
+        for rule in tb.RULES:
+            h, _ = tb.tid_entail(ctx, st, rule, vocab)  # warm-up
+            tb.tid_set_free(h)
+            ms = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h, stats = tb.tid_entail(ctx, st, rule, vocab)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                tb.tid_set_free(h)
+            t = statistics.median(ms)
+            scan_bytes = 8 * st_np.n + 8 * stats["res2"]
+            res[f"R{rule}"] = {"gpu_ms": round(t, 3), **stats,
+                               "store_pass_bytes": scan_bytes,
+                               "store_pass_GBps": round(scan_bytes / (t / 1e3) / 1e9, 1),
+                               "frac_of_measured_peak": round(scan_bytes / (t / 1e3) / 1e9 / peak, 4)}
+        tb.tid_store_free(st)
+        del cols
+        return res, vocab
+
+    full = synth.with_schema(store_np)
+    out = {"workload": f"university-{store_np.n} + its RDFS schema ({full.meta['schema_triples']} triples)",
+           "rules": run(full)[0]}
+    if with_oracle:
+        from oracle import oracle as orc
+        orc.build()
+        small = synth.with_schema(synth.university_store(oracle_n))
+        g_small, vocab = run(small)
+        cmp_ = {}
+        for rule in tb.RULES:
+            t0 = time.perf_counter()
+            orc.entail(small.s, small.p, small.o, rule, vocab)
+            cmp_[f"R{rule}"] = {"oracle_ms": round((time.perf_counter() - t0) * 1e3, 1),
+                                "gpu_ms": g_small[f"R{rule}"]["gpu_ms"]}
+            cmp_[f"R{rule}"]["speedup_vs_oracle"] = round(cmp_[f"R{rule}"]["oracle_ms"] /
+                                                          max(cmp_[f"R{rule}"]["gpu_ms"], 1e-6), 1)
+        out["oracle_comparison"] = {"n_triples": small.n, "cores": 1, "kind": "oracle", "rules": cmp_}
+    torch.cuda.empty_cache()
     return out
 
 
@@ -798,6 +863,7 @@ def main():
     ap.add_argument("--batch-triples", type=int, default=BATCH_TRIPLES,
                     help="store size of --batch-only (default: the 500M workload; smaller only for profiling)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-requests row")
+    ap.add_argument("--no-entail", action="store_true", help="skip the RDFS entailment row")
     ap.add_argument("--serve-only", action="store_true",
                     help="profiling aid: one served-versus-plain measurement only, printed as JSON")
     ap.add_argument("--triples", type=int, default=N_TRIPLES,

@@ -308,6 +308,49 @@ int tid_set_to_host(tid_set *set, int32_t *buf, int64_t cap_rows, int64_t *rows_
 int tid_set_free(tid_set *set);
 
 /* ------------------------------------------------------------------------ */
+/* RDFS entailment -- Section 5, Table "RDFS Entailment rules"               */
+/* ------------------------------------------------------------------------ */
+
+/* IDs of the vocabulary terms the rules name. */
+typedef struct {
+    int32_t type;             /* rdf:type */
+    int32_t domain;           /* rdfs:domain */
+    int32_t range;            /* rdfs:range */
+    int32_t sub_property_of;  /* rdfs:subPropertyOf */
+    int32_t sub_class_of;     /* rdfs:subClassOf */
+} tid_rdfs_vocab;
+
+/* the paper's step counts for one rule (its columns #Res1, #Dist1, #Res2,
+ * #Dist2 and All): matches of the schema premise, its distinct join terms,
+ * store triples found by the second search, their distinct join terms, and
+ * distinct conclusions */
+typedef struct {
+    int64_t res1, dist1, res2, dist2, all;
+} tid_entail_stats;
+
+/* rules: 2 (s p o, p domain D => s type D), 3 (s p o, p range R => o type R),
+ * 5 (p subPropertyOf q, q subPropertyOf r => p subPropertyOf r),
+ * 7 (s p o, p subPropertyOf q => s q o), 9 (s type x, x subClassOf y =>
+ * s type y), 11 (x subClassOf y, y subClassOf z => x subClassOf z) */
+#define TID_RULE_R2  2
+#define TID_RULE_R3  3
+#define TID_RULE_R5  5
+#define TID_RULE_R7  7
+#define TID_RULE_R9  9
+#define TID_RULE_R11 11
+
+/* The conclusions of one rule over the store, as the paper evaluates it:
+ * search the schema premise, take the distinct terms at its join position,
+ * search the store for the triples of the other premise whose term at the join
+ * position is one of them (one pass: a hash probe per triple), join the two
+ * result vectors on that term, keep the distinct conclusions.  *out receives a
+ * canonical three-column set (s, p, o) labelled 0, 1, 2; conclusions already in
+ * the store are included.  stats may be NULL.  Errors: TID_ERR_ARG (unknown rule,
+ * null vocab), TID_ERR_ID (a vocabulary ID <= 0).  Synchronises. */
+int tid_entail(tid_ctx *ctx, const tid_store *st, int rule, const tid_rdfs_vocab *vocab,
+               tid_set **out, tid_entail_stats *stats);
+
+/* ------------------------------------------------------------------------ */
 /* serving: a request loop over a resident store                             */
 /* ------------------------------------------------------------------------ */
 /*

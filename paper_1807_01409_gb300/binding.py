@@ -48,6 +48,18 @@ class tid_server_stats(C.Structure):
 TID_REQ_INDEX, TID_REQ_PLAN = 1, 2
 
 
+class tid_rdfs_vocab(C.Structure):
+    _fields_ = [("type", C.c_int32), ("domain", C.c_int32), ("range", C.c_int32),
+                ("sub_property_of", C.c_int32), ("sub_class_of", C.c_int32)]
+
+
+class tid_entail_stats(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in ("res1", "dist1", "res2", "dist2", "all")]
+
+
+RULES = (2, 3, 5, 7, 9, 11)
+
+
 class tid_pred(C.Structure):
     _fields_ = [("var", C.c_int32), ("op", C.c_int32), ("a", C.c_int32), ("b", C.c_int32)]
 
@@ -120,6 +132,8 @@ def lib():
         "tid_exec": (C.c_int, [_vp, _vp, C.POINTER(tid_plan_node), C.c_int, C.POINTER(_vp)]),
         "tid_match_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, C.c_int64, tid_pattern, _vp, C.c_int64,
                                         _vp]),
+        "tid_entail": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(tid_rdfs_vocab), C.POINTER(_vp),
+                                 C.POINTER(tid_entail_stats)]),
         "tid_server_create": (C.c_int, [C.c_int, _vp, _vp, _vp, C.c_int64, C.POINTER(tid_server_config),
                                         C.POINTER(_vp)]),
         "tid_server_now_ns": (C.c_int64, []),
@@ -426,6 +440,16 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+def tid_entail(ctx, st, rule, vocab):
+    """Conclusions of RDFS rule `rule` (2, 3, 5, 7, 9, 11) as a 3-column set (s, p, o),
+    and the step counts; vocab: dict with type, domain, range, subprop, subclass IDs."""
+    v = tid_rdfs_vocab(int(vocab["type"]), int(vocab["domain"]), int(vocab["range"]),
+                       int(vocab["subprop"]), int(vocab["subclass"]))
+    out, stats = _vp(), tid_entail_stats()
+    _check(lib().tid_entail(ctx, st, int(rule), C.byref(v), C.byref(out), C.byref(stats)), "tid_entail")
+    return out, {f: getattr(stats, f) for f, _ in tid_entail_stats._fields_}
 
 
 class Server:

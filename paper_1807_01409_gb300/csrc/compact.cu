@@ -124,6 +124,45 @@ struct UniqueRow {  // rows in perm order; keep the first of each run of equal r
     }
 };
 
+struct SemiJoinRow {  // store triple r, kept when a slot holds a fixed term and another slot's
+                      // term is in a key set (open-addressing table of keys, 0 = empty)
+    const int32_t *S, *P, *O;
+    int need;                   // slots read (bit 0 s, 1 p, 2 o)
+    int fixed_slot;             // -1: none
+    int32_t fixed_val;
+    int key_slot;
+    const int32_t *table;
+    uint32_t tmask;             // table size - 1 (a power of two)
+    int k;
+    int8_t src[TID_MAX_COLS];   // slot giving output column c
+    __device__ __forceinline__ const int32_t *column(int slot) const { return slot == 0 ? S : (slot == 1 ? P : O); }
+    // the fixed and the key column first; the other columns only for rows that pass
+    __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
+        if (fixed_slot >= 0 && column(fixed_slot)[r] != fixed_val) return false;
+        const int32_t key = column(key_slot)[r];
+        if (key == 0) return false;
+        uint32_t h = ((uint32_t)key * 0x9E3779B1u) & tmask;
+        bool found = false;
+        for (uint32_t probe = 0; probe <= tmask; ++probe) {  // the table is at most half full
+            const int32_t e = __ldg(table + h);
+            if (e == key) {
+                found = true;
+                break;
+            }
+            if (e == 0) break;
+            h = (h + 1) & tmask;
+        }
+        if (!found) return false;
+        const int32_t t0 = (need & 1) ? S[r] : 0;
+        const int32_t t1 = (need & 2) ? P[r] : 0;
+        const int32_t t2 = (need & 4) ? O[r] : 0;
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < k) v[c] = src[c] == 0 ? t0 : (src[c] == 1 ? t1 : t2);
+        return true;
+    }
+};
+
 template <typename K>
 struct PackedUniqueRow {  // sorted packed keys; keep the first of each run of equal keys
     const K *keys;
@@ -355,6 +394,28 @@ int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, cons
     OutCols oc{};
     for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
     return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev, mm);
+}
+
+int compact_semijoin(tid_ctx *ctx, const tid_store *st, int fixed_slot, int32_t fixed_val, int key_slot,
+                     const int32_t *table, uint32_t tmask, const int8_t *src, tid_set *out) {
+    SemiJoinRow r{};
+    r.S = st->s;
+    r.P = st->p;
+    r.O = st->o;
+    r.fixed_slot = fixed_slot;
+    r.fixed_val = fixed_val;
+    r.key_slot = key_slot;
+    r.table = table;
+    r.tmask = tmask;
+    r.k = out->k;
+    r.need = (fixed_slot >= 0 ? 1 << fixed_slot : 0) | (1 << key_slot);
+    for (int c = 0; c < out->k; ++c) {
+        r.src[c] = src[c];
+        r.need |= 1 << src[c];
+    }
+    OutCols oc{};
+    for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
+    return launch_compact(ctx, r, st->n, out->k, oc, out->cap, out->d_rows, out->slot.dev);
 }
 
 int compact_filter(tid_ctx *ctx, const tid_set *in, int64_t n, const Pred *preds, int n_preds, tid_set *out) {

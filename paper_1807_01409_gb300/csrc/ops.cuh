@@ -44,6 +44,10 @@ int scan_exclusive_u32(tid_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t 
 int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, const int32_t *idx, int64_t n,
                  const Pred *preds, int n_preds, tid_set *out, uint32_t *mm);
 int compact_filter(tid_ctx *ctx, const tid_set *in, int64_t n, const Pred *preds, int n_preds, tid_set *out);
+// store triples (in store order) whose fixed_slot holds fixed_val (fixed_slot -1:
+// any) and whose key_slot term is in the key table; output column c = slot src[c]
+int compact_semijoin(tid_ctx *ctx, const tid_store *st, int fixed_slot, int32_t fixed_val, int key_slot,
+                     const int32_t *table, uint32_t tmask, const int8_t *src, tid_set *out);
 int compact_unique(tid_ctx *ctx, const int32_t *const *cols, int k, const int32_t *perm, int64_t n,
                    tid_set *out);
 // sorted packed keys (64-bit if wide, else 32-bit) -> distinct rows of k columns

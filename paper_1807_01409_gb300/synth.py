@@ -709,3 +709,62 @@ def serving_requests(s, p, o, m: int = 4000, seed: int = QUERY_SEED, mix=SERVE_M
             break
     del s_sorted, order
     return ["index" if k == 0 else "plan" for k in kinds], payloads, arrivals
+
+
+# ----------------------------------------------------------------------------
+# an RDFS schema for the university store (entailment workload)
+# ----------------------------------------------------------------------------
+
+# (sub-property, super-property) by predicate index: two chains of length two
+# (10 -> 4 -> 7 -> 19 and 6 -> 7) and two single links
+SUBPROPS = [(4, 7), (6, 7), (7, 19), (10, 4), (13, 12), (16, 15)]
+
+
+def rdfs_vocab(subjects: int) -> dict:
+    """IDs of rdf:type (the store's type predicate) and of the four schema
+    predicates, placed after the store's 20 predicate IDs."""
+    lay = uni_layout(subjects)
+    base = int(lay["pred_base"]) + len(PRED_FREQ)
+    return {"type": int(lay["pred_ids"][0]), "domain": base, "range": base + 1, "subprop": base + 2,
+            "subclass": base + 3}
+
+
+def rdfs_schema(subjects: int):
+    """Schema triples (s, p, o int32 arrays) of the university store: each top class's
+    512 (sub)class IDs form a binary subClassOf tree under the top class, top
+    classes 1..7 are subclasses of top class 0; every predicate has rdfs:domain its
+    domain classes' top classes, entity predicates rdfs:range their range classes'
+    top classes; SUBPROPS are subPropertyOf links."""
+    lay = uni_layout(subjects)
+    v = rdfs_vocab(subjects)
+    pid = [int(x) for x in lay["pred_ids"]]
+    cb = int(lay["class_base"])
+
+    def cls(k, j):
+        return cb + k * SUBCLASSES + j
+
+    t = []
+    for k in range(len(CLASS_FRACTIONS)):
+        for j in range(1, SUBCLASSES):
+            t.append((cls(k, j), v["subclass"], cls(k, (j - 1) // 2)))
+        if k:
+            t.append((cls(k, 0), v["subclass"], cls(0, 0)))
+    for j in range(1, len(PRED_KIND)):
+        kind, dom, rng_ = PRED_KIND[j]
+        for c in sorted(set(dom)):
+            t.append((pid[j], v["domain"], cls(c, 0)))
+        if kind == "ent":
+            for c in sorted(set(rng_)):
+                t.append((pid[j], v["range"], cls(c, 0)))
+    for a, b in SUBPROPS:
+        t.append((pid[a], v["subprop"], pid[b]))
+    a = np.array(sorted(set(t)), np.int32)
+    return a[:, 0].copy(), a[:, 1].copy(), a[:, 2].copy()
+
+
+def with_schema(store: Store) -> Store:
+    """The store followed by its schema triples (still a set: the schema uses
+    predicates the data does not)."""
+    ss, sp, so = rdfs_schema(store.meta["subjects"])
+    return Store(np.concatenate([store.s, ss]), np.concatenate([store.p, sp]), np.concatenate([store.o, so]),
+                 name=store.name + "+rdfs", meta=dict(store.meta, schema_triples=int(ss.shape[0])))

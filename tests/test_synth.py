@@ -55,3 +55,16 @@ def test_university_queries_selectivity_span():
     assert len(qs) == 64
     real = np.array([r for _, _, r in qs])
     assert real.max() >= 0.05 and real.min() <= 1e-4
+
+
+def test_rdfs_schema_is_disjoint_from_the_data():
+    st = synth.university_store(200_000)
+    v = synth.rdfs_vocab(st.meta["subjects"])
+    ss, sp, so = synth.rdfs_schema(st.meta["subjects"])
+    assert set(np.unique(sp).tolist()) <= {v["domain"], v["range"], v["subprop"], v["subclass"]}
+    assert not set(np.unique(st.p).tolist()) & {v["domain"], v["range"], v["subprop"], v["subclass"]}
+    assert v["type"] in set(np.unique(st.p).tolist())
+    full = synth.with_schema(st)
+    assert np.unique(np.stack([full.s, full.p, full.o], 1), axis=0).shape[0] == full.n
+    # the subclass tree: 8 x 511 edges inside the top classes and 7 links between them
+    assert int((sp == v["subclass"]).sum()) == 8 * 511 + 7
