@@ -226,6 +226,11 @@ int tid_filter(tid_ctx *ctx, const tid_set *in, const tid_pred *preds, int n_pre
 #define TID_JOIN_AUTO       0
 #define TID_JOIN_SORT_MERGE 1
 #define TID_JOIN_HASH       2
+/* or-ed into algo: a left outer join (SPARQL OPTIONAL; Section 4.2 names the
+ * outer and left joins of the library the paper used).  Every row of L without
+ * a match in R appears once, with R's other columns 0 (unbound).  Runs as a
+ * sort-merge join (TID_JOIN_LEFT | TID_JOIN_HASH is TID_ERR_ARG). */
+#define TID_JOIN_LEFT       0x100
 
 /* Inner join of L and R on ALL their shared variables (Section 4.2 and its
  * relationship table: the shared term may come from any of S/P/O on either

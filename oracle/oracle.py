@@ -15,6 +15,8 @@ Paper passages followed (TripleID-Q, IEEE TPDS 2018):
 * ``bind``         -- Section 4.2, result vectors R_qi (terms at the variable slots).
 * ``join``         -- Section 4.2 steps 1-3 and the relationship table (shared term
                       at any of S/P/O on either side); inner join.
+* ``left_join``    -- the left (outer) join Section 4.2 names among its library's joins:
+                      SPARQL OPTIONAL, unmatched left rows padded with 0.
 * ``union``        -- Section 4.1; results keep only distinct values (Section 4.3).
 * ``filter``       -- Section 4.3 (filter during extraction), on integer IDs with the
                       order-preserving literal encoding the same section proposes.
@@ -259,6 +261,19 @@ def join(Ls: TupleSet, Rs: TupleSet, method: str = "auto") -> TupleSet:
     return _set(out_vars, out)
 
 
+def left_join(Ls: TupleSet, Rs: TupleSet, method: str = "auto") -> TupleSet:
+    """Left outer join (OPTIONAL; Section 4.2 names the left and outer joins of the
+    library the paper used): the inner join's rows, plus every row of L that joins
+    no row of R, with R's other columns 0 (unbound)."""
+    inner = join(Ls, Rs, method)
+    shared, lkey, rkey, rrest, out_vars = join_schema(Ls.vars, Rs.vars)
+    rkeys = {tuple(r[j] for j in rkey) for r in Rs.rows.tolist() if all(r[j] != 0 for j in rkey)}
+    pad = [l + [0] * len(rrest) for l in Ls.rows.tolist()
+           if not (all(l[i] != 0 for i in lkey) and tuple(l[i] for i in lkey) in rkeys)]
+    rows = np.concatenate([inner.rows, np.array(pad, np.int32).reshape(-1, len(out_vars))], axis=0)
+    return _set(out_vars, rows)
+
+
 def union_schema(sets):
     out = []
     for t in sets:
@@ -323,7 +338,7 @@ def execute(s, p, o, plan) -> TupleSet:
             r = filter(ev(nd["input"]), nd["var"], nd["cmp"], nd["a"], nd.get("b", 0))
         elif op == "join":
             a, b = nd["inputs"]
-            r = join(ev(a), ev(b))
+            r = left_join(ev(a), ev(b)) if nd.get("algo") == "left" else join(ev(a), ev(b))
         elif op == "union":
             r = union([ev(j) for j in nd["inputs"]])
         elif op == "project":

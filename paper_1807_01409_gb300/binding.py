@@ -71,7 +71,8 @@ class tid_plan_node(C.Structure):
 
 
 CMP = {"eq": 0, "ne": 1, "lt": 2, "le": 3, "gt": 4, "ge": 5, "range": 6}
-JOIN = {"auto": 0, "sort_merge": 1, "sortmerge": 1, "hash": 2}
+TID_JOIN_LEFT = 0x100
+JOIN = {"auto": 0, "sort_merge": 1, "sortmerge": 1, "hash": 2, "left": TID_JOIN_LEFT}
 OP = {"match": 1, "filter": 2, "join": 3, "union": 4, "project": 5}
 
 

@@ -22,6 +22,11 @@
 //    2048 slots is copied into shared memory by every probing CTA.
 // A key value 0 (unbound) never matches.  The output is sorted to canonical
 // order; a join of two sets is a set, so no duplicate removal is needed.
+//
+// Left outer join (OPTIONAL; the library the paper used also offered outer and
+// left joins, Section 4.2): sort-merge only; a left row without a match counts
+// as one output row (its right range marked empty) and is written with the
+// right side's other columns 0 (unbound).
 
 #include <algorithm>
 
@@ -70,7 +75,9 @@ unsigned grid_for(int64_t n, int threads) {
 // ---- sort-merge --------------------------------------------------------------
 
 // per left row: [lo, hi) of equal keys in the sorted right keys
-__global__ void k_sm_count(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, uint32_t *__restrict__ cnt,
+constexpr uint32_t NO_MATCH = 0xFFFFFFFFu;  // left outer join: a left row written once, padded
+
+__global__ void k_sm_count(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, bool left, uint32_t *__restrict__ cnt,
                            uint32_t *__restrict__ lo_out, unsigned long long *__restrict__ total) {
     unsigned long long acc = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -93,6 +100,10 @@ __global__ void k_sm_count(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, uin
                 }
                 lo = (uint32_t)a;
                 c = (uint32_t)(a2 - a);
+            }
+            if (left && c == 0) {
+                c = 1;
+                lo = NO_MATCH;
             }
             cnt[l] = c;
             lo_out[l] = lo;
@@ -117,6 +128,12 @@ __global__ void k_join_write(const uint32_t *__restrict__ off, int64_t nl, const
             else b = m;
         }
         const int64_t l = a - 1;
+        if (lo[l] == NO_MATCH) {  // left outer join: the left row alone, right columns unbound
+            const int64_t lr = lperm ? lperm[l] : l;
+            for (int c = 0; c < kl; ++c) out.c[c][o] = L.c[c][lr];
+            for (int c = 0; c < nrest; ++c) out.c[kl + c][o] = 0;
+            continue;
+        }
         const int64_t j = (int64_t)lo[l] + (o - (int64_t)off[l]);
         int64_t lr, rr;
         if (left_is_probe) {
@@ -277,6 +294,8 @@ int read_u64(tid_ctx *ctx, const unsigned long long *d, unsigned long long *h) {
 
 int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out) {
     *out = nullptr;
+    const bool left = (algo & TID_JOIN_LEFT) != 0;
+    algo &= ~TID_JOIN_LEFT;
     int64_t nl = 0, nr = 0;
     TID_TRY(set_rows_host(L, &nl));
     TID_TRY(set_rows_host(R, &nr));
@@ -303,6 +322,32 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
     if (algo != TID_JOIN_AUTO && algo != TID_JOIN_SORT_MERGE && algo != TID_JOIN_HASH)
         return fail(TID_ERR_ARG, "tid_join: unknown algorithm %d", algo);
 
+    if (left && algo == TID_JOIN_HASH)
+        return fail(TID_ERR_ARG, "tid_join: a left outer join runs as a sort-merge join");
+    if (left && nl > 0 && nr == 0) {  // every left row, unbound on the right
+        tid_set *e = nullptr;
+        TID_TRY(set_alloc(ctx, kout, ovars, nl, &e));
+        int rc = TID_OK;
+        for (int c = 0; c < kout && rc == TID_OK; ++c) {
+            cudaError_t ce = c < L->k ? cudaMemcpyAsync(e->col[c], L->col[c], (size_t)nl * 4, cudaMemcpyDeviceToDevice,
+                                                        ctx->stream)
+                                      : cudaMemsetAsync(e->col[c], 0, (size_t)nl * 4, ctx->stream);
+            if (ce != cudaSuccess) rc = fail_cuda(ce, "tid_join: left rows");
+        }
+        e->bounded = L->bounded;
+        for (int c = 0; c < kout; ++c) {
+            e->lo[c] = c < L->k ? L->lo[c] : 0x80000000u;
+            e->hi[c] = c < L->k ? L->hi[c] : 0x80000000u;
+        }
+        if (rc == TID_OK) rc = set_rows_const(e, nl);
+        if (rc == TID_OK) rc = set_ready(e);
+        if (rc != TID_OK) {
+            set_free(e);
+            return rc;
+        }
+        *out = e;
+        return TID_OK;
+    }
     if (nl == 0 || nr == 0) {
         tid_set *e = nullptr;
         TID_TRY(set_alloc(ctx, kout, ovars, 0, &e));
@@ -321,7 +366,7 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         rprefix = rprefix && rkey[i] == i;
     }
     if (algo == TID_JOIN_AUTO) algo = (nk == 0 || (lprefix && rprefix)) ? TID_JOIN_SORT_MERGE : TID_JOIN_HASH;
-    if (nk == 0) algo = TID_JOIN_SORT_MERGE;  // cross product
+    if (nk == 0 || left) algo = TID_JOIN_SORT_MERGE;  // cross product; left outer join
 
     cudaStream_t st = ctx->stream;
     Scratch s(ctx);
@@ -372,7 +417,7 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         TID_TRY(s.get(&cnt, nl));
         TID_TRY(s.get(&lo, nl));
         TID_TRY(s.get(&off, nl));
-        k_sm_count<<<grid_for(nl, 256), 256, 0, st>>>(LK, nl, RK, nr, nk, cnt, lo, d_total);
+        k_sm_count<<<grid_for(nl, 256), 256, 0, st>>>(LK, nl, RK, nr, nk, left, cnt, lo, d_total);
         TID_TRY(launch_check("k_sm_count"));
         TID_TRY(scan_exclusive_u32(ctx, cnt, off, nl, nullptr));
     } else {
@@ -441,8 +486,8 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         b.hi[c] = L->hi[c];
     }
     for (int c = 0; c < nrest; ++c) {
-        b.lo[L->k + c] = R->lo[rrest[c]];
-        b.hi[L->k + c] = R->hi[rrest[c]];
+        b.lo[L->k + c] = left ? std::min(R->lo[rrest[c]], 0x80000000u) : R->lo[rrest[c]];  // 0 pads
+        b.hi[L->k + c] = left ? std::max(R->hi[rrest[c]], 0x80000000u) : R->hi[rrest[c]];
     }
     return canonicalize(ctx, ocols, kout, ovars, (int64_t)total, false, (L->bounded && R->bounded) ? &b : nullptr,
                         out);

@@ -286,6 +286,33 @@ def pin_project(o):
     assert pr.vars == (2, 0) and pr.rows.tolist() == [list(x) for x in want]
 
 
+def pin_left_join_rowwise(o):
+    """Left join, row by row: each left row with its matching right rows (all
+    shared columns equal and bound), or alone with the right side's other columns
+    0 when it has none."""
+    rng = np.random.default_rng(31)
+    for t in range(30):
+        kl, kr = int(rng.integers(1, 4)), int(rng.integers(1, 4))
+        lv = tuple(int(x) for x in rng.choice(6, size=kl, replace=False))
+        rv = tuple(int(x) for x in rng.choice(6, size=kr, replace=False))
+        L = o.TupleSet(lv, o.canonical(rng.integers(0, 4, (int(rng.integers(0, 40)), kl)).astype(np.int32)))
+        R = o.TupleSet(rv, o.canonical(rng.integers(0, 4, (int(rng.integers(0, 40)), kr)).astype(np.int32)))
+        shared = [v for v in lv if v in rv]
+        rest = [j for j, v in enumerate(rv) if v not in lv]
+        want = set()
+        for l in L.rows.tolist():
+            hits = [r for r in R.rows.tolist()
+                    if all(l[lv.index(v)] == r[rv.index(v)] != 0 for v in shared)]
+            if hits:
+                for r in hits:
+                    want.add(tuple(l) + tuple(r[j] for j in rest))
+            else:
+                want.add(tuple(l) + (0,) * len(rest))
+        got = o.left_join(L, R)
+        assert got.vars == lv + tuple(rv[j] for j in rest)
+        assert got.rows.tolist() == [list(x) for x in sorted(want)], t
+
+
 # RDFS rules of the paper's entailment table (Section 5), for the brute force:
 # two premises and a conclusion over variable names and vocabulary terms
 _RULES_BF = {
@@ -359,4 +386,4 @@ def pin_entail_bruteforce(o):
 ALL_PINS = [pin_golden_rule11, pin_match_bruteforce, pin_match_tallies,
             pin_bind_join_bruteforce, pin_join_cross_product, pin_union_laws,
             pin_filter_algebra, pin_canonical, pin_project, pin_entail_golden,
-            pin_entail_bruteforce]
+            pin_entail_bruteforce, pin_left_join_rowwise]

@@ -166,6 +166,44 @@ def test_join_random_sets(ctx, orc, algo, shape, size):
     tb.tid_set_free(hr)
 
 
+@pytest.mark.parametrize("shape", range(len(JOIN_SHAPES)))
+@pytest.mark.parametrize("size", [(0, 10), (10, 0), (1, 1), (300, 500), (5000, 40_000), (30_000, 2000)])
+def test_left_join_random_sets(ctx, orc, shape, size):
+    """Left outer join (OPTIONAL) equals the oracle's, unmatched left rows padded with 0."""
+    lv, rv = JOIN_SHAPES[shape]
+    rng = np.random.default_rng((hash((shape, size)) + 17) % 2**32)
+    nl, nr = size
+    hi = 6 if (lv, rv) == ((5, 6), (7, 8)) else max(4, int(np.sqrt(max(nl, nr))) // 2)
+    if (lv, rv) == ((5, 6), (7, 8)):
+        nl, nr = min(nl, 300), min(nr, 200)
+    L = _rand_set(orc, rng, lv, nl, hi, zeros=True)
+    R = _rand_set(orc, rng, rv, nr, hi, zeros=True)
+    hl = tb.tid_set_from_host(ctx, L.rows, lv)
+    hr = tb.tid_set_from_host(ctx, R.rows, rv)
+    _same(_host(tb.tid_join(ctx, hl, hr, "left")), orc.left_join(L, R))
+    with pytest.raises(tb.TidError) as e:
+        tb.tid_join(ctx, hl, hr, tb.TID_JOIN_LEFT | tb.JOIN["hash"])
+    assert e.value.code == tb.TID_ERR_ARG
+    tb.tid_set_free(hl)
+    tb.tid_set_free(hr)
+
+
+def test_optional_plans(ctx, orc):
+    """Star plans on the university store with every join OPTIONAL: typed subjects
+    with whichever properties they have."""
+    st_np = synth.university_store(1_000_000)
+    st = _store(ctx, st_np.s, st_np.p, st_np.o)
+    for name, plan in synth.university_plans(st_np)[:16]:
+        plan = [dict(nd, algo="left") if nd["op"] == "join" else nd for nd in plan]
+        got = _host(tb.tid_exec(ctx, st, plan))
+        want = orc.execute(st_np.s, st_np.p, st_np.o, plan)
+        try:
+            _same(got, want)
+        except AssertionError as e:
+            raise AssertionError(f"{name}: {e}")
+    tb.tid_store_free(st)
+
+
 def test_join_skewed_key(ctx, orc):
     """One key shared by many rows on both sides: its output spreads over threads."""
     rng = np.random.default_rng(3)

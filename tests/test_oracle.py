@@ -102,12 +102,14 @@ def test_execute_plans_against_solution_mappings(orc):
     assert r.vars == (X, Y, Z) and r.rows.tolist() == [list(w) for w in want]
 
 
-# planted mistakes in the Python rule evaluator (oracle.py), caught by the entailment pins
+# planted mistakes in the Python layer (oracle.py): rule evaluator and left join
 ENTAIL_MUTATIONS = [
     ("keys = np.unique(t1.rows[:, t1.vars.index(on)])", "keys = np.unique(t1.rows[:, 0])"),  # wrong column
     ("idx2 = cand[np.isin(col[cand], keys)] if cand.shape[0] else cand", "idx2 = cand"),  # no key restriction
     ('slot = r["data"].index(r["on"])', "slot = 0"),                                         # wrong join slot
     ('for t in r["then"]:', 'for t in reversed(r["then"]):'),                                # conclusion reversed
+    ("if not (all(l[i] != 0", "if (all(l[i] != 0"),                  # left join: pads the matched rows
+    ("pad = [l + [0] * len(rrest)", "pad = [l + [1] * len(rrest)"),   # left join: wrong padding
 ]
 
 
@@ -129,7 +131,7 @@ def test_entail_pins_catch_planted_mistake(orc, mut, tmp_path):
         sys.modules.pop("oracle_entail_mut", None)
     mod._SRC, mod._BUILD, mod._SO, mod._lib = orc._SRC, orc._BUILD, orc._SO, None
     failed = []
-    for pin in (pins.pin_entail_golden, pins.pin_entail_bruteforce):
+    for pin in (pins.pin_entail_golden, pins.pin_entail_bruteforce, pins.pin_left_join_rowwise):
         try:
             pin(mod)
         except Exception:
