@@ -4,27 +4,32 @@
 // (0 = "?") by its own thread, and the matching positions are reported.  The
 // paper marks a boolean positionArray and copies it back to the host; here the
 // hits are compacted on the device, in ascending order, reading the bound
-// columns once and writing each index once:
+// columns once and writing each index once.  Only the columns a pattern binds
+// are read (template on the bound mask).
 //
-//  * every CTA owns one contiguous chunk of the store (up to 384K or 768K
-//    triples; the grid is sized to what is resident, so chunks are
-//    ~n / (SMs x CTAs/SM));
-//  * phase 1 streams the chunk with 16-byte loads (past L1, 256-byte L2
-//    prefetch; the next step's loads are issued before the current step is
-//    recorded) and keeps a 1-bit-per-triple hit bitmap in shared memory, in
-//    triple order: eight lanes merge their 4-bit masks into one 32-bit word
-//    with three xor-shuffles and one of them stores it; plus a hit count --
-//    nothing else waits in this phase;
-//  * one decoupled look-back over the chunk counts (lookback.cuh, 256 chunks
-//    per L2 round trip) gives the chunk's output offset;
-//  * phase 2 expands the bitmap: each warp takes a contiguous run of words,
-//    32 at a time (one per lane): popc, a warp prefix sum, then each lane
-//    writes the indices of its set bits -- work in proportion to the hits.
-// Only the columns a pattern binds are read (template on the bound mask).
-// Stores larger than (resident CTAs x chunk) triples take several launches;
-// each continues the output where the previous one ended.
+// k1_scan (tid_match): one cooperative launch in three phases, so that SMs that
+// stream faster also do more of the work.
+//  * phase A: warps draw runs of 12 1024-triple steps from one counter (the
+//    next run is drawn while the current one loads) and load them with 16-byte
+//    streaming
+//    loads, and write the step's 32-word hit bitmap (eight lanes merge their
+//    4-bit masks with three xor-shuffles) and its hit count to global memory;
+//  * grid barrier; phase B: CTA c sums the counts of its fixed range of steps;
+//  * grid barrier; phase C: CTA c's offset is the sum of the totals of CTAs
+//    before it; it scans its steps' counts in shared memory and expands each
+//    step: a warp turns the step's 32 words into indices in a shared-memory
+//    stage (popc, warp prefix sum, set bits) and copies the stage out with
+//    coalesced stores.
+// Barrier waits are bounded (LB_SPIN_LIMIT polls, then TID_ERR_TIMEOUT).
 //
-// Bytes per launch: 4 * (bound columns) * n read + 4 * hits written.
+// k1_match (tid_match_noalloc, whose scratch is a fixed array): every CTA owns
+// one contiguous chunk, streams it into a shared-memory bitmap, takes its
+// output offset from one decoupled look-back over the chunk counts
+// (lookback.cuh) and expands the bitmap; stores larger than (resident CTAs x
+// chunk) triples take several launches.
+//
+// Bytes per launch: 4 * (bound columns) * n read + 4 * hits written
+// (k1_scan: + n/8 bitmap written and read + 8 bytes per 1024 triples of counts).
 
 #include <algorithm>
 
@@ -293,6 +298,263 @@ int run_mask(bool vec, cudaStream_t st, const int32_t *S, const int32_t *P, cons
                : run_segments<MASK, false>(st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows, sc);
 }
 
+// ---- k1_scan: dynamic steps, grid barriers, ordered expansion -------------------
+
+constexpr int K2S_STEP = 1024;                 // triples per warp step (32 lanes x 8 groups x 4)
+constexpr int K2S_WORDS = K2S_STEP / 32;       // bitmap words per step
+constexpr int K2S_CHUNK = K1_THREADS;          // steps scanned per round of phase C
+// Steps per draw: long enough that one counter serves all warps and the warps
+// stream one region of the store at a time (HBM pages), short enough that the
+// last draws end together (measured on GB300: 12 best among 1-48; 64 separate
+// counters over store partitions were slower).
+constexpr int K2S_DRAW = 12;
+constexpr int K2S_TICKET = 32;                 // step counter (own cache line in the control words)
+constexpr size_t K2S_CTL_BYTES = 256;
+
+struct ScanScratch {
+    uint32_t *bits;      // K2S_WORDS words per step
+    uint32_t *cnt;       // hits per step
+    unsigned *ctl;       // [1] barrier 1, [2] barrier 2, [K2S_TICKET] step counter
+    unsigned *cta_tot;   // hits per CTA range (phase B)
+    int *err;
+    int64_t steps;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// All CTAs of a cooperative launch meet here; false if the wait gave up.
+__device__ bool grid_barrier(unsigned *counter, unsigned expected, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counter, 1u);
+        int ok = 1;
+        unsigned polls = 0;
+        while (ld_acquire_u32(counter) < expected) {
+            if (++polls > LB_SPIN_LIMIT) {
+                atomicExch(err, TID_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int MASK, bool VEC>
+__global__ void __launch_bounds__(K1_THREADS)
+k1_scan(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int32_t *__restrict__ O, int64_t n,
+        int32_t ks, int32_t kp, int32_t ko, int32_t *__restrict__ out, int64_t cap, int64_t *__restrict__ d_rows,
+        int64_t *__restrict__ h_rows, ScanScratch sc) {
+    // step j covers triples [1024 j, 1024 j + 1024); lane l loads, in group g,
+    // triples 1024 j + 128 g + 4 l + (0..3), so lanes 8k..8k+7 hold word 4 g + k
+    static_assert(K1_G == 8, "bitmap layout assumes 8 load groups per step");
+    __shared__ uint32_t s_stage[K1_WARPS][K2S_STEP];
+    __shared__ uint32_t s_cnt[K2S_CHUNK], s_off[K2S_CHUNK];
+    __shared__ unsigned s_red[K1_WARPS];
+    __shared__ long long s_base;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned sub = lane & 7u;
+
+    // ---- phase A: runs of K2S_DRAW steps drawn from one counter
+    {
+        unsigned *ticket = sc.ctl + K2S_TICKET;
+        unsigned t = 0;  // first step of the current run
+        if (lane == 0) t = atomicAdd(ticket, (unsigned)K2S_DRAW);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        unsigned k = 0;  // position in the run
+        while ((int64_t)(t + k) < sc.steps) {
+            const int64_t step = (int64_t)t + k;
+            unsigned nxt = 0;  // the next run, drawn while the last step of this one loads
+            if (lane == 0 && k + 1 == (unsigned)K2S_DRAW) nxt = atomicAdd(ticket, (unsigned)K2S_DRAW);
+            const int64_t base = step * K2S_STEP + lane * 4;
+            int4 vs[K1_G], vp[K1_G], vo[K1_G];
+            if (VEC && (step + 1) * K2S_STEP <= n) {
+#pragma unroll
+                for (int g = 0; g < K1_G; ++g) {
+                    if (MASK & 1) vs[g] = ld_stream_v4(S + base + g * 128);
+                    if (MASK & 2) vp[g] = ld_stream_v4(P + base + g * 128);
+                    if (MASK & 4) vo[g] = ld_stream_v4(O + base + g * 128);
+                }
+            } else {  // ragged last step (elements past n read as 0, which no bound key equals)
+#pragma unroll
+                for (int g = 0; g < K1_G; ++g) {
+                    if (MASK & 1) vs[g] = load4<VEC>(S, base + g * 128, n);
+                    if (MASK & 2) vp[g] = load4<VEC>(P, base + g * 128, n);
+                    if (MASK & 4) vo[g] = load4<VEC>(O, base + g * 128, n);
+                }
+            }
+            unsigned c = 0;
+            uint32_t *bw = sc.bits + (size_t)step * K2S_WORDS;
+#pragma unroll
+            for (int g = 0; g < K1_G; ++g) {
+                unsigned mm = 0xFu;
+                if (MASK & 1) mm &= eq4(vs[g], ks);
+                if (MASK & 2) mm &= eq4(vp[g], kp);
+                if (MASK & 4) mm &= eq4(vo[g], ko);
+                unsigned v = mm << (4 * sub);
+                v |= __shfl_xor_sync(0xffffffffu, v, 1);
+                v |= __shfl_xor_sync(0xffffffffu, v, 2);
+                v |= __shfl_xor_sync(0xffffffffu, v, 4);
+                if (sub == (unsigned)g) {
+                    __stcg(bw + g * 4 + (lane >> 3), v);
+                    c += __popc(v);
+                }
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+            if (lane == 0) __stcg(sc.cnt + step, c);
+            if (++k == (unsigned)K2S_DRAW) {
+                t = __shfl_sync(0xffffffffu, nxt, 0);
+                k = 0;
+            }
+        }
+    }
+    if (!grid_barrier(sc.ctl + 1, gridDim.x, sc.err)) return;
+
+    // ---- phase B: this CTA's range of steps
+    const int64_t per = (sc.steps + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = min((int64_t)blockIdx.x * per, sc.steps), r1 = min(r0 + per, sc.steps);
+    unsigned t = 0;
+    for (int64_t j = r0 + threadIdx.x; j < r1; j += K1_THREADS) t += __ldcg(sc.cnt + j);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+    if (lane == 0) s_red[warp] = t;
+    __syncthreads();
+    __shared__ unsigned s_mine;
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int w = 0; w < K1_WARPS; ++w) tot += s_red[w];
+        __stcg(sc.cta_tot + blockIdx.x, tot);
+        s_mine = tot;
+    }
+    if (!grid_barrier(sc.ctl + 2, gridDim.x, sc.err)) return;
+
+    // ---- phase C: offset of this range, then ordered expansion
+    unsigned long long pre = 0, all = 0;
+    for (unsigned c = threadIdx.x; c < gridDim.x; c += K1_THREADS) {
+        const unsigned v = __ldcg(sc.cta_tot + c);
+        all += v;
+        if (c < blockIdx.x) pre += v;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        pre += __shfl_xor_sync(0xffffffffu, pre, d);
+        all += __shfl_xor_sync(0xffffffffu, all, d);
+    }
+    __syncthreads();  // s_red is reused
+    __shared__ unsigned long long s_pre[K1_WARPS], s_all[K1_WARPS];
+    if (lane == 0) {
+        s_pre[warp] = pre;
+        s_all[warp] = all;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long p = 0, a = 0;
+        for (int w = 0; w < K1_WARPS; ++w) {
+            p += s_pre[w];
+            a += s_all[w];
+        }
+        s_base = (long long)p;
+        if (blockIdx.x == 0) {
+            *d_rows = (int64_t)a;
+            *h_rows = (int64_t)a;
+        }
+    }
+    __syncthreads();
+    if (s_mine == 0) return;  // no hit in this range
+    long long run = s_base;
+    for (int64_t q0 = r0; q0 < r1; q0 += K2S_CHUNK) {
+        // block scan of this round's step counts
+        const int64_t j = q0 + threadIdx.x;
+        const unsigned c = j < r1 ? __ldcg(sc.cnt + j) : 0u;
+        unsigned x = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+            if ((int)lane >= d) x += y;
+        }
+        if (lane == 31) s_red[warp] = x;
+        __syncthreads();
+        unsigned wb = 0, rt = 0;
+        for (int w = 0; w < K1_WARPS; ++w) {
+            if (w < (int)warp) wb += s_red[w];
+            rt += s_red[w];
+        }
+        s_cnt[threadIdx.x] = c;
+        s_off[threadIdx.x] = wb + x - c;
+        __syncthreads();
+        // warp w expands steps q0 + 32 w .. q0 + 32 w + 31
+        uint32_t *stage = s_stage[warp];
+        for (int i = 0; i < 32; ++i) {
+            const int li = (int)warp * 32 + i;
+            const int64_t step = q0 + li;
+            if (step >= r1) break;
+            const unsigned sc_n = s_cnt[li];
+            if (sc_n == 0) continue;
+            uint32_t word = __ldcg(sc.bits + (size_t)step * K2S_WORDS + lane);
+            const unsigned pc = __popc(word);
+            unsigned xo = pc;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, xo, d);
+                if ((int)lane >= d) xo += y;
+            }
+            unsigned at = xo - pc;
+            const uint32_t wbase = (uint32_t)(step * K2S_STEP) + lane * 32;
+            while (word) {
+                const int b = __ffs(word) - 1;
+                stage[at++] = wbase + (uint32_t)b;
+                word &= word - 1;
+            }
+            __syncwarp();
+            const long long o0 = run + s_off[li];
+            for (unsigned e = lane; e < sc_n; e += 32) {
+                const long long pos = o0 + e;
+                if ((unsigned long long)pos < (unsigned long long)cap) out[pos] = (int32_t)stage[e];
+            }
+            __syncwarp();
+        }
+        run += rt;
+        __syncthreads();  // s_red, s_cnt, s_off are reused
+    }
+}
+
+template <int MASK, bool VEC>
+int scan_grid(unsigned *grid) {
+    static unsigned cached = 0;
+    if (!cached) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k1_scan<MASK, VEC>, K1_THREADS, 0) != cudaSuccess ||
+            v <= 0)
+            return fail(TID_ERR_CUDA, "k1_scan: no resident CTA");
+        cached = (unsigned)(v * sm_count());
+    }
+    *grid = cached;
+    return TID_OK;
+}
+
+template <int MASK, bool VEC>
+int run_scan(cudaStream_t st, const int32_t *S, const int32_t *P, const int32_t *O, int64_t n, int32_t ks,
+             int32_t kp, int32_t ko, int32_t *out, int64_t cap, int64_t *d_rows, int64_t *h_rows,
+             const ScanScratch &sc, unsigned grid) {
+    void *args[] = {(void *)&S, (void *)&P, (void *)&O, (void *)&n, (void *)&ks, (void *)&kp, (void *)&ko,
+                    (void *)&out, (void *)&cap, (void *)&d_rows, (void *)&h_rows, (void *)&sc};
+    TID_TRY_CUDA(cudaLaunchCooperativeKernel((const void *)k1_scan<MASK, VEC>, dim3(grid), dim3(K1_THREADS), args, 0,
+                                             st),
+                 "k1_scan");
+    return TID_OK;
+}
+
 }  // namespace
 
 // Status words one K1 launch needs at most (one per CTA of the largest grid).
@@ -338,6 +600,55 @@ int launch_match(cudaStream_t st, const int32_t *S, const int32_t *P, const int3
     }
 }
 
+// k1_scan with scratch from the context's pool (see tid_match).
+template <int MASK, bool VEC>
+static int scan_with_scratch(tid_ctx *ctx, const int32_t *S, const int32_t *P, const int32_t *O, int64_t n,
+                             int32_t ks, int32_t kp, int32_t ko, int32_t *out, int64_t cap, int64_t *d_rows,
+                             int64_t *h_rows) {
+    cudaStream_t st = ctx->stream;
+    unsigned grid = 0;
+    TID_TRY((scan_grid<MASK, VEC>(&grid)));
+    const int64_t steps = ceil_div(n, (int64_t)K2S_STEP);
+    grid = (unsigned)std::min<int64_t>(grid, std::max<int64_t>(1, steps));
+    const size_t bits_b = (size_t)steps * K2S_WORDS * 4, cnt_b = ((size_t)steps * 4 + 255) / 256 * 256;
+    const size_t ctl_b = K2S_CTL_BYTES, tot_b = (size_t)grid * 4;  // control words: barriers and counters
+    void *blk = nullptr;
+    TID_TRY(dev_alloc(ctx, &blk, bits_b + cnt_b + ctl_b + tot_b));
+    ScanScratch sc{};
+    sc.bits = (uint32_t *)blk;
+    sc.cnt = (uint32_t *)((char *)blk + bits_b);
+    sc.ctl = (unsigned *)((char *)blk + bits_b + cnt_b);
+    sc.cta_tot = (unsigned *)((char *)blk + bits_b + cnt_b + ctl_b);
+    sc.err = ctx->err_dev;
+    sc.steps = steps;
+    int rc = TID_OK;
+    cudaError_t e = cudaMemsetAsync(sc.ctl, 0, ctl_b, st);
+    if (e != cudaSuccess) rc = fail_cuda(e, "k1_scan control words");
+    if (rc == TID_OK) rc = run_scan<MASK, VEC>(st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows, sc, grid);
+    dev_free(ctx, blk);
+    return rc;
+}
+
+int launch_scan(tid_ctx *ctx, const int32_t *S, const int32_t *P, const int32_t *O, int64_t n, bool aligned16,
+                int32_t ks, int32_t kp, int32_t ko, int32_t *out, int64_t cap, int64_t *d_rows, int64_t *h_rows) {
+    const int mask = (ks != 0 ? 1 : 0) | (kp != 0 ? 2 : 0) | (ko != 0 ? 4 : 0);
+    if (n == 0 || mask == 0) {  // nothing to scan, or every position: no scratch needed
+        LbScratch none{};
+        return launch_match(ctx->stream, S, P, O, n, aligned16, ks, kp, ko, out, cap, d_rows, h_rows, none);
+    }
+#define K1S_CALL(M, V) scan_with_scratch<M, V>(ctx, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows)
+    switch (mask) {
+        case 1: return aligned16 ? K1S_CALL(1, true) : K1S_CALL(1, false);
+        case 2: return aligned16 ? K1S_CALL(2, true) : K1S_CALL(2, false);
+        case 3: return aligned16 ? K1S_CALL(3, true) : K1S_CALL(3, false);
+        case 4: return aligned16 ? K1S_CALL(4, true) : K1S_CALL(4, false);
+        case 5: return aligned16 ? K1S_CALL(5, true) : K1S_CALL(5, false);
+        case 6: return aligned16 ? K1S_CALL(6, true) : K1S_CALL(6, false);
+        default: return aligned16 ? K1S_CALL(7, true) : K1S_CALL(7, false);
+    }
+#undef K1S_CALL
+}
+
 }  // namespace tid
 
 // ---------------------------------------------------------------------------
@@ -355,11 +666,8 @@ extern "C" int tid_match(tid_ctx *ctx, const tid_store *st, tid_pattern pat, tid
     const int8_t var = -1;
     tid_set *set = nullptr;
     TID_TRY(set_alloc(ctx, 1, &var, n, &set));
-    LbScratch sc{};
-    int rc = ctx_scratch(ctx, match_scratch_words(), &sc);
-    if (rc == TID_OK)
-        rc = launch_match(ctx->stream, st->s, st->p, st->o, n, st->aligned16, pat.s, pat.p, pat.o,
-                          set->col[0], set->cap, set->d_rows, set->slot.dev, sc);
+    int rc = launch_scan(ctx, st->s, st->p, st->o, n, st->aligned16, pat.s, pat.p, pat.o, set->col[0], set->cap,
+                         set->d_rows, set->slot.dev);
     if (rc == TID_OK) rc = set_ready(set);
     if (rc != TID_OK) {
         set_free(set);
