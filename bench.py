@@ -83,7 +83,7 @@ def _peaks():
 def _traffic_record(kernel_src):
     """Per-launch DRAM bytes of the scan kernel from the committed ncu summary,
     valid only while the kernel source is unchanged since the capture."""
-    p = os.path.join(ROOT, "profiles", "k1_match_traffic.json")
+    p = os.path.join(ROOT, "profiles", "k1_scan_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
