@@ -121,4 +121,36 @@ __device__ __forceinline__ long long lb_exclusive_prefix(const Lookback &lb, uns
     return excl;
 }
 
+// ---- grid barrier (cooperative launches only: every CTA is resident) --------
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// All CTAs of a cooperative launch meet here; false if the wait gave up.
+__device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned expected, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counter, 1u);
+        int ok = 1;
+        unsigned polls = 0;
+        while (ld_acquire_u32(counter) < expected) {
+            if (++polls > LB_SPIN_LIMIT) {
+                atomicExch(err, TID_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 }  // namespace tid

@@ -320,36 +320,6 @@ struct ScanScratch {
     int64_t steps;
 };
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// All CTAs of a cooperative launch meet here; false if the wait gave up.
-__device__ bool grid_barrier(unsigned *counter, unsigned expected, int *err) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(counter, 1u);
-        int ok = 1;
-        unsigned polls = 0;
-        while (ld_acquire_u32(counter) < expected) {
-            if (++polls > LB_SPIN_LIMIT) {
-                atomicExch(err, TID_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-            __nanosleep(100);
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 template <int MASK, bool VEC>
 __global__ void __launch_bounds__(K1_THREADS)
 k1_scan(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int32_t *__restrict__ O, int64_t n,
