@@ -14,7 +14,8 @@
 //    streaming
 //    loads, and write the step's 32-word hit bitmap (eight lanes merge their
 //    4-bit masks with three xor-shuffles) and its hit count to global memory;
-//  * grid barrier; phase B: CTA c sums the counts of its fixed range of steps;
+//    each step's count is also added (atomically) to the total of the CTA
+//    whose fixed range of steps holds it;
 //  * grid barrier; phase C: CTA c's offset is the sum of the totals of CTAs
 //    before it; it scans its steps' counts in shared memory and expands each
 //    step: a warp turns the step's 32 words into indices in a shared-memory
@@ -314,8 +315,8 @@ constexpr size_t K2S_CTL_BYTES = 256;
 struct ScanScratch {
     uint32_t *bits;      // K2S_WORDS words per step
     uint32_t *cnt;       // hits per step
-    unsigned *ctl;       // [1] barrier 1, [2] barrier 2, [K2S_TICKET] step counter
-    unsigned *cta_tot;   // hits per CTA range (phase B)
+    unsigned *ctl;       // [1] grid barrier, [K2S_TICKET] step counter
+    unsigned *cta_tot;   // hits per CTA range (zeroed with the control words)
     int *err;
     int64_t steps;
 };
@@ -334,6 +335,9 @@ k1_scan(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int3
     __shared__ long long s_base;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned sub = lane & 7u;
+
+    // CTA c owns steps [c per, (c + 1) per) in phase C
+    const int64_t per = (sc.steps + gridDim.x - 1) / gridDim.x;
 
     // ---- phase A: runs of K2S_DRAW steps drawn from one counter
     {
@@ -382,7 +386,10 @@ k1_scan(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int3
             }
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
-            if (lane == 0) __stcg(sc.cnt + step, c);
+            if (lane == 0) {
+                __stcg(sc.cnt + step, c);
+                if (c) atomicAdd(sc.cta_tot + step / per, c);  // the total of the range that owns the step
+            }
             if (++k == (unsigned)K2S_DRAW) {
                 t = __shfl_sync(0xffffffffu, nxt, 0);
                 k = 0;
@@ -391,23 +398,8 @@ k1_scan(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int3
     }
     if (!grid_barrier(sc.ctl + 1, gridDim.x, sc.err)) return;
 
-    // ---- phase B: this CTA's range of steps
-    const int64_t per = (sc.steps + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = min((int64_t)blockIdx.x * per, sc.steps), r1 = min(r0 + per, sc.steps);
-    unsigned t = 0;
-    for (int64_t j = r0 + threadIdx.x; j < r1; j += K1_THREADS) t += __ldcg(sc.cnt + j);
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
-    if (lane == 0) s_red[warp] = t;
-    __syncthreads();
-    __shared__ unsigned s_mine;
-    if (threadIdx.x == 0) {
-        unsigned tot = 0;
-        for (int w = 0; w < K1_WARPS; ++w) tot += s_red[w];
-        __stcg(sc.cta_tot + blockIdx.x, tot);
-        s_mine = tot;
-    }
-    if (!grid_barrier(sc.ctl + 2, gridDim.x, sc.err)) return;
+    const unsigned mine = __ldcg(sc.cta_tot + blockIdx.x);
 
     // ---- phase C: offset of this range, then ordered expansion
     unsigned long long pre = 0, all = 0;
@@ -421,7 +413,6 @@ k1_scan(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int3
         pre += __shfl_xor_sync(0xffffffffu, pre, d);
         all += __shfl_xor_sync(0xffffffffu, all, d);
     }
-    __syncthreads();  // s_red is reused
     __shared__ unsigned long long s_pre[K1_WARPS], s_all[K1_WARPS];
     if (lane == 0) {
         s_pre[warp] = pre;
@@ -441,7 +432,7 @@ k1_scan(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int3
         }
     }
     __syncthreads();
-    if (s_mine == 0) return;  // no hit in this range
+    if (mine == 0) return;  // no hit in this range
     long long run = s_base;
     for (int64_t q0 = r0; q0 < r1; q0 += K2S_CHUNK) {
         // block scan of this round's step counts
@@ -592,7 +583,7 @@ static int scan_with_scratch(tid_ctx *ctx, const int32_t *S, const int32_t *P, c
     sc.err = ctx->err_dev;
     sc.steps = steps;
     int rc = TID_OK;
-    cudaError_t e = cudaMemsetAsync(sc.ctl, 0, ctl_b, st);
+    cudaError_t e = cudaMemsetAsync(sc.ctl, 0, ctl_b + tot_b, st);  // control words and range totals
     if (e != cudaSuccess) rc = fail_cuda(e, "k1_scan control words");
     if (rc == TID_OK) rc = run_scan<MASK, VEC>(st, S, P, O, n, ks, kp, ko, out, cap, d_rows, h_rows, sc, grid);
     dev_free(ctx, blk);
