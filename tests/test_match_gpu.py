@@ -137,3 +137,40 @@ def test_university_full_size_all_queries(ctx, orc):
         want = orc.match(st.s, st.p, st.o, pat.key())
         assert np.array_equal(got, want), pat.key()
     tb.tid_store_free(store)
+
+
+def test_concurrent_contexts(ctx, orc):
+    """Two host threads, each with its own context and stream, scan at the same time
+    (the scan is a cooperative launch whose grid fills the GPU): every result equals
+    the oracle's and no in-kernel wait gives up."""
+    import threading
+    st = synth.university_store(20_000_000)
+    qs = [q for q, _, _ in synth.university_queries(st)][:24]
+    cols = [_dev(c) for c in (st.s, st.p, st.o)]
+    torch.cuda.synchronize()
+    want = {q.key(): orc.match(st.s, st.p, st.o, q.key()) for q in qs}
+    errors = []
+
+    def worker(order):
+        c = tb.tid_ctx_create(0, None)
+        try:
+            store = tb.tid_load(c, *cols, copy=0)
+            for _ in range(3):
+                hs = [(q, tb.tid_match(c, store, q)) for q in order]
+                for q, h in hs:
+                    got = tb.tid_set_to_host(h)[:, 0]
+                    tb.tid_set_free(h)
+                    if not np.array_equal(got, want[q.key()]):
+                        errors.append(q.key())
+            tb.tid_store_free(store)
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+        finally:
+            tb.tid_ctx_destroy(c)
+
+    ths = [threading.Thread(target=worker, args=(qs,)), threading.Thread(target=worker, args=(qs[::-1],))]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert not errors, errors[:5]
