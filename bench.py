@@ -445,10 +445,10 @@ def run_ours(args, rank, world, local):
 
     # ------------------------------------------------------------------ e2e
     # host buffers: the store is copied in from pinned memory and every result
-    # list copied back, each step, through the public C ABI
+    # list copied back into pinned memory, each step, through the public C ABI
     host_cols = [torch.from_numpy(c).pin_memory() for c in (store_np.s, store_np.p, store_np.o)]
     e2e_steps = max(1, min(args.steps, 3))
-    out_bufs = [np.empty((h, 1), np.int32) for h in hits]
+    out_bufs = [torch.empty((max(h, 1), 1), dtype=torch.int32).pin_memory().numpy() for h in hits]
     d2h = 4 * sum(hits)
     h2d = 3 * 4 * store_np.n
 
