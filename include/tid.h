@@ -91,6 +91,14 @@ int tid_ctx_destroy(tid_ctx *ctx);
 /* Message of the last failing call on this thread ("" if none). */
 const char *tid_last_error(void);
 
+/* Testing aid for failure handling (the paper has no counterpart): after
+ * `after` more device allocations on this context succeed, every further one
+ * fails with TID_ERR_OOM as if the device were out of memory; after < 0 turns
+ * it off.  The failure is made on the host (no allocation is attempted); calls
+ * that fail this way release what they allocated and leave the context
+ * usable. */
+int tid_ctx_inject_alloc_failure(tid_ctx *ctx, int64_t after);
+
 /* ------------------------------------------------------------------------ */
 /* store -- Section 3: the TripleID file of (SubjID, PredID, ObjID)          */
 /* ------------------------------------------------------------------------ */

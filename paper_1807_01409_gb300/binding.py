@@ -133,6 +133,7 @@ def lib():
         "tid_exec": (C.c_int, [_vp, _vp, C.POINTER(tid_plan_node), C.c_int, C.POINTER(_vp)]),
         "tid_match_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, C.c_int64, tid_pattern, _vp, C.c_int64,
                                         _vp]),
+        "tid_ctx_inject_alloc_failure": (C.c_int, [_vp, C.c_int64]),
         "tid_entail": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(tid_rdfs_vocab), C.POINTER(_vp),
                                  C.POINTER(tid_entail_stats)]),
         "tid_server_create": (C.c_int, [C.c_int, _vp, _vp, _vp, C.c_int64, C.POINTER(tid_server_config),
@@ -441,6 +442,11 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+def tid_ctx_inject_alloc_failure(ctx, after):
+    """After `after` more device allocations on ctx, fail the rest with TID_ERR_OOM (< 0: off)."""
+    _check(lib().tid_ctx_inject_alloc_failure(ctx, int(after)), "tid_ctx_inject_alloc_failure")
 
 
 def tid_entail(ctx, st, rule, vocab):

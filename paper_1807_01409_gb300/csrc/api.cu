@@ -52,6 +52,9 @@ DeviceGuard::~DeviceGuard() {
 // ---------------------------------------------------------------------------
 int dev_alloc(tid_ctx *ctx, void **p, size_t bytes) {
     *p = nullptr;
+    const int64_t fa = ctx->fail_after.load(std::memory_order_relaxed);
+    if (fa >= 0 && ctx->allocs.fetch_add(1, std::memory_order_relaxed) >= fa)
+        return fail(TID_ERR_OOM, "device allocation refused (injected failure)");
     if (bytes == 0) bytes = 256;
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
     if (e != cudaSuccess) {
@@ -337,9 +340,18 @@ extern "C" int tid_ctx_destroy(tid_ctx *ctx) {
     return TID_OK;
 }
 
+extern "C" int tid_ctx_inject_alloc_failure(tid_ctx *ctx, int64_t after) {
+    clear_error();
+    if (!ctx) return fail(TID_ERR_ARG, "tid_ctx_inject_alloc_failure: null context");
+    ctx->allocs.store(0);
+    ctx->fail_after.store(after < 0 ? -1 : after);
+    return TID_OK;
+}
+
 extern "C" int tid_load(tid_ctx *ctx, const int32_t *s, const int32_t *p, const int32_t *o,
                         int64_t n, int where, int copy, tid_store **out) {
     clear_error();
+    tid::Range nvtx_range("tid_load");
     if (!ctx || !out) return fail(TID_ERR_ARG, "tid_load: null argument");
     *out = nullptr;
     if (n < 0 || n > INT32_MAX) return fail(TID_ERR_ARG, "tid_load: n = %lld out of range", (long long)n);
@@ -441,6 +453,7 @@ extern "C" int tid_set_info(const tid_set *set, int *cols, int64_t *capacity, co
 
 extern "C" int tid_set_to_host(tid_set *set, int32_t *buf, int64_t cap_rows, int64_t *rows_out) {
     clear_error();
+    tid::Range nvtx_range("tid_set_to_host");
     if (!set) return fail(TID_ERR_ARG, "tid_set_to_host: null set");
     int64_t rows = 0;
     TID_TRY(tid_set_rows(set, &rows));

@@ -592,6 +592,7 @@ using namespace tid;
 
 extern "C" int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, int q, tid_set **outs) {
     clear_error();
+    tid::Range nvtx_range("tid_match_batch");
     if (!ctx || !st || (q > 0 && (!pats || !outs))) return fail(TID_ERR_ARG, "tid_match_batch: null argument");
     if (q < 0) return fail(TID_ERR_ARG, "tid_match_batch: q = %d", q);
     if (st->ctx != ctx) return fail(TID_ERR_ARG, "tid_match_batch: store belongs to another context");

@@ -77,6 +77,7 @@ int rows_of(tid_set *s, int64_t *n) { return set_rows_host(s, n); }
 extern "C" int tid_entail(tid_ctx *ctx, const tid_store *st, int rule, const tid_rdfs_vocab *vocab, tid_set **out,
                           tid_entail_stats *stats) {
     clear_error();
+    tid::Range nvtx_range("tid_entail");
     if (!ctx || !st || !vocab || !out) return fail(TID_ERR_ARG, "tid_entail: null argument");
     *out = nullptr;
     if (st->ctx != ctx) return fail(TID_ERR_ARG, "tid_entail: store belongs to another context");

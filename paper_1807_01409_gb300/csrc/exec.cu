@@ -186,6 +186,7 @@ int exec_plan(tid_ctx *ctx, const tid_store *st, const tid_plan_node *nodes, int
 
 extern "C" int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *nodes, int n_nodes, tid_set **out) {
     clear_error();
+    tid::Range nvtx_range("tid_exec");
     if (!ctx || !st || !nodes || !out) return fail(TID_ERR_ARG, "tid_exec: null argument");
     *out = nullptr;
     if (st->ctx != ctx) return fail(TID_ERR_ARG, "tid_exec: store belongs to another context");

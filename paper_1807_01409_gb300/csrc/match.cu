@@ -618,6 +618,7 @@ int launch_scan(tid_ctx *ctx, const int32_t *S, const int32_t *P, const int32_t 
 extern "C" int tid_match(tid_ctx *ctx, const tid_store *st, tid_pattern pat, tid_set **out) {
     using namespace tid;
     clear_error();
+    tid::Range nvtx_range("tid_match");
     if (!ctx || !st || !out) return fail(TID_ERR_ARG, "tid_match: null argument");
     if (st->ctx != ctx) return fail(TID_ERR_ARG, "tid_match: store belongs to another context");
     if (pat.s < 0 || pat.p < 0 || pat.o < 0) return fail(TID_ERR_ID, "tid_match: negative ID in pattern");

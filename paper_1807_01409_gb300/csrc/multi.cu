@@ -302,6 +302,7 @@ using namespace tid;
 
 extern "C" int tid_match_multi(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, int m, tid_set **outs) {
     clear_error();
+    tid::Range nvtx_range("tid_match_multi");
     if (!ctx || !st || !pats || !outs) return fail(TID_ERR_ARG, "tid_match_multi: null argument");
     if (m < 1 || m > TID_MAX_MULTI) return fail(TID_ERR_ARG, "tid_match_multi: m = %d (1..%d)", m, TID_MAX_MULTI);
     if (st->ctx != ctx) return fail(TID_ERR_ARG, "tid_match_multi: store belongs to another context");

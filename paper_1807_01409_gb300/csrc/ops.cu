@@ -246,6 +246,7 @@ static int check_set(const tid_ctx *ctx, const tid_set *s, const char *who) {
 extern "C" int tid_bind(tid_ctx *ctx, const tid_store *st, tid_pattern pat, const tid_set *idx, const tid_pred *preds,
                         int n_preds, tid_set **out) {
     clear_error();
+    tid::Range nvtx_range("tid_bind");
     if (!ctx || !st || !out) return fail(TID_ERR_ARG, "tid_bind: null argument");
     *out = nullptr;
     TID_TRY(check_set(ctx, idx, "tid_bind"));
@@ -257,6 +258,7 @@ extern "C" int tid_bind(tid_ctx *ctx, const tid_store *st, tid_pattern pat, cons
 
 extern "C" int tid_filter(tid_ctx *ctx, const tid_set *in, const tid_pred *preds, int n_preds, tid_set **out) {
     clear_error();
+    tid::Range nvtx_range("tid_filter");
     if (!ctx || !out) return fail(TID_ERR_ARG, "tid_filter: null argument");
     *out = nullptr;
     TID_TRY(check_set(ctx, in, "tid_filter"));
@@ -266,6 +268,7 @@ extern "C" int tid_filter(tid_ctx *ctx, const tid_set *in, const tid_pred *preds
 
 extern "C" int tid_join(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out) {
     clear_error();
+    tid::Range nvtx_range("tid_join");
     if (!ctx || !out) return fail(TID_ERR_ARG, "tid_join: null argument");
     *out = nullptr;
     TID_TRY(check_set(ctx, L, "tid_join"));
@@ -276,6 +279,7 @@ extern "C" int tid_join(tid_ctx *ctx, const tid_set *L, const tid_set *R, int al
 
 extern "C" int tid_union(tid_ctx *ctx, const tid_set *const *in, int k, tid_set **out) {
     clear_error();
+    tid::Range nvtx_range("tid_union");
     if (!ctx || !out) return fail(TID_ERR_ARG, "tid_union: null argument");
     *out = nullptr;
     DeviceGuard g(ctx->device);
@@ -284,6 +288,7 @@ extern "C" int tid_union(tid_ctx *ctx, const tid_set *const *in, int k, tid_set 
 
 extern "C" int tid_project(tid_ctx *ctx, const tid_set *in, const int8_t *vars, int n_vars, tid_set **out) {
     clear_error();
+    tid::Range nvtx_range("tid_project");
     if (!ctx || !out) return fail(TID_ERR_ARG, "tid_project: null argument");
     *out = nullptr;
     TID_TRY(check_set(ctx, in, "tid_project"));

@@ -193,6 +193,7 @@ int grow_staging(Worker &W, size_t rows) {
 }
 
 void run_wave(tid_server *S, Worker &W, std::vector<Request *> &wave) {
+    Range nvtx_range("tid_server_wave");
     tid_ctx *ctx = W.ctx;
     const tid_store *st = W.st;
     const int nw = (int)wave.size();

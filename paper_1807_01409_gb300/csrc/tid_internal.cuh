@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -102,6 +105,9 @@ struct tid_ctx {
     std::vector<std::pair<int, int>> free_slots;
     std::vector<tid::PendingSlot> pending;
     std::mutex mu;
+    // testing aid (tid_ctx_inject_alloc_failure): allocations left before they fail
+    std::atomic<int64_t> fail_after{-1};
+    std::atomic<int64_t> allocs{0};
 };
 
 struct tid_store {
@@ -133,6 +139,15 @@ struct tid_set {
 namespace tid {
 
 // device / context helpers (api.cu)
+// An NVTX range over one C-ABI call (visible in profiler timelines; free when
+// no tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev);
