@@ -1,5 +1,6 @@
 """Synthetic inputs: seeded, exact size, sets, IDs in range, recipe shape."""
 import numpy as np
+import pytest
 
 from paper_1807_01409_gb300 import synth
 
@@ -68,3 +69,65 @@ def test_rdfs_schema_is_disjoint_from_the_data():
     assert np.unique(np.stack([full.s, full.p, full.o], 1), axis=0).shape[0] == full.n
     # the subclass tree: 8 x 511 edges inside the top classes and 7 links between them
     assert int((sp == v["subclass"]).sum()) == 8 * 511 + 7
+
+
+def test_device_recipe_matches_the_host_recipe_on_cpu():
+    """university_store_torch (run here on the CPU) draws a set of exactly n triples
+    whose predicate frequencies match the host generator's and whose IDs follow its
+    layout."""
+    torch = pytest.importorskip("torch")
+    n = 400_000
+    s, p, o = synth.university_store_torch(n, device="cpu")
+    assert s.shape[0] == p.shape[0] == o.shape[0] == n
+    assert torch.unique(torch.stack([s, p, o], 1), dim=0).shape[0] == n
+    lay = synth.uni_layout(synth.uni_subjects(n))
+    pid = lay["pred_ids"]
+    freq = np.bincount(p.numpy() - int(pid[0]), minlength=len(pid)) / n
+    host = synth.university_store(n)  # the same recipe on the host (duplicates removed the same way)
+    hfreq = np.bincount(host.p - int(pid[0]), minlength=len(pid)) / n
+    assert np.allclose(freq, hfreq, atol=0.002)
+    assert int(s.min()) >= 1 and int(s.max()) <= synth.uni_subjects(n)
+
+
+def test_batch_queries_sizes_and_shapes():
+    """Every drawn query's tally size lies within the window of its target whenever
+    such a pattern exists, all seven shapes occur, and the sizes are the value
+    tallies of the store."""
+    torch = pytest.importorskip("torch")
+    s, p, o = synth.university_store_torch(300_000, device="cpu")
+    qs = synth.batch_queries(s, p, o, m=700, hi=1e5)
+    shapes = {q.shape() for q, _, _ in qs}
+    assert len(shapes) == 7, shapes
+    within = sum(1 for _, t, sz in qs if t / 1.5 <= sz <= t * 1.5)
+    assert within >= 0.9 * len(qs)
+    S, P, O = (x.numpy() for x in (s, p, o))
+    for q, _, sz in qs[:40]:
+        m = np.ones(S.shape[0], bool)
+        for col, v in ((S, q.s), (P, q.p), (O, q.o)):
+            if v:
+                m &= col == v
+        assert int(m.sum()) == sz, (q.key(), sz)
+
+
+def test_serving_requests_stream():
+    """Poisson arrivals at the stated rate, the three classes in their proportions,
+    and every plan well formed (bound slots anonymous, joins on a shared variable)."""
+    torch = pytest.importorskip("torch")
+    s, p, o = synth.university_store_torch(300_000, device="cpu")
+    kinds, payloads, arr = synth.serving_requests(s, p, o, m=2000, rate=20000.0)
+    assert np.all(np.diff(arr) > 0)
+    assert abs(2000 / arr[-1] - 20000.0) < 2000.0
+    frac_index = kinds.count("index") / len(kinds)
+    assert abs(frac_index - synth.SERVE_MIX[0]) < 0.04
+    for k, x in zip(kinds, payloads):
+        if k == "index":
+            assert any(x.key())
+            continue
+        for nd in x:
+            if nd["op"] == "match":
+                pat = nd["pattern"]
+                assert all(v == -1 for v, key in zip(pat.var, pat.key()) if key)
+                assert any(v >= 0 for v in pat.var)
+        if x[-1]["op"] == "join":
+            a, b = (x[i]["pattern"] for i in x[-1]["inputs"])
+            assert {v for v in a.var if v >= 0} & {v for v in b.var if v >= 0}
