@@ -472,8 +472,10 @@ def run_ours(args, rank, world, local):
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(store_np, synth.university_queries(store_np))
+    # the other rows are per-GPU characteristics: measured in single-GPU runs only
+    extra = world == 1
     rows = None
-    if not args.no_rows:
+    if extra and not args.no_rows:
         rows = measure_rows(tb, ctx, store, store_np, stream, _peaks()[0],
                             with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
@@ -481,16 +483,16 @@ def run_ours(args, rank, world, local):
     del cols
     torch.cuda.empty_cache()
     entail = None
-    if not args.no_entail:
+    if extra and not args.no_entail:
         entail = measure_entail(tb, ctx, stream, store_np, _peaks()[0],
                                 with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     batch = None
-    if not args.no_batch:
+    if extra and not args.no_batch:
         batch = measure_batch(tb, ctx, stream, _peaks()[0],
                               with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     tb.tid_ctx_destroy(ctx)
     serve = None
-    if not args.no_serve:
+    if extra and not args.no_serve:
         serve = measure_serve(tb, with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     if rank == 0:
