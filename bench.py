@@ -80,15 +80,27 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+K1_REGION = ("// ---- k1_scan: dynamic steps", "int launch_scan(")  # the kernel, its grid and launch
+
+
+def _kernel_region_sha1(kernel_src):
+    src = open(kernel_src).read()
+    a, b = src.index(K1_REGION[0]), src.index(K1_REGION[1])
+    return hashlib.sha1(src[a:b].encode()).hexdigest()
+
+
 def _traffic_record(kernel_src):
-    """Per-launch DRAM bytes of the scan kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
+    """Per-launch DRAM bytes of the scan kernel from the committed ncu record,
+    valid only while the kernel's code (its device code, grid and launch) is
+    unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "k1_scan_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    h = hashlib.sha1(open(kernel_src, "rb").read()).hexdigest()
-    if d.get("kernel_sha1") != h:
+    try:
+        if d.get("kernel_region_sha1") != _kernel_region_sha1(kernel_src):
+            return None
+    except ValueError:  # the region markers moved: treat as changed
         return None
     return d
 
