@@ -6,6 +6,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -63,3 +64,26 @@ def test_reference_arm_prints_on_rank0_only(tmp_path):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
                         "--steps", "1", "--warmup", "1"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_all_cores_oracle_scan_equals_whole_store_scan():
+    """The all-cores CPU baseline runs the oracle's match on contiguous slices;
+    offset and concatenated, the slices give the whole store's list, including
+    slice counts that leave empty or one-triple slices."""
+    from concurrent.futures import ThreadPoolExecutor
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import oracle
+    from paper_1807_01409_gb300 import synth
+    st = synth.university_store(50_000)
+    keys = [q.key() for q, _, _ in synth.university_queries(st)[:8]] + [(0, 0, 0)]
+    with ThreadPoolExecutor(max_workers=4) as pool:
+        for cores in (1, 3, 7, 64):
+            for key in keys:
+                want = oracle.match(st.s, st.p, st.o, key)
+                got = bench._match_on_cores(oracle, st, key, pool, cores)
+                assert got.dtype == want.dtype and np.array_equal(got, want), (cores, key)
+    tiny = synth.Store(st.s[:3].copy(), st.p[:3].copy(), st.o[:3].copy(), "tiny")
+    with ThreadPoolExecutor(max_workers=2) as pool:
+        assert np.array_equal(bench._match_on_cores(oracle, tiny, (0, 0, 0), pool, 8),
+                              np.arange(3, dtype=np.int32))
