@@ -189,7 +189,11 @@ def pin_bind_join_bruteforce(o):
             # keep some cases all-variable in the unconstrained slot
             a = o.bind(S, P, O, ka, va, o.match(S, P, O, ka))
             b = o.bind(S, P, O, kb, vb, o.match(S, P, O, kb))
+            # a result vector has one column per distinct variable, in slot order
+            assert a.vars == tuple(dict.fromkeys(v for v in va if v >= 0)), (va, a.vars)
+            assert b.vars == tuple(dict.fromkeys(v for v in vb if v >= 0)), (vb, b.vars)
             j = o.join(a, b)
+            assert j.vars == a.vars + tuple(v for v in b.vars if v not in a.vars), (a.vars, b.vars, j.vars)
             want = solutions(S, P, O, [(ka, va), (kb, vb)], j.vars)
             assert sorted(map(tuple, j.rows.tolist())) == want, (seed, va, vb, ka, kb)
             assert j.rows.tolist() == [list(r) for r in want]  # canonical order
@@ -279,11 +283,16 @@ def pin_canonical(o):
 
 
 def pin_project(o):
+    """SELECT keeps the named variables in the named order, with DISTINCT: the
+    Python set of the picked tuple entries (columns drawn from disjoint value
+    ranges, so a swapped or re-sorted column list cannot pass)."""
     rng = np.random.default_rng(6)
-    T = o.TupleSet((0, 1, 2), o.canonical(rng.integers(1, 6, (200, 3))))
-    pr = o.project(T, (2, 0))
-    want = sorted({(c, a) for a, b, c in T.rows.tolist()})
-    assert pr.vars == (2, 0) and pr.rows.tolist() == [list(x) for x in want]
+    rows = np.stack([rng.integers(1, 6, 200), rng.integers(10, 14, 200), rng.integers(20, 60, 200)], axis=1)
+    T = o.TupleSet((0, 1, 2), o.canonical(rows))
+    for pick in ((2, 0), (1,), (2, 1, 0), (0, 2)):
+        pr = o.project(T, pick)
+        want = sorted({tuple(r[v] for v in pick) for r in T.rows.tolist()})
+        assert pr.vars == pick and pr.rows.tolist() == [list(x) for x in want], pick
 
 
 def pin_left_join_rowwise(o):
@@ -383,7 +392,44 @@ def pin_entail_bruteforce(o):
             assert stats["all"] == len(want)
 
 
+def pin_execute_plans(o):
+    """Whole plans (star, chain, union, filter, project) on small graphs equal
+    the solution-mapping enumeration of the same graph pattern (the plan nodes
+    of Sections 4.1-4.3 evaluated in order)."""
+    from paper_1807_01409_gb300.synth import Pattern
+    X, Y, Z = 0, 1, 2
+    S, P, O = tiny_graph(31, 40, ids=6)
+    star = [{"op": "match", "pattern": Pattern(0, 2, 0, var=(X, -1, Y))},
+            {"op": "match", "pattern": Pattern(0, 3, 0, var=(X, -1, Z))},
+            {"op": "join", "inputs": [0, 1]}]
+    r = o.execute(S, P, O, star)
+    want = solutions(S, P, O, [((0, 2, 0), (X, -1, Y)), ((0, 3, 0), (X, -1, Z))], r.vars)
+    assert r.rows.tolist() == [list(w) for w in want]
+    chain = [{"op": "match", "pattern": Pattern(0, 0, 0, var=(X, -1, Y))},
+             {"op": "match", "pattern": Pattern(0, 4, 0, var=(Y, -1, Z))},
+             {"op": "join", "inputs": [0, 1]},
+             {"op": "project", "input": 2, "vars": [X, Z]}]
+    r = o.execute(S, P, O, chain)
+    want = solutions(S, P, O, [((0, 0, 0), (X, -1, Y)), ((0, 4, 0), (Y, -1, Z))], (X, Z))
+    assert r.rows.tolist() == [list(w) for w in want]
+    # FILTER (?Y in [2, 4]) over the chain's first pattern
+    flt = [{"op": "match", "pattern": Pattern(0, 0, 0, var=(X, -1, Y))},
+           {"op": "filter", "input": 0, "var": Y, "cmp": "range", "a": 2, "b": 4}]
+    r = o.execute(S, P, O, flt)
+    want = [w for w in solutions(S, P, O, [((0, 0, 0), (X, -1, Y))], (X, Y)) if 2 <= w[1] <= 4]
+    assert r.rows.tolist() == [list(w) for w in want]
+    # UNION of two branches with different variables
+    un = [{"op": "match", "pattern": Pattern(1, 0, 0, var=(-1, X, Y))},
+          {"op": "match", "pattern": Pattern(0, 2, 0, var=(Y, -1, Z))},
+          {"op": "union", "inputs": [0, 1]}]
+    r = o.execute(S, P, O, un)
+    a = solutions(S, P, O, [((1, 0, 0), (-1, X, Y))], (X, Y))
+    b = solutions(S, P, O, [((0, 2, 0), (Y, -1, Z))], (Y, Z))
+    want = sorted({(x, y, 0) for x, y in a} | {(0, y, z) for y, z in b})
+    assert r.vars == (X, Y, Z) and r.rows.tolist() == [list(w) for w in want]
+
+
 ALL_PINS = [pin_golden_rule11, pin_match_bruteforce, pin_match_tallies,
             pin_bind_join_bruteforce, pin_join_cross_product, pin_union_laws,
             pin_filter_algebra, pin_canonical, pin_project, pin_entail_golden,
-            pin_entail_bruteforce, pin_left_join_rowwise]
+            pin_entail_bruteforce, pin_left_join_rowwise, pin_execute_plans]

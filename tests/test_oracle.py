@@ -34,6 +34,17 @@ MUTATIONS = [
     ("if (m > 0 && row_cmp(tmp + (m - 1) * k, r, cols, k) == 0) continue;", ""),   # no dedupe
     ("if (outs) outs[j][counts[j]] = (int32_t)i;\n                counts[j]++;",
      "if (outs) outs[j][counts[j]] = (int32_t)i;\n                counts[j]++;\n                break;"),  # first key only
+    ("keys[3 * j + 1], keys[3 * j + 2])", "keys[3 * j + 2], keys[3 * j + 1])"),     # multi: p and o keys swapped
+    ("int32_t term[3] = {S[i], P[i], O[i]};", "int32_t term[3] = {S[i], O[i], P[i]};"),  # bind: p and o slots swapped
+    ("int32_t x = a[cols[c]], y = b[cols[c]];",
+     "uint32_t x = (uint32_t)a[cols[c]], y = (uint32_t)b[cols[c]];"),              # unsigned row order
+    ("if (has_zero_key(l, nk, lkey)) { ++a; continue; }\n        if (has_zero_key(r, nk, rkey)) { ++b; continue; }",
+     ""),                                                                           # sort-merge: unbound keys join
+    ("while (b2 < nr && key_cmp(l, lkey, R + pr[b2] * kr, rkey, nk) == 0) ++b2;", ""),  # sort-merge: right group of one
+    ("while (a2 < nl && key_cmp(L + pl[a2] * kl, lkey, r, rkey, nk) == 0) ++a2;", ""),  # sort-merge: left group of one
+    ("case 1: keep = x != a; break;", "case 1: keep = x == a; break;"),            # NE as EQ
+    ("case 4: keep = x > a; break;", "case 4: keep = x >= a; break;"),             # GT as GE
+    ("if (x == 0) keep = 0;\n        else switch (op) {", "switch (op) {"),         # unbound rows pass filters
 ]
 
 
@@ -66,44 +77,17 @@ def test_sortmerge_equals_nested_on_random_sets(orc):
         assert a.vars == b.vars and np.array_equal(a.rows, b.rows)
 
 
-def test_execute_plans_against_solution_mappings(orc):
-    """Whole plans (star, chain, union, filter, project) on small graphs equal
-    the solution-mapping enumeration of the same graph pattern."""
-    from paper_1807_01409_gb300.synth import Pattern
-    X, Y, Z = 0, 1, 2
-    S, P, O = pins.tiny_graph(31, 40, ids=6)
-    star = [{"op": "match", "pattern": Pattern(0, 2, 0, var=(X, -1, Y))},
-            {"op": "match", "pattern": Pattern(0, 3, 0, var=(X, -1, Z))},
-            {"op": "join", "inputs": [0, 1]}]
-    r = orc.execute(S, P, O, star)
-    want = pins.solutions(S, P, O, [((0, 2, 0), (X, -1, Y)), ((0, 3, 0), (X, -1, Z))], r.vars)
-    assert r.rows.tolist() == [list(w) for w in want]
-    chain = [{"op": "match", "pattern": Pattern(0, 0, 0, var=(X, -1, Y))},
-             {"op": "match", "pattern": Pattern(0, 4, 0, var=(Y, -1, Z))},
-             {"op": "join", "inputs": [0, 1]},
-             {"op": "project", "input": 2, "vars": [X, Z]}]
-    r = orc.execute(S, P, O, chain)
-    want = pins.solutions(S, P, O, [((0, 0, 0), (X, -1, Y)), ((0, 4, 0), (Y, -1, Z))], (X, Z))
-    assert r.rows.tolist() == [list(w) for w in want]
-    # FILTER (?Y in [2, 4]) over the chain's first pattern
-    flt = [{"op": "match", "pattern": Pattern(0, 0, 0, var=(X, -1, Y))},
-           {"op": "filter", "input": 0, "var": Y, "cmp": "range", "a": 2, "b": 4}]
-    r = orc.execute(S, P, O, flt)
-    want = [w for w in pins.solutions(S, P, O, [((0, 0, 0), (X, -1, Y))], (X, Y)) if 2 <= w[1] <= 4]
-    assert r.rows.tolist() == [list(w) for w in want]
-    # UNION of two branches with different variables
-    un = [{"op": "match", "pattern": Pattern(1, 0, 0, var=(-1, X, Y))},
-          {"op": "match", "pattern": Pattern(0, 2, 0, var=(Y, -1, Z))},
-          {"op": "union", "inputs": [0, 1]}]
-    r = orc.execute(S, P, O, un)
-    a = pins.solutions(S, P, O, [((1, 0, 0), (-1, X, Y))], (X, Y))
-    b = pins.solutions(S, P, O, [((0, 2, 0), (Y, -1, Z))], (Y, Z))
-    want = sorted({(x, y, 0) for x, y in a} | {(0, y, z) for y, z in b})
-    assert r.vars == (X, Y, Z) and r.rows.tolist() == [list(w) for w in want]
-
-
-# planted mistakes in the Python layer (oracle.py): rule evaluator and left join
-ENTAIL_MUTATIONS = [
+# planted mistakes in the Python layer (oracle.py): schemas, union, project, plans,
+# the rule evaluator and the left join
+PY_MUTATIONS = [
+    ("if v not in out:\n            out.append(v)", "out.append(v)"),                        # repeated var twice
+    ("rrest = [j for j, v in enumerate(Rv) if v not in Lv]", "rrest = [j for j, v in enumerate(Rv)]"),  # shared kept twice
+    ("a = np.zeros((t.n, len(uv)), np.int32)", "a = np.ones((t.n, len(uv)), np.int32)"),     # union pads with 1
+    ("a[:, uv.index(v)] = t.rows[:, j]", "a[:, j] = t.rows[:, j]"),                          # union ignores schema
+    ("cols = [t.vars.index(v) for v in vars_]", "cols = sorted(t.vars.index(v) for v in vars_)"),  # project order
+    ('r = filter(ev(nd["input"]), nd["var"], nd["cmp"], nd["a"], nd.get("b", 0))',
+     'r = ev(nd["input"])'),                                                                 # plan drops FILTER
+    ('r = union([ev(j) for j in nd["inputs"]])', 'r = union([ev(nd["inputs"][0])])'),        # plan: first branch only
     ("keys = np.unique(t1.rows[:, t1.vars.index(on)])", "keys = np.unique(t1.rows[:, 0])"),  # wrong column
     ("idx2 = cand[np.isin(col[cand], keys)] if cand.shape[0] else cand", "idx2 = cand"),  # no key restriction
     ('slot = r["data"].index(r["on"])', "slot = 0"),                                         # wrong join slot
@@ -113,10 +97,10 @@ ENTAIL_MUTATIONS = [
 ]
 
 
-@pytest.mark.parametrize("mut", range(len(ENTAIL_MUTATIONS)))
-def test_entail_pins_catch_planted_mistake(orc, mut, tmp_path):
+@pytest.mark.parametrize("mut", range(len(PY_MUTATIONS)))
+def test_python_layer_pins_catch_planted_mistake(orc, mut, tmp_path):
     import importlib.util
-    old, new = ENTAIL_MUTATIONS[mut]
+    old, new = PY_MUTATIONS[mut]
     src = open(orc.__file__).read()
     assert old in src, "mutation site vanished from oracle.py"
     bad = tmp_path / "oracle_entail_mut.py"
@@ -131,9 +115,9 @@ def test_entail_pins_catch_planted_mistake(orc, mut, tmp_path):
         sys.modules.pop("oracle_entail_mut", None)
     mod._SRC, mod._BUILD, mod._SO, mod._lib = orc._SRC, orc._BUILD, orc._SO, None
     failed = []
-    for pin in (pins.pin_entail_golden, pins.pin_entail_bruteforce, pins.pin_left_join_rowwise):
+    for pin in pins.ALL_PINS:
         try:
             pin(mod)
         except Exception:
             failed.append(pin.__name__)
-    assert failed, f"no pin caught entailment mutation {mut}: {new!r}"
+    assert failed, f"no pin caught Python-layer mutation {mut}: {new!r}"
