@@ -74,3 +74,62 @@ def test_pattern_array_matches_the_c_struct():
     c = tb.pattern_array([Pattern(0, 5, 0, var=(0, -1, 1))])
     t = tb.tid_pattern.from_buffer_copy(c.tobytes())
     assert (t.s, t.p, t.o, tuple(t.var)) == (0, 5, 0, (0, -1, 1))
+
+
+def test_binding_structs_and_constants_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C layout (size and every
+    field offset, as gcc lays them out) and the binding's constants equal the
+    header's macros: a mismatch would pass wrong arguments through the ABI."""
+    import ctypes
+    from paper_1807_01409_gb300 import binding as tb
+    structs = {
+        "tid_pattern": (tb.tid_pattern, ["s", "p", "o", "var", "reserved"]),
+        "tid_pred": (tb.tid_pred, ["var", "op", "a", "b"]),
+        "tid_plan_node": (tb.tid_plan_node, ["op", "n_in", ("in", "in_"), "pattern", "pred", "algo",
+                                              "n_vars", "vars"]),
+        "tid_rdfs_vocab": (tb.tid_rdfs_vocab, ["type", "domain", "range", "sub_property_of", "sub_class_of"]),
+        "tid_entail_stats": (tb.tid_entail_stats, ["res1", "dist1", "res2", "dist2", "all"]),
+        "tid_server_config": (tb.tid_server_config, ["workers", "max_wave", "batch_scans", "reserved",
+                                                      "budget_bytes"]),
+        "tid_server_stats": (tb.tid_server_stats, ["submitted", "completed", "failed", "waves",
+                                                    "max_wave_seen", "peak_admitted_bytes", "scan_patterns"]),
+    }
+    consts = {
+        "TID_OK": tb.TID_OK, "TID_ERR_ARG": tb.TID_ERR_ARG, "TID_ERR_ID": tb.TID_ERR_ID,
+        "TID_ERR_OOM": tb.TID_ERR_OOM, "TID_ERR_CAPACITY": tb.TID_ERR_CAPACITY,
+        "TID_ERR_TIMEOUT": tb.TID_ERR_TIMEOUT, "TID_ERR_CUDA": tb.TID_ERR_CUDA,
+        "TID_HOST": tb.TID_HOST, "TID_DEVICE": tb.TID_DEVICE, "TID_MAX_COLS": tb.TID_MAX_COLS,
+        "TID_MAX_MULTI": tb.TID_MAX_MULTI, "TID_BATCH_KEYS": tb.TID_BATCH_KEYS,
+        "TID_REQ_INDEX": tb.TID_REQ_INDEX, "TID_REQ_PLAN": tb.TID_REQ_PLAN,
+        "TID_JOIN_AUTO": tb.JOIN["auto"], "TID_JOIN_SORT_MERGE": tb.JOIN["sort_merge"],
+        "TID_JOIN_HASH": tb.JOIN["hash"], "TID_JOIN_LEFT": tb.TID_JOIN_LEFT,
+        **{f"TID_CMP_{k.upper()}": v for k, v in tb.CMP.items()},
+        **{f"TID_OP_{k.upper()}": v for k, v in tb.OP.items()},
+        **{f"TID_RULE_R{r}": r for r in tb.RULES},
+    }
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "tid.h"', "int main(void) {"]
+    for name, (_, fields) in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in fields:
+            c = f[0] if isinstance(f, tuple) else f
+            lines.append(f'printf("{name} {c} %zu\\n", offsetof({name}, {c}));')
+    for m in consts:
+        lines.append(f'printf("#{m} %lld\\n", (long long)({m}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    layout, macro = {}, {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        f = line.split()
+        if f[0].startswith("#"):
+            macro[f[0][1:]] = int(f[1])
+        else:
+            layout[(f[0], f[1])] = int(f[2])
+    for name, (cls, fields) in structs.items():
+        assert ctypes.sizeof(cls) == layout[(name, "size")], name
+        for f in fields:
+            c, py = (f if isinstance(f, tuple) else (f, f))
+            assert getattr(cls, py).offset == layout[(name, c)], (name, c)
+    assert macro == consts
