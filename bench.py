@@ -492,6 +492,7 @@ def run_ours(args, rank, world, local):
         barrier()
     ms = max_over_ranks(t_start.elapsed_time(t_end), world, "cuda")
     kernel_ms = [ev[k][j][0].elapsed_time(ev[k][j][1]) for k in range(args.steps) for j in range(nq)]
+    step_stats = step_span_stats(ev)
     total_kernel_ms = sum(kernel_ms)
     alg_bytes_step = sum(4 * b * store_np.n + 4 * h for b, h in zip(bound, hits))
     scanned_step = nq * store_np.n
@@ -561,6 +562,7 @@ def run_ours(args, rank, world, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "step_ms": step_stats,
             "config": {"workload": WORKLOAD if store_np.n == N_TRIPLES else
                        f"university-{store_np.n}: profiling size, not the benchmark workload",
                        "n_triples": store_np.n, "queries": nq,
@@ -586,6 +588,16 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def step_span_stats(ev):
+    """Best and median step time (ms, this rank) from per-launch event pairs
+    ev[step][launch] = (start, end): a step spans its first launch's start to its
+    last launch's end."""
+    spans = [steps[0][0].elapsed_time(steps[-1][1]) for steps in ev if steps]
+    if not spans:
+        return None
+    return {"best": min(spans), "median": statistics.median(spans), "steps": len(spans)}
 
 
 def _pct(x, q):

@@ -87,3 +87,23 @@ def test_all_cores_oracle_scan_equals_whole_store_scan():
     with ThreadPoolExecutor(max_workers=2) as pool:
         assert np.array_equal(bench._match_on_cores(oracle, tiny, (0, 0, 0), pool, 8),
                               np.arange(3, dtype=np.int32))
+
+
+def test_step_span_stats():
+    """Per-step spans from (start, end) event pairs: first start to last end."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Ev:
+        def __init__(self, t):
+            self.t = t
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    ev = [[(Ev(0.0), Ev(1.0)), (Ev(1.5), Ev(4.0))],
+          [(Ev(10.0), Ev(11.0)), (Ev(11.0), Ev(13.0))],
+          [(Ev(20.0), Ev(20.5)), (Ev(21.0), Ev(26.0))]]
+    st = bench.step_span_stats(ev)
+    assert st == {"best": 3.0, "median": 4.0, "steps": 3}
+    assert bench.step_span_stats([]) is None
