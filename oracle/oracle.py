@@ -52,6 +52,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 
 OPS = {"eq": 0, "ne": 1, "lt": 2, "le": 3, "gt": 4, "ge": 5, "range": 6}
 NESTED_LOOP_CAP = 100_000_000  # |L|*|R| above this switches to the sort-merge join
+JOIN_PATHS = {"nested": 0, "sortmerge": 0}  # joins run per path, for the parity log
 
 _lib = None
 
@@ -249,6 +250,7 @@ def join(Ls: TupleSet, Rs: TupleSet, method: str = "auto") -> TupleSet:
     if method == "auto":
         method = "nested" if Ls.n * Rs.n <= NESTED_LOOP_CAP else "sortmerge"
     f = {"nested": lib().or_join_nested, "sortmerge": lib().or_join_sortmerge}[method]
+    JOIN_PATHS[method] += 1
     Lr = np.ascontiguousarray(Ls.rows, np.int32)
     Rr = np.ascontiguousarray(Rs.rows, np.int32)
     args = (_p32(Lr), Ls.n, Ls.k, _p32(Rr), Rs.n, Rs.k, len(shared),

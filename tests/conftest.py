@@ -17,3 +17,12 @@ def orc():
     from oracle import oracle
     oracle.build()
     return oracle
+
+
+def pytest_terminal_summary(terminalreporter):
+    """The parity log names the oracle's join path: the nested loop below its
+    cap, its own sort-merge join above it."""
+    mod = sys.modules.get("oracle.oracle")
+    if mod is not None and any(mod.JOIN_PATHS.values()):
+        terminalreporter.write_line(
+            "oracle joins: {nested} nested-loop, {sortmerge} sort-merge".format(**mod.JOIN_PATHS))
