@@ -111,6 +111,22 @@ def test_shards_concatenate_to_the_whole_store(ctx, orc, world):
             tb.tid_store_free(sh)
 
 
+EXTREME = np.array([1, 2, 3, 2 ** 30 - 1, 2 ** 30, 2 ** 30 + 1, 2 ** 31 - 2, 2 ** 31 - 1], np.int32)
+
+
+def test_extreme_ids(ctx, orc):
+    """IDs at both ends of the positive int32 range (entities just below the
+    literal base 2^30, literals above it, the largest ID)."""
+    rng = np.random.default_rng(77)
+    n = 300_001
+    S, P, O = (EXTREME[rng.integers(0, EXTREME.size, n)] for _ in range(3))
+    store = tb.tid_load(ctx, _dev(S), _dev(P), _dev(O), copy=1)
+    vals = [0] + EXTREME.tolist()
+    for key in [(a, b, c) for a in vals[::3] for b in vals[::2] for c in vals[::3]]:
+        assert np.array_equal(_match(ctx, store, key), orc.match(S, P, O, key)), key
+    tb.tid_store_free(store)
+
+
 def test_dense_and_empty_results(ctx, orc):
     n = 300_000
     S = np.arange(1, n + 1, dtype=np.int32)
