@@ -66,6 +66,33 @@ def test_noalloc_equals_tid_match_on_consecutive_calls(which):
         tb.tid_ctx_destroy(ctx)
 
 
+def test_noalloc_cuts_at_capacity():
+    """A buffer shorter than the result: the first cap positions are written, the
+    buffer past cap is untouched and the count is the full match count."""
+    from paper_1807_01409_gb300 import build
+    build.build()
+    st = synth.university_store(200_003)
+    cols = [torch.from_numpy(c).cuda() for c in (st.s, st.p, st.o)]
+    ctx = tb.tid_ctx_create(0, None)
+    store = tb.tid_load(ctx, *cols, copy=0)
+    try:
+        want = _reference(ctx, store, synth.Pattern(0, int(st.p[0]), 0))
+        assert want.shape[0] > 100
+        for cap in (0, 1, 37, want.shape[0] - 1):
+            out = torch.full((want.shape[0] + 64,), -7, dtype=torch.int32, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            torch.cuda.synchronize()
+            tb.tid_match_noalloc(0, None, cols[0], cols[1], cols[2], (0, int(st.p[0]), 0), out, cnt, cap=cap)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            assert int(cnt.item()) == want.shape[0], cap
+            assert np.array_equal(got[:cap], want[:cap]), cap
+            assert (got[cap:] == -7).all(), cap
+    finally:
+        tb.tid_store_free(store)
+        tb.tid_ctx_destroy(ctx)
+
+
 def test_noalloc_rejects_bad_arguments():
     from paper_1807_01409_gb300 import build
     build.build()
