@@ -440,7 +440,10 @@ int tid_server_wait(tid_server *srv, int64_t id, int64_t timeout_ms);
 int tid_server_result(tid_server *srv, int64_t id, int *status, int *cols, int8_t *vars, int64_t *rows,
                       const int32_t **data, int64_t *latency_ns);
 
-/* Forget a finished request and its host data. */
+/* Forget a finished request and its host data (the data pointer returned by
+ * tid_server_result is invalid afterwards).  Any thread may call any
+ * tid_server_* function; a release while another thread waits on the same id
+ * is safe (that wait returns TID_OK, the request having finished). */
 int tid_server_release(tid_server *srv, int64_t id);
 
 int tid_server_get_stats(tid_server *srv, tid_server_stats *out);

@@ -18,6 +18,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -75,7 +76,8 @@ struct tid_server {
     std::condition_variable cv_work;  // queue changed, memory freed, or stop
     std::condition_variable cv_done;  // a request finished
     std::deque<Request *> queue;
-    std::unordered_map<int64_t, std::unique_ptr<Request>> reqs;
+    // shared: a waiter keeps its request alive if another thread releases it
+    std::unordered_map<int64_t, std::shared_ptr<Request>> reqs;
     int64_t next_id = 1;
     int64_t admitted_bytes = 0;
     int admitted_reqs = 0;
@@ -402,8 +404,12 @@ extern "C" int tid_server_submit(tid_server *S, int kind, const tid_plan_node *n
     } else {
         return fail(TID_ERR_ARG, "tid_server_submit: unknown kind %d", kind);
     }
-    std::unique_ptr<Request> r(new (std::nothrow) Request());
-    if (!r) return fail(TID_ERR_OOM, "host allocation");
+    std::shared_ptr<Request> r;
+    try {
+        r = std::make_shared<Request>();
+    } catch (const std::bad_alloc &) {
+        return fail(TID_ERR_OOM, "host allocation");
+    }
     r->kind = kind;
     r->nodes.assign(nodes, nodes + n_nodes);
     r->arrival_ns = arrival_ns > 0 ? arrival_ns : now_ns();
@@ -427,7 +433,8 @@ extern "C" int tid_server_wait(tid_server *S, int64_t id, int64_t timeout_ms) {
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->reqs.find(id);
     if (it == S->reqs.end()) return fail(TID_ERR_ARG, "tid_server_wait: unknown request %lld", (long long)id);
-    Request *r = it->second.get();
+    const std::shared_ptr<Request> keep = it->second;  // alive across the wait
+    Request *r = keep.get();
     if (timeout_ms < 0) {
         S->cv_done.wait(lk, [&] { return r->done; });
     } else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; })) {
