@@ -78,7 +78,10 @@ typedef struct {
 
 /* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t
  * owned by the caller (it must outlive the context), or NULL for a stream the
- * context creates and owns.  On success *out receives the context. */
+ * context creates and owns.  On success *out receives the context.  A process
+ * drives one GPU (launch shapes are worked out once per process): a context
+ * on another device than the first one any call of the process used fails
+ * with TID_ERR_ARG.  Run one process per GPU. */
 int tid_ctx_create(int device, void *cuda_stream, tid_ctx **out);
 
 /* Wait for all work on the context's stream; returns TID_ERR_TIMEOUT if an
@@ -180,7 +183,8 @@ int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, 
  * address (with that device current); make that first call before any stream
  * capture.  All calls share the array and it keeps the last call's contents:
  * calls whose GPU work overlaps race on it, so order them (one stream, or
- * events).  Errors: TID_ERR_ARG (bad pointers, sizes or device), TID_ERR_ID
+ * events).  Errors: TID_ERR_ARG (bad pointers, sizes or device, or another
+ * device than this process's, as for tid_ctx_create), TID_ERR_ID
  * (negative pattern value), TID_ERR_CAPACITY (a GPU that would run more than
  * TID_NOALLOC_MAX_CHUNKS chunks per launch), TID_ERR_CUDA. */
 #define TID_NOALLOC_MAX_CHUNKS 4096

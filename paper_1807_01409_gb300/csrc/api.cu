@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "ops.cuh"
@@ -31,6 +32,17 @@ int fail_cuda(cudaError_t e, const char *what) {
 }
 
 void clear_error() { g_err.clear(); }
+
+// One GPU per process: launch shapes and shared-memory opt-ins are worked out
+// once per process, on the device of its first context (or no-alloc scan).
+static std::atomic<int> g_device{-1};
+
+int claim_device(int device) {
+    int first = -1;
+    if (g_device.compare_exchange_strong(first, device) || first == device) return TID_OK;
+    return fail(TID_ERR_ARG, "device %d: this process already runs on device %d (one GPU per process)", device,
+                first);
+}
 
 int launch_check(const char *what) {
     cudaError_t e = cudaGetLastError();
@@ -270,6 +282,7 @@ extern "C" int tid_ctx_create(int device, void *cuda_stream, tid_ctx **out) {
     int ndev = 0;
     TID_TRY_CUDA(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
     if (device < 0 || device >= ndev) return fail(TID_ERR_ARG, "tid_ctx_create: no device %d", device);
+    TID_TRY(claim_device(device));
     DeviceGuard g(device);
     tid_ctx *c = new (std::nothrow) tid_ctx();
     if (!c) return fail(TID_ERR_OOM, "host allocation");

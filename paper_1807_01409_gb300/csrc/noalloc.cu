@@ -71,6 +71,7 @@ extern "C" int tid_match_noalloc(int device, void *cuda_stream, const int32_t *s
     TID_TRY_CUDA(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
     if (device < 0 || device >= ndev || device >= NOALLOC_MAX_DEVICES)
         return fail(TID_ERR_ARG, "tid_match_noalloc: no device %d", device);
+    TID_TRY(claim_device(device));
 
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceScratch *d = nullptr;

@@ -21,6 +21,9 @@ namespace tid {
 int fail(int code, const char *fmt, ...);
 int fail_cuda(cudaError_t e, const char *what);
 void clear_error();
+// TID_OK if `device` is this process's GPU (the first device any call used),
+// else TID_ERR_ARG
+int claim_device(int device);
 
 #define TID_TRY_CUDA(expr, what)                                   \
     do {                                                           \
