@@ -107,3 +107,25 @@ def test_step_span_stats():
     st = bench.step_span_stats(ev)
     assert st == {"best": 3.0, "median": 4.0, "steps": 3}
     assert bench.step_span_stats([]) is None
+
+
+def test_traffic_record_follows_the_kernel_source(tmp_path):
+    """The committed DRAM-traffic record is used only while the scan kernel's
+    source (its section of match.cu) is the one it was captured on."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_1807_01409_gb300", "csrc", "match.cu")
+    text = open(src).read()
+    rec = bench._traffic_record(src)
+    if rec is not None:  # recorded on this kernel: the region hash matches
+        assert rec["kernel_region_sha1"] == bench._kernel_region_sha1(src)
+    outside = tmp_path / "outside.cu"  # an edit outside the kernel's section keeps the record
+    outside.write_text("// host-side note\n" + text)
+    assert (bench._traffic_record(str(outside)) is None) == (rec is None)
+    a = text.index(bench.K1_REGION[0]) + len(bench.K1_REGION[0])
+    inside = tmp_path / "inside.cu"  # an edit inside it drops the record
+    inside.write_text(text[:a] + "\n// changed\n" + text[a:])
+    assert bench._traffic_record(str(inside)) is None
+    gone = tmp_path / "gone.cu"  # section markers missing: no record
+    gone.write_text(text.replace(bench.K1_REGION[0], ""))
+    assert bench._traffic_record(str(gone)) is None
