@@ -37,6 +37,18 @@ void clear_error() { g_err.clear(); }
 // once per process, on the device of its first context (or no-alloc scan).
 static std::atomic<int> g_device{-1};
 
+int sm_count() {
+    static std::atomic<int> cached[64];  // zero: not yet queried
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    int v = dev < 64 ? cached[dev].load(std::memory_order_relaxed) : 0;
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        if (dev < 64) cached[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 int claim_device(int device) {
     int first = -1;
     if (g_device.compare_exchange_strong(first, device) || first == device) return TID_OK;
@@ -486,7 +498,7 @@ extern "C" int tid_set_to_host(tid_set *set, int32_t *buf, int64_t cap_rows, int
         cudaError_t e = cudaMemcpyAsync(dcols, set->col, sizeof(int32_t *) * set->k, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) {
             const int64_t blocks = ceil_div(rows * set->k, 256);
-            k_interleave<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, ctx->stream>>>(
+            k_interleave<<<grid_for(blocks, 1), 256, 0, ctx->stream>>>(
                 dcols, set->k, set->d_rows, (int32_t *)tmp);
             e = cudaGetLastError();
         }

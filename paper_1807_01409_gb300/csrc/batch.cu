@@ -264,17 +264,6 @@ __global__ void __launch_bounds__(256) k_batch_scan(uint32_t *counts, int64_t GW
     }
 }
 
-int sm_count_kb() {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0, v = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
-        cached = v;
-    }
-    return cached;
-}
-
 // resident CTAs of both passes with `smem` bytes of dynamic shared memory
 template <int U, bool SKIP>
 int kb_grid(size_t smem, unsigned *grid) {
@@ -295,7 +284,7 @@ int kb_grid(size_t smem, unsigned *grid) {
     TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, k_batch<U, false, SKIP>, KB_THREADS, smem),
                  "occupancy");
     if (std::min(v, w) < 1) return fail(TID_ERR_CAPACITY, "tid_match_batch: %zu bytes of shared memory per CTA", smem);
-    *grid = (unsigned)(std::min(v, w) * sm_count_kb());
+    *grid = (unsigned)(std::min(v, w) * sm_count());
     return TID_OK;
 }
 

@@ -200,8 +200,7 @@ extern "C" int tid_entail(tid_ctx *ctx, const tid_store *st, int rule, const tid
         } else {
             const int32_t v = term[R.then_term];
             if (rows > 0) {
-                const int64_t blocks = std::min<int64_t>(ceil_div(rows, 256), 152 * 8);
-                k_fill_i32<<<(unsigned)blocks, 256, 0, stream>>>(O->col[slot], rows, v);
+                k_fill_i32<<<grid_for(rows, 256, 8), 256, 0, stream>>>(O->col[slot], rows, v);
                 rc = launch_check("k_fill_i32");
             }
             O->lo[slot] = O->hi[slot] = (uint32_t)v ^ 0x80000000u;

@@ -67,11 +67,6 @@ __device__ __forceinline__ void block_add_u64(unsigned long long v, unsigned lon
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
 }
 
-unsigned grid_for(int64_t n, int threads) {
-    const int64_t b = ceil_div(n, threads);
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
-}
-
 // ---- sort-merge --------------------------------------------------------------
 
 // per left row: [lo, hi) of equal keys in the sorted right keys

@@ -245,17 +245,6 @@ __global__ void k1_iota(int64_t n, int32_t *__restrict__ out, int64_t cap,
     }
 }
 
-int sm_count() {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0, v = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
-        cached = v;
-    }
-    return cached;
-}
-
 // resident CTAs of one k1 instance (opts the kernel into 64 KB of dynamic shared memory)
 template <int MASK, bool VEC>
 unsigned resident_ctas() {

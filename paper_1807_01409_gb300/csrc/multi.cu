@@ -239,17 +239,6 @@ k2_match_multi(const int32_t *__restrict__ S, const int32_t *__restrict__ P, con
     }
 }
 
-int sm_count_k2() {
-    static int cached = 0;
-    if (!cached) {
-        int dev = 0, v = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
-        cached = v;
-    }
-    return cached;
-}
-
 template <int U, bool VEC>
 unsigned resident_k2() {
     static unsigned cached = 0;
@@ -259,7 +248,7 @@ unsigned resident_k2() {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k2_match_multi<U, VEC>, K2_THREADS, k2_bitmap_bytes<U>()) !=
                 cudaSuccess || v <= 0)
             v = 1;
-        cached = (unsigned)(v * sm_count_k2());
+        cached = (unsigned)(v * sm_count());
     }
     return cached;
 }

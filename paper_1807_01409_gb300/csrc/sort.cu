@@ -320,11 +320,6 @@ __global__ void k_set_rows(int64_t *d_rows, int64_t *h_rows, int64_t n) {
     *h_rows = n;
 }
 
-unsigned grid_for(int64_t n, int threads) {
-    const int64_t b = ceil_div(n, threads);
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
-}
-
 struct Scratch {  // stream-ordered temporaries freed on scope exit
     tid_ctx *ctx;
     std::vector<void *> ptrs;

@@ -179,4 +179,14 @@ unsigned int match_scratch_words();  // status words one K1 launch may need
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+int sm_count();  // SMs of the current device (queried once per device)
+
+// Grid of a grid-stride kernel: one CTA per `per_cta` items, at most `per_sm`
+// CTAs per SM, at least one.
+inline unsigned grid_for(int64_t n, int64_t per_cta, int per_sm = 16) {
+    const int64_t b = ceil_div(n, per_cta);
+    const int64_t cap = (int64_t)sm_count() * per_sm;
+    return (unsigned)(b < 1 ? 1 : (b < cap ? b : cap));
+}
+
 }  // namespace tid
