@@ -265,6 +265,13 @@ def run_reference(args, rank, world):
 # the other rows of the path, each through the C ABI at full size
 # ---------------------------------------------------------------------------
 
+def gather_sectors(idx) -> int:
+    """Distinct 32-byte sectors (8 int32) that a gather at these ascending row
+    indices touches in one int32 column."""
+    sec = np.asarray(idx, np.int64) >> 3
+    return 0 if sec.size == 0 else int(np.count_nonzero(np.diff(sec)) + 1)
+
+
 def measure_rows(tb, ctx, store, st, stream, peak, with_oracle=True, reps=3):
     """Multi-pattern scan, bind (+filter fused), filter, sort (project), join (both
     algorithms), union and plan execution on the university store.  For each:
@@ -346,6 +353,11 @@ def measure_rows(tb, ctx, store, st, stream, peak, with_oracle=True, reps=3):
                                     lo_v, hi_v), scale=h / samp) if orc else None
     out["a3_bind_filter"] = entry(ms, 4 * h + 8 * h + 8 * m + 16 * m, cpu_ms, rows_in=h, rows_out=m,
                                   oracle_sample=f"first {samp} indices, time scaled x{h / samp:.1f}")
+    # the gathers move whole 32-byte sectors: the least DRAM traffic they can cause
+    sect = gather_sectors(tb.tid_set_to_host(idx)[:, 0])
+    sb = 2 * 32 * sect + 4 * h + 8 * m + 16 * m
+    out["a3_bind_filter"].update({"sector_bytes": int(sb), "gathered_sectors_per_column": sect,
+                                  "frac_of_measured_peak_sector_bytes": round(sb / (ms / 1e3) / 1e9 / peak, 4)})
 
     # a4: filter on a bound set (x, v) of all (?x p1 ?v)
     full = tb.tid_bind(ctx, store, lit, idx, [])

@@ -129,3 +129,15 @@ def test_traffic_record_follows_the_kernel_source(tmp_path):
     gone = tmp_path / "gone.cu"  # section markers missing: no record
     gone.write_text(text.replace(bench.K1_REGION[0], ""))
     assert bench._traffic_record(str(gone)) is None
+
+
+def test_gather_sectors():
+    """Sectors of 8 int32 touched by a gather at ascending indices."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.gather_sectors(np.array([], np.int32)) == 0
+    assert bench.gather_sectors(np.array([0, 1, 7], np.int32)) == 1
+    assert bench.gather_sectors(np.array([7, 8], np.int32)) == 2
+    assert bench.gather_sectors(np.array([0, 16, 17, 40, 2 ** 31 - 1], np.int32)) == 4
+    idx = np.sort(np.random.default_rng(3).choice(10_000, 3000, replace=False)).astype(np.int32)
+    assert bench.gather_sectors(idx) == np.unique(idx // 8).size
