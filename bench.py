@@ -253,7 +253,9 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "n_triples": store.n, "queries": len(queries),
+            "config": {"workload": WORKLOAD if store.n == N_TRIPLES else
+                       f"university-{store.n}: profiling size, not the benchmark workload",
+                       "n_triples": store.n, "queries": len(queries),
                        "sample_per_step": per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{per_step} queries per step over the full store"},
