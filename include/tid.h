@@ -122,6 +122,10 @@ int tid_load(tid_ctx *ctx, const int32_t *s, const int32_t *p, const int32_t *o,
 int tid_store_info(const tid_store *st, int64_t *n, const int32_t **s,
                    const int32_t **p, const int32_t **o);
 
+/* Free a store (NULL accepted).  Its own copy of the columns is released
+ * stream-ordered on the context stream, so work already queued there that
+ * reads it finishes first; borrowed columns are left to their owner.  Sets
+ * made from the store hold their own memory and stay valid. */
 int tid_store_free(tid_store *st);
 
 /* ------------------------------------------------------------------------ */
@@ -322,6 +326,10 @@ int tid_set_info(const tid_set *set, int *cols, int64_t *capacity,
  * and TID_ERR_CAPACITY is returned.  Synchronises. */
 int tid_set_to_host(tid_set *set, int32_t *buf, int64_t cap_rows, int64_t *rows_out);
 
+/* Free a set (NULL accepted).  Its memory is released stream-ordered on its
+ * context's stream (work already queued there that reads it finishes first);
+ * a set that views a shared allocation (tid_match_batch lists) releases it
+ * with the last such set. */
 int tid_set_free(tid_set *set);
 
 /* ------------------------------------------------------------------------ */
@@ -450,6 +458,7 @@ int tid_server_result(tid_server *srv, int64_t id, int *status, int *cols, int8_
  * is safe (that wait returns TID_OK, the request having finished). */
 int tid_server_release(tid_server *srv, int64_t id);
 
+/* Counters since tid_server_create (see tid_server_stats). */
 int tid_server_get_stats(tid_server *srv, tid_server_stats *out);
 
 /* Finish every queued request, stop the workers and free the server. */
