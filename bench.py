@@ -548,28 +548,27 @@ def run_ours(args, rank, world, local):
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(store_np, synth.university_queries(store_np))
-    # the other rows are per-GPU characteristics: measured in single-GPU runs only
+    # the other rows are per-GPU characteristics: measured in single-GPU runs only;
+    # a row that fails reports its error and the line is printed all the same
     extra = world == 1
+    oracle_too = rank == 0 and world == 1 and not args.no_cpu_baseline
     rows = None
     if extra and not args.no_rows:
-        rows = measure_rows(tb, ctx, store, store_np, stream, _peaks()[0],
-                            with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+        rows = _row(lambda: measure_rows(tb, ctx, store, store_np, stream, _peaks()[0], with_oracle=oracle_too))
 
     tb.tid_store_free(store)
     del cols
     torch.cuda.empty_cache()
     entail = None
     if extra and not args.no_entail:
-        entail = measure_entail(tb, ctx, stream, store_np, _peaks()[0],
-                                with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+        entail = _row(lambda: measure_entail(tb, ctx, stream, store_np, _peaks()[0], with_oracle=oracle_too))
     batch = None
     if extra and not args.no_batch:
-        batch = measure_batch(tb, ctx, stream, _peaks()[0],
-                              with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
-    tb.tid_ctx_destroy(ctx)
+        batch = _row(lambda: measure_batch(tb, ctx, stream, _peaks()[0], with_oracle=oracle_too))
+    _row(lambda: tb.tid_ctx_destroy(ctx))
     serve = None
     if extra and not args.no_serve:
-        serve = measure_serve(tb, with_oracle=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+        serve = _row(lambda: measure_serve(tb, with_oracle=oracle_too))
 
     if rank == 0:
         line = {
@@ -602,6 +601,14 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _row(fn):
+    """fn()'s result, or {"error": ...} if it raises."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001 -- reported in the JSON line
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def step_span_stats(ev):

@@ -141,3 +141,13 @@ def test_gather_sectors():
     assert bench.gather_sectors(np.array([0, 16, 17, 40, 2 ** 31 - 1], np.int32)) == 4
     idx = np.sort(np.random.default_rng(3).choice(10_000, 3000, replace=False)).astype(np.int32)
     assert bench.gather_sectors(idx) == np.unique(idx // 8).size
+
+
+def test_failed_row_is_reported_not_raised():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench._row(lambda: {"a": 1}) == {"a": 1}
+
+    def boom():
+        raise RuntimeError("no device")
+    assert bench._row(boom) == {"error": "RuntimeError: no device"}
