@@ -58,22 +58,6 @@ def test_every_mask_ragged(ctx, orc, n):
     tb.tid_store_free(store)
 
 
-def test_extreme_ids(ctx, orc):
-    """Every key over IDs at both ends of the positive int32 range, including
-    the largest, as one batch."""
-    ext = np.array([1, 2, 2 ** 30 - 1, 2 ** 30, 2 ** 31 - 2, 2 ** 31 - 1], np.int32)
-    rng = np.random.default_rng(78)
-    n = 200_003
-    S, P, O = (ext[rng.integers(0, ext.size, n)] for _ in range(3))
-    store = tb.tid_load(ctx, _dev(S), _dev(P), _dev(O), copy=1)
-    vals = [0] + ext.tolist()
-    keys = [(a, b, c) for a in vals for b in vals for c in vals]
-    got = _lists(tb.tid_match_batch(ctx, store, keys))
-    for k, g in zip(keys, got):
-        assert np.array_equal(g, orc.match(S, P, O, k)), k
-    tb.tid_store_free(store)
-
-
 def test_tiny_store_with_repeats(ctx, orc):
     st = synth.tiny_store()
     store = tb.tid_load(ctx, *[_dev(c) for c in (st.s, st.p, st.o)], copy=0)

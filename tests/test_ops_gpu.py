@@ -290,38 +290,6 @@ def test_worked_example_plan(ctx):
     tb.tid_store_free(st)
 
 
-@pytest.mark.parametrize("algo", ["sort_merge", "hash"])
-def test_extreme_id_plans(ctx, orc, algo):
-    """Plans over IDs at both ends of the positive int32 range: packed sort keys
-    of 31 bits per column (two columns in 64 bits, three past it), joins, a
-    union, a literal-range filter and a projection."""
-    vals = np.r_[np.arange(1, 17), np.arange(2 ** 30 - 16, 2 ** 30 + 16), np.arange(2 ** 31 - 16, 2 ** 31)]
-    vals = vals.astype(np.int64)
-    rng = np.random.default_rng(79)
-    t = np.unique(np.stack([rng.choice(vals, 60_000) for _ in range(3)], axis=1), axis=0)
-    t = t[rng.permutation(t.shape[0])].astype(np.int32)
-    S, P, O = t[:, 0].copy(), t[:, 1].copy(), t[:, 2].copy()
-    st = _store(ctx, S, P, O)
-    p1, p2 = int(vals[0]), int(vals[-1])
-    X, Y, Z, Q = 0, 1, 2, 3
-    plans = [
-        [{"op": "match", "pattern": synth.Pattern(0, p1, 0, var=(X, -1, Y))},
-         {"op": "match", "pattern": synth.Pattern(0, p2, 0, var=(Y, -1, Z))},
-         {"op": "join", "inputs": [0, 1], "algo": algo},
-         {"op": "project", "input": 2, "vars": [Z, X]}],
-        [{"op": "match", "pattern": synth.Pattern(0, 0, 0, var=(X, Q, Y))},
-         {"op": "match", "pattern": synth.Pattern(0, p2, 0, var=(Y, -1, Z))},
-         {"op": "join", "inputs": [0, 1], "algo": algo}],
-        [{"op": "match", "pattern": synth.Pattern(0, p1, 0, var=(X, -1, Y))},
-         {"op": "match", "pattern": synth.Pattern(0, p2, 0, var=(X, -1, Z))},
-         {"op": "union", "inputs": [0, 1]},
-         {"op": "filter", "input": 2, "var": X, "cmp": "range", "a": 2 ** 30, "b": 2 ** 31 - 1}],
-    ]
-    for plan in plans:
-        _same(_host(tb.tid_exec(ctx, st, plan)), orc.execute(S, P, O, plan))
-    tb.tid_store_free(st)
-
-
 @pytest.mark.parametrize("algo", ["auto", "sort_merge", "hash"])
 def test_university_plans(ctx, orc, algo):
     st_np = synth.university_store(1_000_000)
