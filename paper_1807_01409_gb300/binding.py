@@ -159,6 +159,24 @@ def last_error() -> str:
     return lib().tid_last_error().decode()
 
 
+def _rows(x):
+    """Length of an array or tensor argument, None for a raw address."""
+    return int(x.shape[0]) if hasattr(x, "shape") and len(x.shape) > 0 else None
+
+
+def _int_dtype(x, name, bits):
+    if hasattr(x, "dtype") and str(x.dtype) not in (f"int{bits}", f"torch.int{bits}"):
+        raise TypeError(f"{name} must be int{bits}")
+
+
+def _within(n, name, *arrays):
+    """n elements must fit every array argument (the library trusts the sizes)."""
+    for a in arrays:
+        L = _rows(a)
+        if L is not None and n > L:
+            raise ValueError(f"{name} = {n} exceeds an argument of length {L}")
+
+
 def _check(rc, what):
     if rc != TID_OK:
         raise TidError(rc, f"{what}: {last_error()}")
@@ -209,6 +227,7 @@ def tid_load(ctx, s, p, o, n=None, where=None, copy=1):
             raise ValueError("store columns must be contiguous")
         if hasattr(c, "is_contiguous") and not c.is_contiguous():
             raise ValueError("store columns must be contiguous")
+    _within(int(n), "n", s, p, o)
     out = _vp()
     _check(lib().tid_load(ctx, _ptr(s), _ptr(p), _ptr(o), int(n), int(where), int(copy), C.byref(out)),
            "tid_load")
@@ -257,6 +276,9 @@ def tid_set_to_host(set_, buf=None):
     rows = tid_set_rows(set_)
     if buf is None:
         buf = np.empty((rows, info["cols"]), np.int32)
+    elif (not isinstance(buf, np.ndarray) or buf.dtype != np.int32 or buf.ndim != 2
+          or buf.shape[1] != info["cols"] or not buf.flags["C_CONTIGUOUS"]):
+        raise ValueError(f"buf must be a C-contiguous int32 array of shape (rows, {info['cols']})")
     got = C.c_int64()
     _check(lib().tid_set_to_host(set_, _ptr(buf) if buf.size else None, buf.shape[0], C.byref(got)),
            "tid_set_to_host")
@@ -285,6 +307,12 @@ def tid_match_noalloc(device, stream, s, p, o, pattern, out, count, n=None, cap=
     device addresses; stream as int or None)."""
     n = int(s.shape[0]) if n is None else int(n)
     cap = int(out.shape[0]) if cap is None else int(cap)
+    for c in (s, p, o, out):
+        _int_dtype(c, "columns and out", 32)
+    _int_dtype(count, "count", 64)
+    _within(n, "n", s, p, o)
+    _within(cap, "cap", out)
+    _within(1, "count", count)
     _check(lib().tid_match_noalloc(int(device), stream if stream else None, _ptr(s), _ptr(p), _ptr(o), n,
                                    as_pattern(pattern), _ptr(out), cap, _ptr(count)), "tid_match_noalloc")
 

@@ -133,3 +133,25 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
             c, py = (f if isinstance(f, tuple) else (f, f))
             assert getattr(cls, py).offset == layout[(name, c)], (name, c)
     assert macro == consts
+
+
+def test_binding_checks_sizes_before_calling():
+    """Sizes the library must trust are checked in the binding: a length or a
+    capacity beyond an argument's own length, or a wrong integer width, raises
+    before anything reaches the device (no GPU needed here)."""
+    import numpy as np
+    from paper_1807_01409_gb300 import binding as tb
+    a = np.ones(8, np.int32)
+    with pytest.raises(ValueError):
+        tb.tid_load(None, a, a, a, n=9)
+    with pytest.raises(TypeError):
+        tb.tid_load(None, a, a.astype(np.int64), a)
+    out, cnt = np.zeros(8, np.int32), np.zeros(1, np.int64)
+    with pytest.raises(ValueError):
+        tb.tid_match_noalloc(0, None, a, a, a, (0, 1, 0), out, cnt, n=9)
+    with pytest.raises(ValueError):
+        tb.tid_match_noalloc(0, None, a, a, a, (0, 1, 0), out, cnt, cap=9)
+    with pytest.raises(TypeError):
+        tb.tid_match_noalloc(0, None, a, a, a, (0, 1, 0), out, np.zeros(1, np.int32))
+    with pytest.raises(ValueError):
+        tb.tid_match_noalloc(0, None, a, a, a, (0, 1, 0), out, np.zeros(0, np.int64))
