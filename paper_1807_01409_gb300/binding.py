@@ -497,6 +497,11 @@ class Server:
         cfg = tid_server_config(int(workers), int(max_wave), 1 if batch_scans else 0, 0, int(budget_bytes))
         h = _vp()
         n = int(s.shape[0])
+        for c in (s, p, o):
+            _int_dtype(c, "store columns", 32)
+            if not (hasattr(c, "is_cuda") and c.is_cuda):
+                raise TypeError("the server borrows device columns (torch CUDA tensors)")
+        _within(n, "n", p, o)
         _check(lib().tid_server_create(int(device), _ptr(s), _ptr(p), _ptr(o), n, C.byref(cfg), C.byref(h)),
                "tid_server_create")
         self.h = h
