@@ -1,15 +1,19 @@
 // Single-pass row compaction over tuple sets, and a device-wide exclusive scan.
 //
-// One kernel template serves three operators that keep a subset of rows in
+// One kernel template serves the operators that keep a subset of rows in
 // their original order and write k output columns:
-//   * bind    -- from triple indices, the terms at a pattern's variable slots,
-//                dropping rows whose repeated variable disagrees; the FILTER
-//                predicates of the subquery are applied in the same pass
-//                (Section 4.3: the filter is applied while the matched triples
-//                are extracted into the subquery's vector);
-//   * filter  -- a predicate on one column of a set;
-//   * unique  -- after a sort, a row is kept when it differs from its
-//                predecessor in sorted order (DISTINCT, Section 4.3).
+//   * bind     -- from triple indices, the terms at a pattern's variable slots,
+//                 dropping rows whose repeated variable disagrees; the FILTER
+//                 predicates of the subquery are applied in the same pass
+//                 (Section 4.3: the filter is applied while the matched triples
+//                 are extracted into the subquery's vector);
+//   * filter   -- a predicate on one column of a set;
+//   * unique   -- after a sort, a row is kept when it differs from its
+//                 predecessor in sorted order (DISTINCT, Section 4.3), on
+//                 column rows or on packed row keys;
+//   * semijoin -- the entailment's keyed store pass (Section 5): a store triple
+//                 is kept when its term at the join position is one of the
+//                 first search's distinct terms (a hash probe).
 // A CTA owns 2048 consecutive rows (256 threads x 8, striped so each warp
 // instruction touches 32 consecutive rows); ranks come from ballots, the
 // tile offset from the decoupled look-back (lookback.cuh).
