@@ -17,6 +17,10 @@
 // scatter writes runs of equal digits contiguously).
 // Bytes per pass: w n (upsweep) + w n read + w n written (downsweep), w = key
 // bytes (4 or 8; 4 + 4 with the permutation).
+//
+// Sets of at most 4096 packed rows skip the passes: one CTA loads the keys into
+// shared memory, bitonic-sorts them, flags and block-scans the distinct ones
+// and unpacks them -- one launch, as the many small sets of a plan need.
 
 #include <algorithm>
 
