@@ -25,7 +25,18 @@ stand in for them with the same kind of skew):
                     frequencies, typed subject classes, 60% entity-valued and
                     40% literal-valued objects); 200M triples at full size, any
                     smaller size for parity runs; 64 single-pattern queries with
-                    target selectivity log-uniform on [1e-6, 0.3].
+                    target selectivity log-uniform on [1e-6, 0.3]; plans of
+                    star and chain joins, unions and literal-range filters.
+* ``university_store_torch`` -- the same recipe drawn on the GPU with torch
+                    (500M / 1B triples in seconds; other values than the host
+                    generator's), for the batched and the serving workloads.
+* ``batch_queries`` -- 4096 single-pattern queries of all seven bound-position
+                    shapes with result sizes log-uniform on [1, 1e7].
+* ``serving_requests`` -- a Poisson request stream (index lookups, two-pattern
+                    star joins, unions and filters) with arrival times.
+* ``rdfs_schema`` -- an RDFS schema over the university classes and predicates
+                    (subClassOf trees, domain/range, subPropertyOf chains) for
+                    the entailment rules of Section 5.
 
 Every store is a set: duplicate triples are removed and the store topped up to
 exactly ``n`` triples, then put in a seeded random order (the store is neither
