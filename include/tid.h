@@ -102,6 +102,15 @@ const char *tid_last_error(void);
  * usable. */
 int tid_ctx_inject_alloc_failure(tid_ctx *ctx, int64_t after);
 
+/* Testing aid for failure detection (the paper has no counterpart): runs on
+ * the context stream one CTA that waits, with the library's bounded in-kernel
+ * wait, at a barrier no other CTA reaches; after `polls` polls (1 .. 2^21) it
+ * gives up and sets the context's error word, as a stalled look-back or grid
+ * barrier would.  Synchronises and returns what the context then reports:
+ * TID_ERR_TIMEOUT (reported once; the context stays usable).  TID_ERR_ARG for
+ * polls out of range. */
+int tid_ctx_test_bounded_wait(tid_ctx *ctx, int64_t polls);
+
 /* ------------------------------------------------------------------------ */
 /* store -- Section 3: the TripleID file of (SubjID, PredID, ObjID)          */
 /* ------------------------------------------------------------------------ */

@@ -134,6 +134,7 @@ def lib():
         "tid_match_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, C.c_int64, tid_pattern, _vp, C.c_int64,
                                         _vp]),
         "tid_ctx_inject_alloc_failure": (C.c_int, [_vp, C.c_int64]),
+        "tid_ctx_test_bounded_wait": (C.c_int, [_vp, C.c_int64]),
         "tid_entail": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(tid_rdfs_vocab), C.POINTER(_vp),
                                  C.POINTER(tid_entail_stats)]),
         "tid_server_create": (C.c_int, [C.c_int, _vp, _vp, _vp, C.c_int64, C.POINTER(tid_server_config),
@@ -470,6 +471,12 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+def tid_ctx_test_bounded_wait(ctx, polls):
+    """Status code of a bounded in-kernel wait that nothing ends (see tid.h):
+    TID_ERR_TIMEOUT when the wait gave up as it should."""
+    return int(lib().tid_ctx_test_bounded_wait(ctx, int(polls)))
 
 
 def tid_ctx_inject_alloc_failure(ctx, after):

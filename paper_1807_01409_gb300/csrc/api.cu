@@ -6,6 +6,7 @@
 #include <atomic>
 #include <new>
 
+#include "lookback.cuh"
 #include "ops.cuh"
 
 namespace tid {
@@ -363,6 +364,32 @@ extern "C" int tid_ctx_destroy(tid_ctx *ctx) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return TID_OK;
+}
+
+namespace {
+// One CTA arrives at a barrier of two that no other CTA reaches: the library's
+// bounded wait gives up after `limit` polls and sets TID_ERR_TIMEOUT.
+__global__ void k_wait_for_nothing(unsigned *counter, int *err, unsigned limit) {
+    tid::grid_barrier(counter, 2u, err, limit);
+}
+}  // namespace
+
+extern "C" int tid_ctx_test_bounded_wait(tid_ctx *ctx, int64_t polls) {
+    clear_error();
+    if (!ctx) return fail(TID_ERR_ARG, "tid_ctx_test_bounded_wait: null context");
+    if (polls < 1 || polls > (int64_t)LB_SPIN_LIMIT)
+        return fail(TID_ERR_ARG, "tid_ctx_test_bounded_wait: polls = %lld", (long long)polls);
+    DeviceGuard g(ctx->device);
+    void *counter = nullptr;
+    TID_TRY(dev_alloc(ctx, &counter, 256));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), ctx->stream);
+    if (e == cudaSuccess) {
+        k_wait_for_nothing<<<1, 32, 0, ctx->stream>>>((unsigned *)counter, ctx->err_dev, (unsigned)polls);
+        e = cudaGetLastError();
+    }
+    dev_free(ctx, counter);
+    if (e != cudaSuccess) return fail_cuda(e, "tid_ctx_test_bounded_wait");
+    return tid_ctx_sync(ctx);
 }
 
 extern "C" int tid_ctx_inject_alloc_failure(tid_ctx *ctx, int64_t after) {

@@ -130,7 +130,8 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 }
 
 // All CTAs of a cooperative launch meet here; false if the wait gave up.
-__device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned expected, int *err) {
+__device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned expected, int *err,
+                                             unsigned limit = LB_SPIN_LIMIT) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -139,7 +140,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned expecte
         int ok = 1;
         unsigned polls = 0;
         while (ld_acquire_u32(counter) < expected) {
-            if (++polls > LB_SPIN_LIMIT) {
+            if (++polls > limit) {
                 atomicExch(err, TID_ERR_TIMEOUT);
                 ok = 0;
                 break;

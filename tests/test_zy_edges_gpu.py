@@ -142,3 +142,22 @@ def test_extreme_id_plans(ctx, orc, algo):
     for plan in plans:
         _same(_host(tb.tid_exec(ctx, st, plan)), orc.execute(S, P, O, plan))
     tb.tid_store_free(st)
+
+
+def test_bounded_wait_gives_up_and_the_context_recovers(ctx, orc):
+    """Failure detection without a GPU fault: a wait that nothing will end (a
+    barrier no other CTA reaches) gives up after its poll limit, the context
+    reports TID_ERR_TIMEOUT once, and then answers correctly."""
+    import time
+    t0 = time.perf_counter()
+    assert tb.tid_ctx_test_bounded_wait(ctx, 2000) == tb.TID_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60
+    tb.tid_ctx_sync(ctx)  # reported once, then clear
+    with pytest.raises(tb.TidError) as e:
+        tb._check(tb.lib().tid_ctx_test_bounded_wait(ctx, 0), "polls")
+    assert e.value.code == tb.TID_ERR_ARG
+    st = synth.tiny_store(20_000)
+    store = tb.tid_load(ctx, _dev(st.s), _dev(st.p), _dev(st.o), copy=1)
+    for q in synth.tiny_queries(st)[:6]:
+        assert np.array_equal(_match(ctx, store, q.key()), orc.match(st.s, st.p, st.o, q.key()))
+    tb.tid_store_free(store)
