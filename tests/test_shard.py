@@ -81,3 +81,37 @@ def test_gathered_shards_equal_the_whole_store_gloo(world):
     got = sorted(q.get(timeout=10) for _ in range(world))
     for rank, ok in got:
         assert all(ok), (rank, ok)
+
+
+def _rank_that_leaves(rank, world, port, q):
+    """Rank 1 leaves before the exchange; rank 0's gather must fail, not hang."""
+    import datetime
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    from paper_1807_01409_gb300 import shard as sh
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)  # leaves between steps, with nothing in flight
+    try:
+        sh.gather_global(np.arange(5, dtype=np.int32), 0)
+        q.put((rank, "returned"))
+    except Exception as e:  # noqa: BLE001 -- the failure is the expected outcome
+        q.put((rank, type(e).__name__))
+
+
+def test_a_rank_that_leaves_fails_the_exchange_gloo():
+    """Failure detection on the host: when a rank exits before the shard
+    exchange, the remaining rank's collective ends with an error within the
+    process group's timeout instead of waiting forever."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_that_leaves, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert procs[1].exitcode == 3
+    assert procs[0].exitcode == 0
+    rank, outcome = q.get(timeout=10)
+    assert rank == 0 and outcome != "returned", outcome
