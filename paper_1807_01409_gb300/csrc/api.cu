@@ -341,6 +341,7 @@ extern "C" int tid_ctx_create(int device, void *cuda_stream, tid_ctx **out) {
 
 extern "C" int tid_ctx_sync(tid_ctx *ctx) {
     clear_error();
+    tid::Range nvtx_range("tid_ctx_sync");
     if (!ctx) return fail(TID_ERR_ARG, "tid_ctx_sync: null ctx");
     DeviceGuard g(ctx->device);
     TID_TRY_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
@@ -487,6 +488,7 @@ int set_rows_host(const tid_set *set, int64_t *rows) { return set_rows_host(cons
 
 extern "C" int tid_set_rows(tid_set *set, int64_t *rows) {
     clear_error();
+    tid::Range nvtx_range("tid_set_rows");
     if (!set || !rows) return fail(TID_ERR_ARG, "tid_set_rows: null argument");
     return set_rows_host(set, rows);
 }

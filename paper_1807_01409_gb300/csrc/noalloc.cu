@@ -62,6 +62,7 @@ extern "C" int tid_match_noalloc(int device, void *cuda_stream, const int32_t *s
                                  int64_t *count) {
     using namespace tid;
     clear_error();
+    Range nvtx_range("tid_match_noalloc");
     if (n < 0 || n > INT32_MAX) return fail(TID_ERR_ARG, "tid_match_noalloc: n = %lld out of range", (long long)n);
     if (n > 0 && (!s || !p || !o)) return fail(TID_ERR_ARG, "tid_match_noalloc: null column");
     if (!count) return fail(TID_ERR_ARG, "tid_match_noalloc: null count");

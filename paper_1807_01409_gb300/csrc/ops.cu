@@ -299,6 +299,7 @@ extern "C" int tid_project(tid_ctx *ctx, const tid_set *in, const int8_t *vars, 
 extern "C" int tid_set_from_host(tid_ctx *ctx, const int32_t *buf, int64_t rows, int cols, const int8_t *vars,
                                  tid_set **out) {
     clear_error();
+    tid::Range nvtx_range("tid_set_from_host");
     if (!ctx || !out || !vars) return fail(TID_ERR_ARG, "tid_set_from_host: null argument");
     *out = nullptr;
     if (cols < 1 || cols > TID_MAX_COLS) return fail(TID_ERR_ARG, "tid_set_from_host: %d columns", cols);

@@ -429,6 +429,7 @@ extern "C" int tid_server_submit(tid_server *S, int kind, const tid_plan_node *n
 
 extern "C" int tid_server_wait(tid_server *S, int64_t id, int64_t timeout_ms) {
     clear_error();
+    Range nvtx_range("tid_server_wait");
     if (!S) return fail(TID_ERR_ARG, "tid_server_wait: null server");
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->reqs.find(id);
