@@ -437,10 +437,11 @@ typedef struct {
 #define TID_REQ_PLAN  2  /* result: the plan's canonical tuple set (as tid_exec)                      */
 
 /* Server on CUDA device `device` over the store s/p/o (n int32 each, device
- * memory, borrowed: unchanged and valid until tid_server_destroy; complete when
- * the call is made, since it reads a strided sample of every column for its
- * estimates before returning).  Starts the workers.  Errors: TID_ERR_ARG (bad
- * configuration), TID_ERR_OOM, TID_ERR_CUDA. */
+ * memory, borrowed: unchanged and valid until tid_server_destroy).  Waits for
+ * the device once (work still writing the columns on any stream finishes),
+ * reads a strided sample of every column for its estimates, and starts the
+ * workers.  Errors: TID_ERR_ARG (bad configuration), TID_ERR_OOM,
+ * TID_ERR_CUDA. */
 int tid_server_create(int device, const int32_t *s, const int32_t *p, const int32_t *o, int64_t n,
                       const tid_server_config *cfg, tid_server **out);
 

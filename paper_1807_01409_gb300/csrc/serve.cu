@@ -379,7 +379,10 @@ extern "C" int tid_server_create(int device, const int32_t *s, const int32_t *p,
     }
     {
         DeviceGuard g(device);
-        const int rc = make_sample(S.get());
+        // the columns may still be being written on another stream: wait for the
+        // device once, before the sample and before any worker reads them
+        const cudaError_t e = cudaDeviceSynchronize();
+        const int rc = e != cudaSuccess ? fail_cuda(e, "tid_server_create: device synchronize") : make_sample(S.get());
         if (rc != TID_OK) {
             destroy_workers(S.get());
             return rc;
