@@ -17,6 +17,8 @@ Paper passages followed (TripleID-Q, IEEE TPDS 2018):
                       at any of S/P/O on either side); inner join.
 * ``left_join``    -- the left (outer) join Section 4.2 names among its library's joins:
                       SPARQL OPTIONAL, unmatched left rows padded with 0.
+* ``right_join``, ``full_join`` -- the right and full outer joins of the same list:
+                      unmatched right rows (and, for full, left rows) padded with 0.
 * ``union``        -- Section 4.1; results keep only distinct values (Section 4.3).
 * ``filter``       -- Section 4.3 (filter during extraction), on integer IDs with the
                       order-preserving literal encoding the same section proposes.
@@ -276,6 +278,36 @@ def left_join(Ls: TupleSet, Rs: TupleSet, method: str = "auto") -> TupleSet:
     return _set(out_vars, rows)
 
 
+def _unmatched_right(Ls: TupleSet, Rs: TupleSet):
+    """Rows of R that join no row of L, in the join's columns (L's, then R's
+    others), L's other columns 0 (unbound)."""
+    shared, lkey, rkey, rrest, out_vars = join_schema(Ls.vars, Rs.vars)
+    lkeys = {tuple(l[i] for i in lkey) for l in Ls.rows.tolist() if all(l[i] != 0 for i in lkey)}
+    pad = []
+    for r in Rs.rows.tolist():
+        key = tuple(r[j] for j in rkey)
+        if all(x != 0 for x in key) and key in lkeys:
+            continue
+        pad.append([r[Rs.vars.index(v)] if v in Rs.vars else 0 for v in out_vars])
+    return np.array(pad, np.int32).reshape(-1, len(out_vars))
+
+
+def right_join(Ls: TupleSet, Rs: TupleSet, method: str = "auto") -> TupleSet:
+    """Right outer join (Section 4.2 names the outer joins of the library the paper
+    used): the inner join's rows, plus every row of R that joins no row of L, with
+    L's other columns 0 (unbound); columns as the inner join's."""
+    inner = join(Ls, Rs, method)
+    return _set(inner.vars, np.concatenate([inner.rows, _unmatched_right(Ls, Rs)], axis=0))
+
+
+def full_join(Ls: TupleSet, Rs: TupleSet, method: str = "auto") -> TupleSet:
+    """Full outer join: the inner join's rows, every row of L that joins no row of
+    R (R's other columns 0) and every row of R that joins no row of L (L's other
+    columns 0)."""
+    left = left_join(Ls, Rs, method)
+    return _set(left.vars, np.concatenate([left.rows, _unmatched_right(Ls, Rs)], axis=0))
+
+
 def union_schema(sets):
     out = []
     for t in sets:
@@ -340,7 +372,8 @@ def execute(s, p, o, plan) -> TupleSet:
             r = filter(ev(nd["input"]), nd["var"], nd["cmp"], nd["a"], nd.get("b", 0))
         elif op == "join":
             a, b = nd["inputs"]
-            r = left_join(ev(a), ev(b)) if nd.get("algo") == "left" else join(ev(a), ev(b))
+            kind = {"left": left_join, "right": right_join, "full": full_join}.get(nd.get("algo"), join)
+            r = kind(ev(a), ev(b))
         elif op == "union":
             r = union([ev(j) for j in nd["inputs"]])
         elif op == "project":

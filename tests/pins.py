@@ -322,6 +322,41 @@ def pin_left_join_rowwise(o):
         assert got.rows.tolist() == [list(x) for x in sorted(want)], t
 
 
+def pin_outer_joins_rowwise(o):
+    """Right and full outer joins, row by row: every pair of rows whose shared
+    columns are all equal and bound gives a row; a right row with no such pair
+    appears alone with the left side's other columns 0 (right and full), and so
+    does a left row with no pair, with the right side's other columns 0 (full).
+    Columns as the inner join's: the left's, then the right's others."""
+    rng = np.random.default_rng(37)
+    for t in range(30):
+        kl, kr = int(rng.integers(1, 4)), int(rng.integers(1, 4))
+        lv = tuple(int(x) for x in rng.choice(6, size=kl, replace=False))
+        rv = tuple(int(x) for x in rng.choice(6, size=kr, replace=False))
+        L = o.TupleSet(lv, o.canonical(rng.integers(0, 4, (int(rng.integers(0, 40)), kl)).astype(np.int32)))
+        R = o.TupleSet(rv, o.canonical(rng.integers(0, 4, (int(rng.integers(0, 40)), kr)).astype(np.int32)))
+        shared = [v for v in lv if v in rv]
+        rest = [j for j, v in enumerate(rv) if v not in lv]
+        out_vars = lv + tuple(rv[j] for j in rest)
+
+        def pairs(l, r):
+            return all(l[lv.index(v)] == r[rv.index(v)] != 0 for v in shared)
+        inner, lonely_l, lonely_r = set(), set(), set()
+        for l in L.rows.tolist():
+            if not any(pairs(l, r) for r in R.rows.tolist()):
+                lonely_l.add(tuple(l) + (0,) * len(rest))
+            for r in R.rows.tolist():
+                if pairs(l, r):
+                    inner.add(tuple(l) + tuple(r[j] for j in rest))
+        for r in R.rows.tolist():
+            if not any(pairs(l, r) for l in L.rows.tolist()):
+                lonely_r.add(tuple(r[rv.index(v)] if v in rv else 0 for v in out_vars))
+        got_r, got_f = o.right_join(L, R), o.full_join(L, R)
+        assert got_r.vars == out_vars and got_f.vars == out_vars
+        assert got_r.rows.tolist() == [list(x) for x in sorted(inner | lonely_r)], t
+        assert got_f.rows.tolist() == [list(x) for x in sorted(inner | lonely_l | lonely_r)], t
+
+
 # RDFS rules of the paper's entailment table (Section 5), for the brute force:
 # two premises and a conclusion over variable names and vocabulary terms
 _RULES_BF = {
@@ -432,4 +467,4 @@ def pin_execute_plans(o):
 ALL_PINS = [pin_golden_rule11, pin_match_bruteforce, pin_match_tallies,
             pin_bind_join_bruteforce, pin_join_cross_product, pin_union_laws,
             pin_filter_algebra, pin_canonical, pin_project, pin_entail_golden,
-            pin_entail_bruteforce, pin_left_join_rowwise, pin_execute_plans]
+            pin_entail_bruteforce, pin_left_join_rowwise, pin_outer_joins_rowwise, pin_execute_plans]

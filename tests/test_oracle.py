@@ -94,6 +94,12 @@ PY_MUTATIONS = [
     ('for t in r["then"]:', 'for t in reversed(r["then"]):'),                                # conclusion reversed
     ("if not (all(l[i] != 0", "if (all(l[i] != 0"),                  # left join: pads the matched rows
     ("pad = [l + [0] * len(rrest)", "pad = [l + [1] * len(rrest)"),   # left join: wrong padding
+    ("if all(x != 0 for x in key) and key in lkeys:",
+     "if key in lkeys or not all(x != 0 for x in key):"),                      # outer: unbound right rows dropped
+    ("pad.append([r[Rs.vars.index(v)] if v in Rs.vars else 0 for v in out_vars])",
+     "pad.append([r[Rs.vars.index(v)] if v in Rs.vars else 1 for v in out_vars])"),  # right: wrong padding
+    ("return _set(left.vars, np.concatenate([left.rows, _unmatched_right(Ls, Rs)], axis=0))",
+     "return left"),                                                                   # full: right rows lost
 ]
 
 
