@@ -256,6 +256,15 @@ int tid_filter(tid_ctx *ctx, const tid_set *in, const tid_pred *preds, int n_pre
  * a match in R appears once, with R's other columns 0 (unbound).  Runs as a
  * sort-merge join (TID_JOIN_LEFT | TID_JOIN_HASH is TID_ERR_ARG). */
 #define TID_JOIN_LEFT       0x100
+/* or-ed into algo: a right outer join -- every row of R without a match in L
+ * appears once, with L's other columns 0 -- and, with TID_JOIN_LEFT as well
+ * (TID_JOIN_FULL), the full outer join.  Output columns as the inner join's
+ * (L's, then R's others).  Built from the left join: right(L, R) is the left
+ * join of R with L with its columns put in that order, full(L, R) the union of
+ * left(L, R) and right(L, R).  Sort-merge only (with TID_JOIN_HASH:
+ * TID_ERR_ARG). */
+#define TID_JOIN_RIGHT      0x200
+#define TID_JOIN_FULL       (TID_JOIN_LEFT | TID_JOIN_RIGHT)
 
 /* Inner join of L and R on ALL their shared variables (Section 4.2 and its
  * relationship table: the shared term may come from any of S/P/O on either

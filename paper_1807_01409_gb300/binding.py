@@ -71,8 +71,10 @@ class tid_plan_node(C.Structure):
 
 
 CMP = {"eq": 0, "ne": 1, "lt": 2, "le": 3, "gt": 4, "ge": 5, "range": 6}
-TID_JOIN_LEFT = 0x100
-JOIN = {"auto": 0, "sort_merge": 1, "sortmerge": 1, "hash": 2, "left": TID_JOIN_LEFT}
+TID_JOIN_LEFT, TID_JOIN_RIGHT = 0x100, 0x200
+TID_JOIN_FULL = TID_JOIN_LEFT | TID_JOIN_RIGHT
+JOIN = {"auto": 0, "sort_merge": 1, "sortmerge": 1, "hash": 2, "left": TID_JOIN_LEFT, "right": TID_JOIN_RIGHT,
+        "full": TID_JOIN_FULL}
 OP = {"match": 1, "filter": 2, "join": 3, "union": 4, "project": 5}
 
 

@@ -19,7 +19,6 @@
 namespace tid {
 int bind_set(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, const tid_set *idx, const tid_pred *preds,
              int n_preds, tid_set **out);
-int project_set(tid_ctx *ctx, const tid_set *in, const int8_t *vars, int n_vars, tid_set **out);
 }  // namespace tid
 
 using namespace tid;

@@ -289,6 +289,7 @@ int read_u64(tid_ctx *ctx, const unsigned long long *d, unsigned long long *h) {
 
 int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out) {
     *out = nullptr;
+    if (algo & TID_JOIN_RIGHT) return outer_join_sets(ctx, L, R, algo, out);
     const bool left = (algo & TID_JOIN_LEFT) != 0;
     algo &= ~TID_JOIN_LEFT;
     int64_t nl = 0, nr = 0;

@@ -233,6 +233,46 @@ int project_set(tid_ctx *ctx, const tid_set *in, const int8_t *vars, int n_vars,
     return canonicalize(ctx, cols, n_vars, vars, n, !identity, in->bounded ? &b : nullptr, out);
 }
 
+// Right and full outer joins (Section 4.2 lists the outer joins of the library
+// the paper used) from the left join: right(L, R) keeps every row of R -- it is
+// the left join of R with L, its columns put in the join's order (L's, then R's
+// others) -- and full(L, R) is the union of left(L, R) and right(L, R), whose
+// matched rows are the same tuples and are kept once.
+int outer_join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out) {
+    *out = nullptr;
+    const int base = algo & ~(TID_JOIN_LEFT | TID_JOIN_RIGHT);
+    if (base != TID_JOIN_AUTO && base != TID_JOIN_SORT_MERGE)
+        return fail(TID_ERR_ARG, "tid_join: outer joins run as sort-merge joins (algo %d)", algo);
+    int8_t ovars[TID_MAX_COLS];
+    int k = 0;
+    for (int c = 0; c < L->k; ++c) ovars[k++] = L->vars[c];
+    for (int d = 0; d < R->k; ++d) {
+        bool shared = false;
+        for (int c = 0; c < L->k; ++c) shared = shared || L->vars[c] == R->vars[d];
+        if (shared) continue;
+        if (k == TID_MAX_COLS) return fail(TID_ERR_ARG, "tid_join: output wider than %d columns", TID_MAX_COLS);
+        ovars[k++] = R->vars[d];
+    }
+    tid_set *rl = nullptr, *right = nullptr;
+    TID_TRY(join_sets(ctx, R, L, TID_JOIN_LEFT | base, &rl));
+    int rc = project_set(ctx, rl, ovars, k, &right);
+    set_free(rl);
+    TID_TRY(rc);
+    if (!(algo & TID_JOIN_LEFT)) {
+        *out = right;
+        return TID_OK;
+    }
+    tid_set *lj = nullptr;
+    rc = join_sets(ctx, L, R, TID_JOIN_LEFT | base, &lj);
+    if (rc == TID_OK) {
+        const tid_set *both[2] = {lj, right};
+        rc = union_sets(ctx, both, 2, out);
+    }
+    set_free(lj);
+    set_free(right);
+    return rc;
+}
+
 }  // namespace tid
 
 using namespace tid;

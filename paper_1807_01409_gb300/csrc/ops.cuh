@@ -74,8 +74,14 @@ int set_rows_const(tid_set *set, int64_t n);
 int set_rows_host(tid_set *set, int64_t *rows);
 int set_rows_host(const tid_set *set, int64_t *rows);
 
-// joins (join.cu)
+// joins (join.cu); right and full outer joins composed from the left join (ops.cu)
 int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out);
+int outer_join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out);
+
+// set operators (ops.cu)
+int filter_set(tid_ctx *ctx, const tid_set *in, const tid_pred *preds, int n_preds, tid_set **out);
+int union_sets(tid_ctx *ctx, const tid_set *const *in, int k, tid_set **out);
+int project_set(tid_ctx *ctx, const tid_set *in, const int8_t *vars, int n_vars, tid_set **out);
 
 // plans (exec.cu): checks a plan's shape and patterns; evaluates a checked plan,
 // taking over matched[i] (an index list, or null to search it) for MATCH nodes

@@ -103,6 +103,7 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
         "TID_REQ_INDEX": tb.TID_REQ_INDEX, "TID_REQ_PLAN": tb.TID_REQ_PLAN,
         "TID_JOIN_AUTO": tb.JOIN["auto"], "TID_JOIN_SORT_MERGE": tb.JOIN["sort_merge"],
         "TID_JOIN_HASH": tb.JOIN["hash"], "TID_JOIN_LEFT": tb.TID_JOIN_LEFT,
+        "TID_JOIN_RIGHT": tb.TID_JOIN_RIGHT, "TID_JOIN_FULL": tb.TID_JOIN_FULL,
         **{f"TID_CMP_{k.upper()}": v for k, v in tb.CMP.items()},
         **{f"TID_OP_{k.upper()}": v for k, v in tb.OP.items()},
         **{f"TID_RULE_R{r}": r for r in tb.RULES},

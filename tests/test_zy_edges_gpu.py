@@ -161,3 +161,47 @@ def test_bounded_wait_gives_up_and_the_context_recovers(ctx, orc):
     for q in synth.tiny_queries(st)[:6]:
         assert np.array_equal(_match(ctx, store, q.key()), orc.match(st.s, st.p, st.o, q.key()))
     tb.tid_store_free(store)
+
+
+OUTER_SHAPES = [((0, 1), (0, 2)), ((0, 1), (2, 0)), ((0, 1, 2), (2, 1, 3)), ((0, 1), (0, 1, 2)), ((5, 6), (7, 8)),
+                ((0,), (0,)), ((3, 0, 1), (1, 4, 0, 5))]
+
+
+@pytest.mark.parametrize("kind", ["right", "full"])
+@pytest.mark.parametrize("shape", range(len(OUTER_SHAPES)))
+@pytest.mark.parametrize("size", [(0, 10), (10, 0), (1, 1), (300, 500), (5000, 40_000)])
+def test_outer_joins_random_sets(ctx, orc, kind, shape, size):
+    """Right and full outer joins equal the oracle's, unmatched rows padded with 0
+    (keys include the unbound value 0, which never matches)."""
+    lv, rv = OUTER_SHAPES[shape]
+    rng = np.random.default_rng((shape * 7919 + size[0] * 31 + size[1] + (kind == "full")) % 2 ** 32)
+    nl, nr = size
+    if (lv, rv) == ((5, 6), (7, 8)):  # cross product: keep it small
+        nl, nr = min(nl, 300), min(nr, 200)
+    hi = max(4, int(np.sqrt(max(nl, nr, 1))) // 2)
+    L = orc.TupleSet(lv, orc.canonical(rng.integers(0, hi, (nl, len(lv)))))
+    R = orc.TupleSet(rv, orc.canonical(rng.integers(0, hi, (nr, len(rv)))))
+    hl = tb.tid_set_from_host(ctx, L.rows, lv)
+    hr = tb.tid_set_from_host(ctx, R.rows, rv)
+    want = orc.right_join(L, R) if kind == "right" else orc.full_join(L, R)
+    _same(_host(tb.tid_join(ctx, hl, hr, kind)), want)
+    with pytest.raises(tb.TidError) as e:
+        tb.tid_join(ctx, hl, hr, tb.JOIN[kind] | tb.JOIN["hash"])
+    assert e.value.code == tb.TID_ERR_ARG
+    tb.tid_set_free(hl)
+    tb.tid_set_free(hr)
+
+
+@pytest.mark.parametrize("kind", ["right", "full"])
+def test_outer_join_plans(ctx, orc, kind):
+    """Star plans on the university store with every join a right or full outer
+    join, through tid_exec, against the oracle's evaluation of the same plan."""
+    st_np = synth.university_store(1_000_000)
+    st = _store(ctx, st_np.s, st_np.p, st_np.o)
+    for name, plan in synth.university_plans(st_np)[:8]:
+        plan = [dict(nd, algo=kind) if nd["op"] == "join" else nd for nd in plan]
+        try:
+            _same(_host(tb.tid_exec(ctx, st, plan)), orc.execute(st_np.s, st_np.p, st_np.o, plan))
+        except AssertionError as e:
+            raise AssertionError(f"{name}: {e}")
+    tb.tid_store_free(st)
