@@ -275,7 +275,10 @@ int tid_filter(tid_ctx *ctx, const tid_set *in, const tid_pred *preds, int n_pre
  * binary search, scan, write) or hash (group the smaller side by key in an
  * open-addressing table, probe with the other).  Output canonical.  The
  * count phase is followed by one synchronisation to size the output; more
- * than 2^31-1 output rows is TID_ERR_CAPACITY. */
+ * than 2^31-1 output rows is TID_ERR_CAPACITY.  algo is TID_JOIN_AUTO,
+ * TID_JOIN_SORT_MERGE or TID_JOIN_HASH, optionally or-ed with TID_JOIN_LEFT,
+ * TID_JOIN_RIGHT or TID_JOIN_FULL for the outer joins above; anything else is
+ * TID_ERR_ARG. */
 int tid_join(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out);
 
 /* Set union of k >= 1 sets (Section 4.1).  The output schema lists the
