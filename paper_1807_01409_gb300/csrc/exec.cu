@@ -53,13 +53,20 @@ namespace tid {
 int validate_plan(const tid_plan_node *nodes, int n_nodes) {
     if (n_nodes < 1) return fail(TID_ERR_ARG, "tid_exec: empty plan");
     TID_TRY(validate(nodes, n_nodes));
-    for (int i = 0; i < n_nodes; ++i)
+    for (int i = 0; i < n_nodes; ++i) {
         if (nodes[i].op == TID_OP_MATCH) {
             int8_t v[TID_MAX_COLS];
             int k = 0;
             bool anon = false;
             TID_TRY(pattern_vars(nodes[i].pattern, v, &k, &anon));
         }
+        if (nodes[i].op == TID_OP_JOIN) {  // the algorithm and outer-join flags tid_join accepts
+            const int a = nodes[i].algo, outer = a & (TID_JOIN_LEFT | TID_JOIN_RIGHT), base = a & ~outer;
+            if ((base != TID_JOIN_AUTO && base != TID_JOIN_SORT_MERGE && base != TID_JOIN_HASH) ||
+                (outer && base == TID_JOIN_HASH))
+                return fail(TID_ERR_ARG, "tid_exec: node %d: join algorithm %d", i, a);
+        }
+    }
     return TID_OK;
 }
 

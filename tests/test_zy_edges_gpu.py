@@ -205,3 +205,19 @@ def test_outer_join_plans(ctx, orc, kind):
         except AssertionError as e:
             raise AssertionError(f"{name}: {e}")
     tb.tid_store_free(st)
+
+
+def test_plan_join_flags_checked_before_running(ctx):
+    """A JOIN node with an unknown algorithm or a hash outer join is refused when
+    the plan is checked (TID_ERR_ARG), before anything runs."""
+    st = synth.tiny_store(10_000)
+    store = tb.tid_load(ctx, _dev(st.s), _dev(st.p), _dev(st.o), copy=1)
+    p0 = int(st.p[0])
+    base = [{"op": "match", "pattern": synth.Pattern(0, p0, 0, var=(0, -1, 1))},
+            {"op": "match", "pattern": synth.Pattern(0, p0, 0, var=(1, -1, 2))}]
+    for algo in (0x400, 3, tb.TID_JOIN_RIGHT | tb.JOIN["hash"], tb.TID_JOIN_LEFT | tb.JOIN["hash"]):
+        plan = base + [{"op": "join", "inputs": [0, 1], "algo": algo}]
+        with pytest.raises(tb.TidError) as e:
+            tb.tid_exec(ctx, store, plan)
+        assert e.value.code == tb.TID_ERR_ARG, algo
+    tb.tid_store_free(store)
