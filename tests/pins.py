@@ -462,6 +462,18 @@ def pin_execute_plans(o):
     b = solutions(S, P, O, [((0, 2, 0), (Y, -1, Z))], (Y, Z))
     want = sorted({(x, y, 0) for x, y in a} | {(0, y, z) for y, z in b})
     assert r.vars == (X, Y, Z) and r.rows.tolist() == [list(w) for w in want]
+    # a chain joined as OPTIONAL (left), right and full outer joins
+    a = solutions(S, P, O, [((0, 2, 0), (X, -1, Y))], (X, Y))
+    b = solutions(S, P, O, [((0, 3, 0), (Y, -1, Z))], (Y, Z))
+    inner = {(x, y, z) for x, y in a for y2, z in b if y == y2}
+    only_a = {(x, y, 0) for x, y in a if not any(y == y2 for y2, _ in b)}
+    only_b = {(0, y, z) for y, z in b if not any(y == y1 for _, y1 in a)}
+    for kind, want in (("left", inner | only_a), ("right", inner | only_b), ("full", inner | only_a | only_b)):
+        plan = [{"op": "match", "pattern": Pattern(0, 2, 0, var=(X, -1, Y))},
+                {"op": "match", "pattern": Pattern(0, 3, 0, var=(Y, -1, Z))},
+                {"op": "join", "inputs": [0, 1], "algo": kind}]
+        r = o.execute(S, P, O, plan)
+        assert r.vars == (X, Y, Z) and r.rows.tolist() == [list(w) for w in sorted(want)], kind
 
 
 ALL_PINS = [pin_golden_rule11, pin_match_bruteforce, pin_match_tallies,

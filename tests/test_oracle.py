@@ -100,6 +100,7 @@ PY_MUTATIONS = [
      "pad.append([r[Rs.vars.index(v)] if v in Rs.vars else 1 for v in out_vars])"),  # right: wrong padding
     ("return _set(left.vars, np.concatenate([left.rows, _unmatched_right(Ls, Rs)], axis=0))",
      "return left"),                                                                   # full: right rows lost
+    ('"right": right_join, "full": full_join}', '"right": left_join, "full": full_join}'),  # plan: right as left
 ]
 
 
