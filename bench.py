@@ -397,6 +397,23 @@ def measure_rows(tb, ctx, store, st, stream, peak, with_oracle=True, reps=3):
         out[f"a6_join_{algo}"] = entry(ms, 4 * nl + 8 * nr + 8 * mj + 16 * mj, cpu_ms, rows_l=nl, rows_r=nr,
                                        rows_out=mj, oracle_sample="full inputs (oracle sort-merge join)")
 
+    # the outer joins on the same inputs: left (OPTIONAL), and right and full composed from it;
+    # algorithmic bytes: both inputs read once, the output written once
+    sl, sr = min(nl, 50_000), min(nr, 400_000)
+    if orc:
+        Ls_, Rs_ = orc.TupleSet((X,), Lh[:sl]), orc.TupleSet((X, Y), Rh[:sr])
+    for kind in ("left", "right", "full"):
+        try:
+            ms, j = timed(lambda: tb.tid_join(ctx, L, R, kind))
+            mj = rows_of(j)
+            cpu_ms = cpu(lambda: getattr(orc, f"{kind}_join")(Ls_, Rs_), scale=(nl + nr) / max(1, sl + sr)) \
+                if orc else None
+            out[f"outer_join_{kind}"] = entry(ms, 4 * nl + 8 * nr + 8 * mj, cpu_ms, rows_l=nl, rows_r=nr, rows_out=mj,
+                                              oracle_sample=f"first {sl} and {sr} rows of the inputs, time scaled "
+                                                            f"x{(nl + nr) / max(1, sl + sr):.1f}")
+        except Exception as e:  # noqa: BLE001 -- reported in the line
+            out[f"outer_join_{kind}"] = {"error": f"{type(e).__name__}: {e}"}
+
     # a7: union of (x, v) and (x, y): schema (x, v, y), padded with 0
     ms, u = timed(lambda: tb.tid_union(ctx, [full, R]))
     mu = rows_of(u)
