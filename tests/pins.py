@@ -204,6 +204,23 @@ def pin_bind_join_bruteforce(o):
             assert j.n == sum(ca[k] * cb.get(k, 0) for k in ca)
 
 
+def pin_bind_anonymous_wildcards(o):
+    """A result vector keeps one row per distinct value of its named variables:
+    an anonymous "?" is existential (the solution mappings projected on the named
+    variables), and a variable named twice needs equal terms."""
+    X, Y = 0, 1
+    cases = [((0, 0, 0), (X, -1, -1)), ((0, 0, 0), (-1, X, -1)), ((0, 0, 0), (-1, -1, X)),
+             ((0, 3, 0), (X, -1, -1)), ((0, 0, 0), (X, -1, Y)), ((0, 0, 2), (X, Y, -1)),
+             ((0, 0, 0), (X, -1, X)), ((1, 0, 0), (-1, X, -1))]
+    for seed in (41, 42):
+        S, P, O = tiny_graph(seed, 45, ids=5)
+        for key, var in cases:
+            got = o.bind(S, P, O, key, var, o.match(S, P, O, key))
+            named = tuple(dict.fromkeys(v for v in var if v >= 0))
+            assert got.vars == named, (key, var)
+            assert got.rows.tolist() == [list(w) for w in solutions(S, P, O, [(key, var)], named)], (seed, key, var)
+
+
 def pin_join_cross_product(o):
     """join(L, R) = rows of L x R whose shared columns agree (and are bound)."""
     rng = np.random.default_rng(5)
@@ -477,6 +494,6 @@ def pin_execute_plans(o):
 
 
 ALL_PINS = [pin_golden_rule11, pin_match_bruteforce, pin_match_tallies,
-            pin_bind_join_bruteforce, pin_join_cross_product, pin_union_laws,
+            pin_bind_join_bruteforce, pin_bind_anonymous_wildcards, pin_join_cross_product, pin_union_laws,
             pin_filter_algebra, pin_canonical, pin_project, pin_entail_golden,
             pin_entail_bruteforce, pin_left_join_rowwise, pin_outer_joins_rowwise, pin_execute_plans]

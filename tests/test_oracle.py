@@ -101,6 +101,7 @@ PY_MUTATIONS = [
     ("return _set(left.vars, np.concatenate([left.rows, _unmatched_right(Ls, Rs)], axis=0))",
      "return left"),                                                                   # full: right rows lost
     ('"right": right_join, "full": full_join}', '"right": left_join, "full": full_join}'),  # plan: right as left
+    ("    return _set(vars_, out[:r])", "    return TupleSet(vars_, out[:r].copy())"),          # bind keeps duplicates
 ]
 
 
