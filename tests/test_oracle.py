@@ -102,6 +102,10 @@ PY_MUTATIONS = [
      "return left"),                                                                   # full: right rows lost
     ('"right": right_join, "full": full_join}', '"right": left_join, "full": full_join}'),  # plan: right as left
     ("    return _set(vars_, out[:r])", "    return TupleSet(vars_, out[:r].copy())"),          # bind keeps duplicates
+    ("rkey = [Rv.index(v) for v in shared]", "rkey = [Lv.index(v) for v in shared]"),         # join: key from wrong side
+    ("out_vars = tuple(Lv) + tuple(Rv[j] for j in rrest)",
+     "out_vars = tuple(Rv[j] for j in rrest) + tuple(Lv)"),                                  # join: schema order swapped
+    ("    for t in sets:\n        for v in t.vars:", "    for t in reversed(sets):\n        for v in t.vars:"),  # union schema order
 ]
 
 
