@@ -221,3 +221,19 @@ def test_plan_join_flags_checked_before_running(ctx):
             tb.tid_exec(ctx, store, plan)
         assert e.value.code == tb.TID_ERR_ARG, algo
     tb.tid_store_free(store)
+
+
+def test_university_plans_full_size_sampled(ctx, orc):
+    """The plans (star, chain, union, filter) on the full 200M-triple store with
+    the default join choice, as the benchmark runs them: every sixth plan is
+    compared in full with the oracle's evaluation."""
+    st_np = synth.university_store(synth.UNI_FULL)
+    st = _store(ctx, st_np.s, st_np.p, st_np.o)
+    try:
+        for name, plan in synth.university_plans(st_np)[::6]:
+            try:
+                _same(_host(tb.tid_exec(ctx, st, plan)), orc.execute(st_np.s, st_np.p, st_np.o, plan))
+            except AssertionError as e:
+                raise AssertionError(f"{name}: {e}")
+    finally:
+        tb.tid_store_free(st)
