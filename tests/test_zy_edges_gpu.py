@@ -237,3 +237,22 @@ def test_university_plans_full_size_sampled(ctx, orc):
                 raise AssertionError(f"{name}: {e}")
     finally:
         tb.tid_store_free(st)
+
+
+def test_entailment_full_size_rules_5_and_11(ctx, orc):
+    """Rules R5 and R11 (the chains of the schema) on the full 200M-triple store
+    plus its RDFS schema, as the benchmark runs them, against the oracle: the
+    conclusions and the paper's step counts."""
+    st_np = synth.with_schema(synth.university_store(synth.UNI_FULL))
+    vocab = synth.rdfs_vocab(st_np.meta["subjects"])
+    st = _store(ctx, st_np.s, st_np.p, st_np.o)
+    try:
+        for rule in (5, 11):
+            h, stats = tb.tid_entail(ctx, st, rule, vocab)
+            got = tb.tid_set_to_host(h).copy()
+            tb.tid_set_free(h)
+            want, wstats = orc.entail(st_np.s, st_np.p, st_np.o, rule, vocab)
+            assert got.shape == want.rows.shape and np.array_equal(got, want.rows), rule
+            assert stats == wstats, (rule, stats, wstats)
+    finally:
+        tb.tid_store_free(st)
