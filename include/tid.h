@@ -327,6 +327,13 @@ typedef struct {
 int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *nodes, int n_nodes,
              tid_set **out);
 
+/* The checks tid_exec and tid_server_submit make before anything runs: node
+ * ops and input counts, inputs that are earlier nodes, join algorithm flags,
+ * and every MATCH pattern (no negative ID, variables only on "?" slots, at
+ * least one variable).  No device work and no context.  Returns TID_OK, or
+ * TID_ERR_ARG / TID_ERR_ID as tid_exec would. */
+int tid_plan_check(const tid_plan_node *nodes, int n_nodes);
+
 /* ------------------------------------------------------------------------ */
 /* tuple sets                                                                */
 /* ------------------------------------------------------------------------ */

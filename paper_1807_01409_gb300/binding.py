@@ -133,6 +133,7 @@ def lib():
         "tid_project": (C.c_int, [_vp, _vp, C.POINTER(C.c_int8), C.c_int, C.POINTER(_vp)]),
         "tid_set_from_host": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, C.POINTER(C.c_int8), C.POINTER(_vp)]),
         "tid_exec": (C.c_int, [_vp, _vp, C.POINTER(tid_plan_node), C.c_int, C.POINTER(_vp)]),
+        "tid_plan_check": (C.c_int, [C.POINTER(tid_plan_node), C.c_int]),
         "tid_match_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, C.c_int64, tid_pattern, _vp, C.c_int64,
                                         _vp]),
         "tid_ctx_inject_alloc_failure": (C.c_int, [_vp, C.c_int64]),
@@ -428,6 +429,12 @@ def plan_nodes(plan):
             for j, v in enumerate(nd["vars"]):
                 x.vars[j] = int(v)
     return nodes
+
+
+def tid_plan_check(plan) -> int:
+    """Status code of the checks tid_exec makes before running a plan (no GPU)."""
+    nodes = plan if isinstance(plan, C.Array) else plan_nodes(plan)
+    return int(lib().tid_plan_check(nodes, len(nodes)))
 
 
 def tid_exec(ctx, st, plan):

@@ -188,6 +188,12 @@ int exec_plan(tid_ctx *ctx, const tid_store *st, const tid_plan_node *nodes, int
 
 }  // namespace tid
 
+extern "C" int tid_plan_check(const tid_plan_node *nodes, int n_nodes) {
+    clear_error();
+    if (!nodes && n_nodes > 0) return fail(TID_ERR_ARG, "tid_plan_check: null plan");
+    return validate_plan(nodes, n_nodes);
+}
+
 extern "C" int tid_exec(tid_ctx *ctx, const tid_store *st, const tid_plan_node *nodes, int n_nodes, tid_set **out) {
     clear_error();
     tid::Range nvtx_range("tid_exec");
