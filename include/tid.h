@@ -174,6 +174,19 @@ int tid_match_multi(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, 
 int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, int q,
                     tid_set **outs);
 
+/* Testing aid for tid_match_batch (the paper has no counterpart): its host-side
+ * planning of pats[0 .. q) -- the distinct (bound positions, key) pairs, split
+ * into sub-batches of at most TID_BATCH_KEYS, each given a perfect-hash table
+ * whose hash parameters are drawn from `seed`, seed + 1, ... (tid_match_batch
+ * uses one fixed starting seed) and split in two when no seed gives a table --
+ * followed by a check of every key the way the kernel looks it up: the
+ * prefilter must admit it, and bucket, displacement and slot must lead to its
+ * own entry, one key per slot.  No device work and no context.  *attempts
+ * receives the number of table builds tried and *sub_batches the number of
+ * sub-batches (either may be NULL).  Returns TID_OK; TID_ERR_ARG / TID_ERR_ID
+ * for bad patterns; TID_ERR_CAPACITY if a check fails (a defect). */
+int tid_batch_table_check(const tid_pattern *pats, int q, uint32_t seed, int *attempts, int *sub_batches);
+
 /* A variant of tid_match that allocates nothing, for callers that may not
  * allocate device memory when they scan (for example a server that gave all
  * free device memory to its own pool at start-up, or a latency-critical loop

@@ -134,6 +134,8 @@ def lib():
         "tid_set_from_host": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, C.POINTER(C.c_int8), C.POINTER(_vp)]),
         "tid_exec": (C.c_int, [_vp, _vp, C.POINTER(tid_plan_node), C.c_int, C.POINTER(_vp)]),
         "tid_plan_check": (C.c_int, [C.POINTER(tid_plan_node), C.c_int]),
+        "tid_batch_table_check": (C.c_int, [C.POINTER(tid_pattern), C.c_int, C.c_uint32, C.POINTER(C.c_int),
+                                            C.POINTER(C.c_int)]),
         "tid_match_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, C.c_int64, tid_pattern, _vp, C.c_int64,
                                         _vp]),
         "tid_ctx_inject_alloc_failure": (C.c_int, [_vp, C.c_int64]),
@@ -357,6 +359,17 @@ def tid_match_batch(ctx, st, patterns):
     ptr = arr.ctypes.data_as(C.POINTER(tid_pattern)) if q else None
     _check(lib().tid_match_batch(ctx, st, ptr, q, outs), "tid_match_batch")
     return [_vp(outs[i]) for i in range(q)]
+
+
+def tid_batch_table_check(patterns, seed):
+    """Host-only check of tid_match_batch's key tables (see tid.h): returns
+    (status, table builds tried, sub-batches)."""
+    arr = pattern_array(patterns)
+    q = int(arr.shape[0])
+    ptr = arr.ctypes.data_as(C.POINTER(tid_pattern)) if q else None
+    tries, subs = C.c_int(0), C.c_int(0)
+    rc = int(lib().tid_batch_table_check(ptr, q, int(seed) & 0xFFFFFFFF, C.byref(tries), C.byref(subs)))
+    return rc, int(tries.value), int(subs.value)
 
 
 def tid_bind(ctx, st, pattern, idx, preds=()):

@@ -56,33 +56,69 @@ struct __align__(16) Entry {  // one table slot: key values under its mask, mask
     int32_t mask_kid;  // mask in bits [30:28], key id in [27:0]; -1 = empty
 };
 
-// Hash of (mask, key under the mask): a multiply-add chain over the bound
-// columns with odd multipliers drawn from the table's seed; the same on host and
-// device.  Bucket and slot take the high bits of products (range reduction by
-// multiply-high), which depend on every bit of the key.
+// Hash of (mask, key under the mask), the same on host and device.  Each bound
+// column's value, xor-ed with a per-column seed, goes through the 32-bit
+// finaliser of MurmurHash3 (Appleby; public domain): a bijection with full
+// avalanche, so the keys of a one-column mask never collide and IDs with
+// arithmetic structure (values a power of two apart, entity and literal IDs
+// 2^30 apart) do not line up.  The mixed values of the mask's columns are
+// combined by xor, rotated per column, with a per-mask seed.  A triple's three
+// mixed values are computed once and serve every mask.  Bucket and slot take
+// the high bits of products (range reduction by multiply-high).
 struct HashParams {
-    uint32_t base, k1, k2, k3, k4;
-    uint32_t f[3];  // prefilter multipliers of s, p, o
+    uint32_t col[3];  // per-column seeds
+    uint32_t msk[8];  // per-mask seeds
+    uint32_t k4;      // slot multiplier
+    uint32_t f[3];    // prefilter multipliers of s, p, o
 };
 
 inline HashParams hash_params(uint32_t seed) {
     HashParams hp;
     uint64_t z = seed;
-    uint32_t v[8];
-    for (int i = 0; i < 8; ++i) {  // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014)
+    uint32_t v[15];
+    for (int i = 0; i < 15; ++i) {  // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014)
         z += 0x9E3779B97F4A7C15ull;
         uint64_t x = z;
         x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
         x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
         v[i] = (uint32_t)((x ^ (x >> 31)) >> 32);
     }
-    hp.base = v[0];
-    hp.k1 = v[1] | 1u;
-    hp.k2 = v[2] | 1u;
-    hp.k3 = v[3] | 1u;
-    hp.k4 = v[4] | 1u;
-    for (int c = 0; c < 3; ++c) hp.f[c] = v[5 + c] | 1u;
+    for (int c = 0; c < 3; ++c) hp.col[c] = v[c];
+    for (int m = 0; m < 8; ++m) hp.msk[m] = v[3 + m];
+    hp.k4 = v[11] | 1u;
+    for (int c = 0; c < 3; ++c) hp.f[c] = v[12 + c] | 1u;
     return hp;
+}
+
+__host__ __device__ __forceinline__ uint32_t kb_fmix(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+
+__host__ __device__ __forceinline__ uint32_t kb_rotl(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }
+
+// mixed value of column c's value v
+__host__ __device__ __forceinline__ uint32_t kb_colmix(const HashParams &hp, int c, uint32_t v) {
+    return kb_fmix(v ^ hp.col[c]);
+}
+
+// hash of mask m from the mixed values of a triple's (or key's) columns
+__host__ __device__ __forceinline__ uint32_t kb_combine(const HashParams &hp, int m, uint32_t ms, uint32_t mp,
+                                                        uint32_t mo) {
+    uint32_t x = hp.msk[m];
+    if (m & 1) x ^= ms;
+    if (m & 2) x ^= kb_rotl(mp, 11);
+    if (m & 4) x ^= kb_rotl(mo, 22);
+    return x;
+}
+
+__host__ __device__ __forceinline__ uint32_t kb_hash(const HashParams &hp, int m, uint32_t s, uint32_t p, uint32_t o) {
+    return kb_combine(hp, m, (m & 1) ? kb_colmix(hp, 0, s) : 0u, (m & 2) ? kb_colmix(hp, 1, p) : 0u,
+                      (m & 4) ? kb_colmix(hp, 2, o) : 0u);
 }
 
 // Prefilter entry of a column value (multiplicative hashing, top 13 bits).  Each
@@ -98,20 +134,11 @@ __host__ __device__ __forceinline__ int kb_fbit(int c, int mask) {  // bit of `m
 }
 
 // masks (bit m) a triple may answer, from its three entries (4-bit each)
-__device__ __forceinline__ uint32_t kb_candidates(uint32_t es, uint32_t ep, uint32_t eo) {
+__host__ __device__ __forceinline__ uint32_t kb_candidates(uint32_t es, uint32_t ep, uint32_t eo) {
     const uint32_t cs = 0x55u | ((es & 1u) << 1) | ((es & 2u) << 2) | ((es & 4u) << 3) | ((es & 8u) << 4);
     const uint32_t cp = 0x33u | ((ep & 3u) << 2) | ((ep & 12u) << 4);
     const uint32_t co = 0x0Fu | (eo << 4);
     return cs & cp & co;
-}
-
-__host__ __device__ __forceinline__ uint32_t kb_hash(const HashParams &hp, int mask, uint32_t s, uint32_t p,
-                                                     uint32_t o) {
-    uint32_t x = hp.base ^ ((uint32_t)mask * 0x9E3779B1u);
-    if (mask & 1) x = (x + s) * hp.k1;
-    if (mask & 2) x = (x + p) * hp.k2;
-    if (mask & 4) x = (x + o) * hp.k3;
-    return x;
 }
 
 __host__ __device__ __forceinline__ uint32_t kb_range(uint32_t x, uint32_t n) {  // floor(x * n / 2^32)
@@ -199,6 +226,10 @@ __global__ void __launch_bounds__(KB_THREADS) k_batch(BatchArgs a) {
             }
             const uint32_t cand = i < hi ? kb_candidates(e3[0], e3[1], e3[2]) : 0u;
             const uint32_t any = __reduce_or_sync(0xffffffffu, cand);
+            // the triple's mixed column values, shared by every mask's hash
+            const uint32_t ms = (U & 1) ? kb_colmix(a.hp, 0, v3[0]) : 0u;
+            const uint32_t mp = (U & 2) ? kb_colmix(a.hp, 1, v3[1]) : 0u;
+            const uint32_t mo = (U & 4) ? kb_colmix(a.hp, 2, v3[2]) : 0u;
             // every candidate mask's lookup first (independent chains), then the hits
             int kid[7];
 #pragma unroll
@@ -208,7 +239,7 @@ __global__ void __launch_bounds__(KB_THREADS) k_batch(BatchArgs a) {
                 // lanes that cannot answer m read slot 0 like the others (a broadcast,
                 // no extra shared-memory wavefront) and keep straight-line code
                 const bool cm = (cand >> m) & 1;
-                const uint32_t h = kb_hash(a.hp, m, vs[u], vp[u], vo[u]);
+                const uint32_t h = kb_combine(a.hp, m, ms, mp, mo);
                 const uint32_t d = s_disp[cm ? kb_bucket(h, a.nb) : 0u];
                 const Entry e = s_tab[cm ? kb_slot(a.hp, h, d, a.ns) : 0u];
                 const bool hit = cm && (e.mask_kid >> 28) == m && (!(m & 1) || e.s == vs[u]) &&
@@ -456,33 +487,106 @@ struct Scratch {
 };
 
 // One sub-batch: key ids 0..K-1; sets[k] receives key id k's list.
-int run_sub_batch(tid_ctx *ctx, const tid_store *st, const std::vector<Key> &keys, std::vector<tid_set *> &sets) {
-    cudaStream_t stream = ctx->stream;
-    const int kids = (int)keys.size();
-    int U = 0;
-    for (auto &k : keys) U |= std::get<0>(k);
-    const uint32_t nb = (uint32_t)std::max(1, (kids + 1) / 2);
-    uint32_t ns = (uint32_t)(kids + kids / 8 + 8);
+// The host-side plan of one sub-batch: its keys (key id = position), the
+// perfect-hash table with its parameters, and the prefilter.
+struct SubPlan {
+    std::vector<Key> keys;
+    int U = 0;  // union of the keys' masks (the columns a pass reads)
+    HashParams hp{};
+    uint32_t nb = 0, ns = 0;
     std::vector<Entry> tab;
     std::vector<uint16_t> disp;
-    std::vector<uint32_t> filt(3 * KB_FILTER_WORDS, 0u);
-    HashParams hp{};
-    for (uint32_t attempt = 0;; ++attempt) {
-        hp = hash_params(0x243F6A88u + attempt);
-        if (build_table(keys, hp, nb, ns, tab, disp)) break;
-        if (attempt == 64) return fail(TID_ERR_CAPACITY, "tid_match_batch: no key table for %d keys", kids);
-        if (attempt % 8 == 7) ns += ns / 8;
+    std::vector<uint32_t> filt;
+};
+
+constexpr uint32_t KB_SEED = 0x243F6A88u;
+constexpr int KB_SEEDS = 16;  // seeds tried before a sub-batch is split in two
+
+// Table and prefilter for `keys`, trying seeds seed, seed + 1, ...; false if
+// none of KB_SEEDS seeds gives a table (the caller splits the keys).
+bool plan_keys(const std::vector<Key> &keys, uint32_t seed, SubPlan &sp, int *attempts) {
+    const int kids = (int)keys.size();
+    sp.keys = keys;
+    sp.U = 0;
+    for (auto &k : keys) sp.U |= std::get<0>(k);
+    sp.nb = (uint32_t)std::max(1, (kids + 1) / 2);
+    sp.ns = (uint32_t)(kids + kids / 8 + 8);
+    bool built = false;
+    for (int attempt = 0; attempt < KB_SEEDS && !built; ++attempt) {
+        ++*attempts;
+        sp.hp = hash_params(seed + (uint32_t)attempt);
+        built = build_table(keys, sp.hp, sp.nb, sp.ns, sp.tab, sp.disp);
     }
+    if (!built) return false;
+    sp.filt.assign(3 * KB_FILTER_WORDS, 0u);
     for (auto &k : keys) {
         int m;
         int32_t kv[3];
         std::tie(m, kv[0], kv[1], kv[2]) = k;
         for (int c = 0; c < 3; ++c)
             if (m & (1 << c)) {
-                const uint32_t f = kb_fentry(hp, c, (uint32_t)kv[c]);
-                filt[c * KB_FILTER_WORDS + (f >> 3)] |= (1u << kb_fbit(c, m)) << ((f & 7u) * 4u);
+                const uint32_t f = kb_fentry(sp.hp, c, (uint32_t)kv[c]);
+                sp.filt[c * KB_FILTER_WORDS + (f >> 3)] |= (1u << kb_fbit(c, m)) << ((f & 7u) * 4u);
             }
     }
+    return true;
+}
+
+// Plans for keys[b, e): one sub-batch if a table is found, else the two halves.
+// A table of one key always exists (any slot is free), so every batch of
+// distinct keys is planned; false only if that ever failed.
+bool plan_range(const std::vector<Key> &keys, size_t b, size_t e, uint32_t seed, std::vector<SubPlan> &plans,
+                std::vector<size_t> &first, int *attempts) {
+    SubPlan sp;
+    const std::vector<Key> sub(keys.begin() + b, keys.begin() + e);
+    if (plan_keys(sub, seed, sp, attempts)) {
+        plans.push_back(std::move(sp));
+        first.push_back(b);
+        return true;
+    }
+    if (e - b < 2) return false;
+    const size_t mid = b + (e - b) / 2;
+    return plan_range(keys, b, mid, seed, plans, first, attempts) &&
+           plan_range(keys, mid, e, seed, plans, first, attempts);
+}
+
+// Sub-batches of at most max_keys distinct keys; first[i] = key id of plans[i]'s key 0.
+int plan_batch(const std::vector<Key> &keys, int max_keys, uint32_t seed, std::vector<SubPlan> &plans,
+               std::vector<size_t> &first, int *attempts) {
+    for (size_t b = 0; b < keys.size(); b += (size_t)max_keys)
+        if (!plan_range(keys, b, std::min(keys.size(), b + (size_t)max_keys), seed, plans, first, attempts))
+            return fail(TID_ERR_CAPACITY, "tid_match_batch: no key table for a single key");
+    return TID_OK;
+}
+
+// Distinct (mask, key) pairs of a batch in first-seen order; kid_of[i] = key id
+// of pattern i, or -1 for (?,?,?) or an empty store (answered by tid_match).
+void batch_keys(const tid_pattern *pats, int q, bool empty_store, std::vector<Key> &keys, std::vector<int> &kid_of) {
+    std::map<Key, int> id_of;
+    kid_of.assign(q, -1);
+    for (int i = 0; i < q; ++i) {
+        const int m = (pats[i].s != 0) | ((pats[i].p != 0) << 1) | ((pats[i].o != 0) << 2);
+        if (m == 0 || empty_store) continue;
+        const Key key = std::make_tuple(m, pats[i].s, pats[i].p, pats[i].o);
+        auto it = id_of.find(key);
+        if (it == id_of.end()) {
+            it = id_of.emplace(key, (int)keys.size()).first;
+            keys.push_back(key);
+        }
+        kid_of[i] = it->second;
+    }
+}
+
+// One sub-batch on the device: key id k of the plan receives sets[k].
+int run_sub_batch(tid_ctx *ctx, const tid_store *st, const SubPlan &sp, std::vector<tid_set *> &sets) {
+    cudaStream_t stream = ctx->stream;
+    const int kids = (int)sp.keys.size();
+    const int U = sp.U;
+    const uint32_t nb = sp.nb, ns = sp.ns;
+    const std::vector<Entry> &tab = sp.tab;
+    const std::vector<uint16_t> &disp = sp.disp;
+    const std::vector<uint32_t> &filt = sp.filt;
+    const HashParams hp = sp.hp;
     const size_t smem = kb_smem_bytes(kids, ns, nb);
     unsigned grid = 0;
     TID_TRY(grid_of(U, true, smem, &grid));
@@ -591,28 +695,18 @@ extern "C" int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_patt
             return fail(TID_ERR_ID, "tid_match_batch: negative ID in pattern %d", i);
     DeviceGuard g(ctx->device);
     // distinct (mask, key) -> key id; (?,?,?) and an empty store go through tid_match
-    std::map<Key, int> id_of;
     std::vector<Key> keys;
-    std::vector<int> kid_of(q, -1);
-    for (int i = 0; i < q; ++i) {
-        const int m = (pats[i].s != 0) | ((pats[i].p != 0) << 1) | ((pats[i].o != 0) << 2);
-        if (m == 0 || st->n == 0) continue;
-        const Key key = std::make_tuple(m, pats[i].s, pats[i].p, pats[i].o);
-        auto it = id_of.find(key);
-        if (it == id_of.end()) {
-            it = id_of.emplace(key, (int)keys.size()).first;
-            keys.push_back(key);
-        }
-        kid_of[i] = it->second;
-    }
-    int rc = TID_OK;
+    std::vector<int> kid_of;
+    batch_keys(pats, q, st->n == 0, keys, kid_of);
+    std::vector<SubPlan> plans;
+    std::vector<size_t> first;
+    int attempts = 0;
+    int rc = plan_batch(keys, KB_MAX_KIDS, KB_SEED, plans, first, &attempts);
     std::vector<tid_set *> by_kid(keys.size(), nullptr);
-    for (size_t b = 0; b < keys.size() && rc == TID_OK; b += KB_MAX_KIDS) {
-        const size_t e = std::min(keys.size(), b + (size_t)KB_MAX_KIDS);
-        std::vector<Key> sub(keys.begin() + b, keys.begin() + e);
-        std::vector<tid_set *> sets(sub.size(), nullptr);
-        rc = run_sub_batch(ctx, st, sub, sets);
-        for (size_t k = 0; k < sets.size(); ++k) by_kid[b + k] = sets[k];
+    for (size_t b = 0; b < plans.size() && rc == TID_OK; ++b) {
+        std::vector<tid_set *> sets(plans[b].keys.size(), nullptr);
+        rc = run_sub_batch(ctx, st, plans[b], sets);
+        for (size_t k = 0; k < sets.size(); ++k) by_kid[first[b] + k] = sets[k];
     }
     // the first pattern of a key id takes its set, equal patterns get views of the same list
     std::vector<bool> taken(keys.size(), false);
@@ -636,5 +730,60 @@ extern "C" int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_patt
         for (size_t k = 0; k < by_kid.size(); ++k) set_free(by_kid[k]);
         return rc;
     }
+    return TID_OK;
+}
+
+// Host-only check of the batch's key tables (no device, no context): the same
+// planning as tid_match_batch, then every key is looked up the way the kernel
+// does -- its prefilter bits, bucket, displacement and slot -- and must find its
+// own entry and key id; no two keys may share a slot.
+extern "C" int tid_batch_table_check(const tid_pattern *pats, int q, uint32_t seed, int *attempts,
+                                     int *sub_batches) {
+    clear_error();
+    if (q < 0 || (q > 0 && !pats)) return fail(TID_ERR_ARG, "tid_batch_table_check: bad patterns");
+    for (int i = 0; i < q; ++i)
+        if (pats[i].s < 0 || pats[i].p < 0 || pats[i].o < 0)
+            return fail(TID_ERR_ID, "tid_batch_table_check: negative ID in pattern %d", i);
+    std::vector<Key> keys;
+    std::vector<int> kid_of;
+    batch_keys(pats, q, false, keys, kid_of);
+    std::vector<SubPlan> plans;
+    std::vector<size_t> first;
+    int tries = 0;
+    TID_TRY(plan_batch(keys, KB_MAX_KIDS, seed, plans, first, &tries));
+    size_t covered = 0;
+    for (size_t b = 0; b < plans.size(); ++b) {
+        const SubPlan &sp = plans[b];
+        if (first[b] != covered) return fail(TID_ERR_CAPACITY, "sub-batch %zu does not follow its predecessor", b);
+        covered += sp.keys.size();
+        std::vector<int> owner(sp.ns, -1);
+        for (int k = 0; k < (int)sp.keys.size(); ++k) {
+            int m;
+            int32_t kv[3];
+            std::tie(m, kv[0], kv[1], kv[2]) = sp.keys[k];
+            uint32_t e3[3];
+            for (int c = 0; c < 3; ++c) {
+                const uint32_t f = kb_fentry(sp.hp, c, (uint32_t)kv[c]);
+                e3[c] = (sp.filt[c * KB_FILTER_WORDS + (f >> 3)] >> ((f & 7u) * 4u)) & 0xFu;
+            }
+            // a triple with this key's values at the bound slots, whatever it holds elsewhere
+            for (uint32_t other = 0; other < 16; ++other) {
+                const uint32_t cand = kb_candidates((m & 1) ? e3[0] : other, (m & 2) ? e3[1] : other,
+                                                    (m & 4) ? e3[2] : other);
+                if (!((cand >> m) & 1)) return fail(TID_ERR_CAPACITY, "prefilter drops key %d of sub-batch %zu", k, b);
+            }
+            const uint32_t h = kb_hash(sp.hp, m, (uint32_t)kv[0], (uint32_t)kv[1], (uint32_t)kv[2]);
+            const uint32_t sl = kb_slot(sp.hp, h, sp.disp[kb_bucket(h, sp.nb)], sp.ns);
+            const Entry &en = sp.tab[sl];
+            if (en.mask_kid != ((m << 28) | k) || ((m & 1) && en.s != kv[0]) || ((m & 2) && en.p != kv[1]) ||
+                ((m & 4) && en.o != kv[2]))
+                return fail(TID_ERR_CAPACITY, "key %d of sub-batch %zu not found at its slot", k, b);
+            if (owner[sl] >= 0) return fail(TID_ERR_CAPACITY, "keys %d and %d share a slot", owner[sl], k);
+            owner[sl] = k;
+        }
+    }
+    if (covered != keys.size()) return fail(TID_ERR_CAPACITY, "sub-batches hold %zu of %zu keys", covered, keys.size());
+    if (attempts) *attempts = tries;
+    if (sub_batches) *sub_batches = (int)plans.size();
     return TID_OK;
 }

@@ -108,6 +108,8 @@ k1_match(const int32_t *__restrict__ S, const int32_t *__restrict__ P, const int
     __syncthreads();
     const unsigned tile = s_tile;
     if (tile >= lb.num_tiles) return;
+    // an earlier segment gave up (its count stayed -1): keep -1, write nothing
+    if (s_base < 0) return;
     const int64_t c0 = seg_begin + (int64_t)tile * chunk_len;
     const int64_t c1 = min(c0 + chunk_len, seg_end);
     const int steps = (int)ceil_div(c1 - c0, K1_STEP);

@@ -12,11 +12,13 @@
 //
 // That array exists once per GPU that loads this library and lives until the
 // process exits.  Every call on a GPU shares it and it keeps the previous
-// call's contents: the ticket counter and the error word are cleared at the
-// start of each call (stream-ordered memsets, no allocation); the status
-// words need no clearing because each launch tags them with a new epoch.
-// Two calls whose GPU work overlaps (different streams without an ordering
-// between them) race on the array and give wrong results: order them.
+// call's contents, so each call first clears all of it (one stream-ordered
+// memset of 32 KB, no allocation): status words, ticket counter and error
+// word start at zero whatever ran before.  After the scan a one-thread kernel
+// sets *count to -1 if any wait gave up, since the caller cannot read the
+// array's error word.  Two calls whose GPU work overlaps (different streams
+// without an ordering between them) race on the array and give wrong results:
+// order them.
 
 #include <mutex>
 
@@ -55,6 +57,12 @@ int device_scratch(int device, DeviceScratch **out) {
     return TID_OK;
 }
 
+// After the scan: a wait that gave up left its code in the error word; the
+// count is then -1, whatever a later tile wrote.
+__global__ void k_noalloc_finish(const unsigned long long *ctl, int64_t *count) {
+    if (*(const int *)(ctl + 1) != 0) *count = -1;
+}
+
 }  // namespace
 
 extern "C" int tid_match_noalloc(int device, void *cuda_stream, const int32_t *s, const int32_t *p,
@@ -85,7 +93,7 @@ extern "C" int tid_match_noalloc(int device, void *cuda_stream, const int32_t *s
                     need, NOALLOC_STATUS_WORDS);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     unsigned long long *ctl = d->base + NOALLOC_STATUS_WORDS;  // ticket, error word
-    TID_TRY_CUDA(cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st), "tid_match_noalloc: clear ticket");
+    TID_TRY_CUDA(cudaMemsetAsync(d->base, 0, sizeof(g_noalloc_scratch), st), "tid_match_noalloc: clear scratch");
     TID_TRY_CUDA(cudaMemsetAsync(count, 0xFF, sizeof(int64_t), st), "tid_match_noalloc: clear count");
     LbScratch sc{};
     sc.status = d->base;
@@ -94,5 +102,7 @@ extern "C" int tid_match_noalloc(int device, void *cuda_stream, const int32_t *s
     sc.err = (int *)(ctl + 1);
     sc.epoch = &d->epoch;
     const bool aligned16 = ((uintptr_t)s % 16 == 0) && ((uintptr_t)p % 16 == 0) && ((uintptr_t)o % 16 == 0);
-    return launch_match(st, s, p, o, n, aligned16, pat.s, pat.p, pat.o, out, cap, count, count, sc);
+    TID_TRY(launch_match(st, s, p, o, n, aligned16, pat.s, pat.p, pat.o, out, cap, count, count, sc));
+    k_noalloc_finish<<<1, 1, 0, st>>>(ctl, count);
+    return launch_check("k_noalloc_finish");
 }

@@ -74,6 +74,32 @@ def test_noalloc_cuts_at_capacity(orc):
         assert (got[cap:] == -7).all(), cap
 
 
+def test_noalloc_store_of_several_segments(orc):
+    """A store larger than one launch covers (resident CTAs x chunk, about 239M
+    triples on a GB300) is scanned in several launches that continue each
+    other's output: counts and lists equal the oracle's, for one- and
+    two-column patterns, with results in every segment."""
+    from paper_1807_01409_gb300 import build
+    build.build()
+    n = (1 << 28) + 13
+    rng = np.random.default_rng(2024)
+    S = rng.integers(1, 1000, n, dtype=np.int32)
+    P = rng.integers(1, 5, n, dtype=np.int32)
+    dS, dP = torch.from_numpy(S).cuda(), torch.from_numpy(P).cuda()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for key in [(int(S[0]), 0, 0), (0, 3, 0), (int(S[-1]), int(P[-1]), 0), (0, 0, int(S[n // 2]))]:
+        torch.cuda.synchronize()
+        tb.tid_match_noalloc(0, None, dS, dP, dS, key, out, cnt)
+        torch.cuda.synchronize()
+        want = orc.match(S, P, S, key)
+        c = int(cnt.item())
+        assert c == want.shape[0], (key, c, want.shape[0])
+        assert want[0] < n // 4 and want[-1] > n - n // 4, key  # hits in the first and the last segment
+        assert np.array_equal(out[:c].cpu().numpy(), want), key
+    del dS, dP, out
+
+
 def test_noalloc_rejects_bad_arguments():
     from paper_1807_01409_gb300 import build
     build.build()
