@@ -463,6 +463,7 @@ typedef struct {
     int64_t max_wave_seen;       /* largest wave */
     int64_t peak_admitted_bytes; /* largest sum of estimates admitted at once */
     int64_t scan_patterns;       /* MATCH nodes searched */
+    int64_t budget_waits;        /* requests that reached the queue's head and waited for budget */
 } tid_server_stats;
 
 #define TID_REQ_INDEX 1  /* nodes = one MATCH node; result: its ascending index list (one column, -1) */

@@ -42,7 +42,7 @@ class tid_server_config(C.Structure):
 
 class tid_server_stats(C.Structure):
     _fields_ = [(f, C.c_int64) for f in ("submitted", "completed", "failed", "waves", "max_wave_seen",
-                                         "peak_admitted_bytes", "scan_patterns")]
+                                         "peak_admitted_bytes", "scan_patterns", "budget_waits")]
 
 
 TID_REQ_INDEX, TID_REQ_PLAN = 1, 2

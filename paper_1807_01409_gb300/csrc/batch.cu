@@ -270,6 +270,119 @@ __global__ void __launch_bounds__(KB_THREADS) k_batch(BatchArgs a) {
         for (int k = lane; k < a.kids; k += 32) row[k] = cnt[k];
 }
 
+// QUEUE shape: only the (triple, mask) pairs the prefilter admits are looked
+// up.  For each 32-triple slot, lane l lists the masks its triple may answer;
+// an exclusive scan over the lanes' counts gives each lane its place in a
+// per-warp queue of (lane, mask) bytes, lane-major, so for any one mask the
+// queue is in triple order.  The warp then looks the queue up 32 entries at a
+// time -- an entry's triple values and mixed columns come from its lane by
+// shuffle -- and counts or writes the hits as the direct shape does (lanes with
+// the same key id grouped by match_any, ranked in queue order, hence in triple
+// order).  Lookups per triple follow the prefilter's candidates instead of the
+// number of masks present; UNROLL slots are loaded per iteration.
+template <int U, bool WRITE, int UNROLL>
+__global__ void __launch_bounds__(KB_THREADS) k_batch_q(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char kb_smem[];
+    __shared__ uint8_t s_queue[KB_WARPS][32 * 7];
+    __shared__ uint32_t s_msk[8];
+    Entry *s_tab = (Entry *)kb_smem;
+    uint16_t *s_disp = (uint16_t *)(s_tab + a.ns);
+    uint32_t *s_filt = (uint32_t *)(kb_smem + sizeof(Entry) * a.ns + kb_disp_bytes(a.nb));
+    uint32_t *s_cnt = s_filt + 3 * KB_FILTER_WORDS;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (uint32_t i = threadIdx.x; i < a.ns; i += KB_THREADS) s_tab[i] = a.table[i];
+    for (uint32_t i = threadIdx.x; i < a.nb; i += KB_THREADS) s_disp[i] = a.disp[i];
+    for (uint32_t i = threadIdx.x; i < 3 * KB_FILTER_WORDS; i += KB_THREADS) s_filt[i] = a.filter[i];
+    if (threadIdx.x < 8) s_msk[threadIdx.x] = a.hp.msk[threadIdx.x];
+    const int64_t gw = (int64_t)blockIdx.x * KB_WARPS + warp;
+    uint32_t *cnt = s_cnt + warp * a.kids;
+    uint32_t *row = a.counts + gw * a.kids;
+    for (int k = lane; k < a.kids; k += 32)
+        cnt[k] = WRITE ? row[k] + (a.abs32 ? (uint32_t)a.off[k] : 0u) : 0u;
+    __syncthreads();
+    uint8_t *queue = s_queue[warp];
+    const int64_t lo = gw * a.slice, hi = min(lo + a.slice, a.n);
+    for (int64_t b0 = lo; b0 < hi; b0 += 32 * UNROLL) {
+        int32_t vs[UNROLL], vp[UNROLL], vo[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int64_t i = b0 + u * 32 + lane;
+            const bool in = i < hi;
+            vs[u] = (U & 1) && in ? __ldcs(a.S + i) : 0;
+            vp[u] = (U & 2) && in ? __ldcs(a.P + i) : 0;
+            vo[u] = (U & 4) && in ? __ldcs(a.O + i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            const int64_t i = b0 + u * 32 + lane;
+            const uint32_t v3[3] = {(uint32_t)vs[u], (uint32_t)vp[u], (uint32_t)vo[u]};
+            uint32_t e3[3] = {0u, 0u, 0u};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (!(U & (1 << c))) continue;
+                const uint32_t f = kb_fentry(a.hp, c, v3[c]);
+                e3[c] = (s_filt[c * KB_FILTER_WORDS + (f >> 3)] >> ((f & 7u) * 4u)) & 0xFu;
+            }
+            const uint32_t cand = i < hi ? kb_candidates(e3[0], e3[1], e3[2]) & 0xFEu : 0u;
+            const unsigned c = __popc(cand);
+            unsigned x = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+                if ((int)lane >= d) x += y;
+            }
+            const unsigned tot = __shfl_sync(0xffffffffu, x, 31);
+            if (tot == 0) continue;
+            unsigned at = x - c;
+            for (uint32_t cm = cand; cm; cm &= cm - 1) queue[at++] = (uint8_t)((lane << 3) | (__ffs(cm) - 1));
+            const uint32_t ms = (U & 1) ? kb_colmix(a.hp, 0, v3[0]) : 0u;
+            const uint32_t mp = (U & 2) ? kb_colmix(a.hp, 1, v3[1]) : 0u;
+            const uint32_t mo = (U & 4) ? kb_colmix(a.hp, 2, v3[2]) : 0u;
+            __syncwarp();
+            for (unsigned r0 = 0; r0 < tot; r0 += 32) {
+                const unsigned e = r0 + lane;
+                const unsigned qe = e < tot ? queue[e] : 0u;
+                const int src = (int)(qe >> 3), m = (int)(qe & 7u);
+                const int32_t ts = (U & 1) ? __shfl_sync(0xffffffffu, vs[u], src) : 0;
+                const int32_t tp = (U & 2) ? __shfl_sync(0xffffffffu, vp[u], src) : 0;
+                const int32_t to = (U & 4) ? __shfl_sync(0xffffffffu, vo[u], src) : 0;
+                const uint32_t hs = (U & 1) ? __shfl_sync(0xffffffffu, ms, src) : 0u;
+                const uint32_t hq = (U & 2) ? __shfl_sync(0xffffffffu, mp, src) : 0u;
+                const uint32_t ho = (U & 4) ? __shfl_sync(0xffffffffu, mo, src) : 0u;
+                int k = -1;
+                if (m != 0) {
+                    uint32_t h = s_msk[m];
+                    if (m & 1) h ^= hs;
+                    if (m & 2) h ^= kb_rotl(hq, 11);
+                    if (m & 4) h ^= kb_rotl(ho, 22);
+                    const uint32_t d = s_disp[kb_bucket(h, a.nb)];
+                    const Entry en = s_tab[kb_slot(a.hp, h, d, a.ns)];
+                    const bool hit = (en.mask_kid >> 28) == m && (!(m & 1) || en.s == ts) &&
+                                     (!(m & 2) || en.p == tp) && (!(m & 4) || en.o == to);
+                    k = hit ? (en.mask_kid & 0x0FFFFFFF) : -1;
+                }
+                if (!__any_sync(0xffffffffu, k >= 0)) continue;
+                const unsigned peers = __match_any_sync(0xffffffffu, k);
+                if (k >= 0) {
+                    const uint32_t cc = cnt[k];
+                    if (WRITE) {
+                        const uint32_t r = cc + __popc(peers & lt);
+                        a.arena[a.abs32 ? (int64_t)r : a.off[k] + r] = (int32_t)(b0 + u * 32 + src);
+                    }
+                    __syncwarp(peers);
+                    if (lane == (unsigned)(__ffs(peers) - 1)) cnt[k] = cc + __popc(peers);
+                }
+                __syncwarp();
+            }
+            __syncwarp();  // the next slot rewrites the queue
+        }
+    }
+    __syncwarp();
+    if (!WRITE)
+        for (int k = lane; k < a.kids; k += 32) row[k] = cnt[k];
+}
+
 // counts[w][k] -> exclusive prefix over w for each k; rows[k] = total of k.
 // Block: 32 key ids (lanes) x 8 ranges of warps (the block's warps).
 __global__ void __launch_bounds__(256) k_batch_scan(uint32_t *counts, int64_t GW, int kids, int64_t *rows) {
@@ -295,123 +408,77 @@ __global__ void __launch_bounds__(256) k_batch_scan(uint32_t *counts, int64_t GW
     }
 }
 
-// resident CTAs of both passes with `smem` bytes of dynamic shared memory
-template <int U, bool SKIP>
+// Kernel shapes the autotuner chooses among.
+enum Shape { SH_DIRECT = 0, SH_DIRECT_SKIP = 1, SH_QUEUE4 = 2, SH_QUEUE8 = 3, SH_COUNT = 4 };
+
+template <int U, bool WRITE, int SH>
+void *kernel_of() {
+    if (SH == SH_DIRECT) return (void *)k_batch<U, WRITE, false>;
+    if (SH == SH_DIRECT_SKIP) return (void *)k_batch<U, WRITE, true>;
+    if (SH == SH_QUEUE4) return (void *)k_batch_q<U, WRITE, 4>;
+    return (void *)k_batch_q<U, WRITE, 8>;
+}
+
+// resident CTAs of both passes of a shape with `smem` bytes of dynamic shared memory
+template <int U, int SH>
 int kb_grid(size_t smem, unsigned *grid) {
     static bool opted = false;
-    if (!opted) {
+    void *kw = kernel_of<U, true, SH>(), *kc = kernel_of<U, false, SH>();
+    if (!opted) {  // dynamic shared memory up to the opt-in limit less the kernel's static share
         int optin = 0, dev = 0;
         cudaGetDevice(&dev);
         TID_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem limit");
-        TID_TRY_CUDA(cudaFuncSetAttribute(k_batch<U, true, SKIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                     "k_batch smem");
-        TID_TRY_CUDA(cudaFuncSetAttribute(k_batch<U, false, SKIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                     "k_batch smem");
+        for (void *k : {kw, kc}) {
+            cudaFuncAttributes fa{};
+            TID_TRY_CUDA(cudaFuncGetAttributes(&fa, k), "k_batch attributes");
+            TID_TRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              optin - (int)fa.sharedSizeBytes),
+                         "k_batch smem");
+        }
         opted = true;
     }
     int v = 0, w = 0;
-    TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<U, true, SKIP>, KB_THREADS, smem),
-                 "occupancy");
-    TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, k_batch<U, false, SKIP>, KB_THREADS, smem),
-                 "occupancy");
+    TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kw, KB_THREADS, smem), "occupancy");
+    TID_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, kc, KB_THREADS, smem), "occupancy");
     if (std::min(v, w) < 1) return fail(TID_ERR_CAPACITY, "tid_match_batch: %zu bytes of shared memory per CTA", smem);
     *grid = (unsigned)(std::min(v, w) * sm_count());
     return TID_OK;
 }
 
-template <int U, bool SKIP>
+template <int U, int SH>
 int run_pass(cudaStream_t st, bool write, unsigned grid, size_t smem, const BatchArgs &a) {
-    if (write) k_batch<U, true, SKIP><<<grid, KB_THREADS, smem, st>>>(a);
-    else k_batch<U, false, SKIP><<<grid, KB_THREADS, smem, st>>>(a);
-    return launch_check("k_batch");
-}
-
-#define KB_DISPATCH(U, call)                              \
-    switch (U) {                                          \
-        case 1: { constexpr int u_ = 1; return call; }    \
-        case 2: { constexpr int u_ = 2; return call; }    \
-        case 3: { constexpr int u_ = 3; return call; }    \
-        case 4: { constexpr int u_ = 4; return call; }    \
-        case 5: { constexpr int u_ = 5; return call; }    \
-        case 6: { constexpr int u_ = 6; return call; }    \
-        default: { constexpr int u_ = 7; return call; }   \
-    }
-
-int grid_of(int U, bool skip, size_t smem, unsigned *grid) {
-    if (skip) KB_DISPATCH(U, (kb_grid<u_, true>(smem, grid)))
-    KB_DISPATCH(U, (kb_grid<u_, false>(smem, grid)))
-}
-
-int pass_of(int U, bool skip, cudaStream_t st, bool write, unsigned grid, size_t smem, const BatchArgs &a) {
-    if (skip) KB_DISPATCH(U, (run_pass<u_, true>(st, write, grid, smem, a)))
-    KB_DISPATCH(U, (run_pass<u_, false>(st, write, grid, smem, a)))
-}
-
-// Autotuner.  The two kernel shapes (SKIP) trade instructions against overlap
-// depending on how often lanes are candidates, which depends on the key set and
-// the store.  On the first sub-batch of each (columns read, log2 of key count),
-// the count pass of both shapes is timed on a prefix of the store (CUDA events,
-// best of two) and the faster one is kept for the process.
-struct TuneKey {
-    int device, U, kbits;
-    bool operator<(const TuneKey &o) const {
-        return std::tie(device, U, kbits) < std::tie(o.device, o.U, o.kbits);
-    }
-};
-std::mutex g_tune_mu;
-std::map<TuneKey, bool> g_tuned;
-
-constexpr int64_t KB_TUNE_TRIPLES = 1 << 25;
-
-// (the passes run on `grid`, the grid the count matrix was sized for)
-int tune_skip(tid_ctx *ctx, int U, int kids, size_t smem, unsigned grid, const BatchArgs &full, bool *skip) {
-    int kbits = 0;
-    while ((1 << kbits) < kids) ++kbits;
-    const TuneKey key{ctx->device, U, kbits};
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) {
-            *skip = it->second;
-            return TID_OK;
-        }
-    }
-    if (full.n < KB_TUNE_TRIPLES / 4) {  // too little store to tell: the shape for few candidates
-        *skip = true;
-        return TID_OK;
-    }
-    cudaStream_t st = ctx->stream;
-    cudaEvent_t ev[3];
-    for (auto &e : ev) TID_TRY_CUDA(cudaEventCreate(&e), "tuner events");
-    float best[2] = {1e30f, 1e30f};
-    int rc = TID_OK;
-    for (int rep = 0; rep < 2 && rc == TID_OK; ++rep)
-        for (int sk = 0; sk < 2 && rc == TID_OK; ++sk) {
-            unsigned g2 = 0;  // opts the shape into the shared memory it needs
-            rc = grid_of(U, sk == 1, smem, &g2);
-            if (rc != TID_OK) break;
-            BatchArgs a = full;
-            a.n = std::min<int64_t>(full.n, KB_TUNE_TRIPLES);
-            const int64_t GW = (int64_t)grid * KB_WARPS, gran = 32 * KB_UNROLL;
-            a.slice = std::max<int64_t>(gran, ceil_div(ceil_div(a.n, GW), gran) * gran);
-            cudaEventRecord(ev[0], st);
-            rc = pass_of(U, sk == 1, st, false, grid, smem, a);
-            cudaEventRecord(ev[1], st);
-            if (rc == TID_OK) {
-                cudaError_t e = cudaEventSynchronize(ev[1]);
-                float ms = 0.f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-                if (e != cudaSuccess) rc = fail_cuda(e, "tuner timing");
-                best[sk] = std::min(best[sk], ms);
-            }
-        }
-    for (auto &e : ev) cudaEventDestroy(e);
-    TID_TRY(rc);
-    *skip = best[1] <= best[0];
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[key] = *skip;
+    void *k = write ? kernel_of<U, true, SH>() : kernel_of<U, false, SH>();
+    BatchArgs args = a;
+    void *params[] = {(void *)&args};
+    TID_TRY_CUDA(cudaLaunchKernel(k, dim3(grid), dim3(KB_THREADS), params, smem, st), "k_batch");
     return TID_OK;
 }
+
+#define KB_DISPATCH_U(SH, U, fn, ...)                                       \
+    switch (U) {                                                          \
+        case 1: return fn<1, SH>(__VA_ARGS__);                            \
+        case 2: return fn<2, SH>(__VA_ARGS__);                            \
+        case 3: return fn<3, SH>(__VA_ARGS__);                            \
+        case 4: return fn<4, SH>(__VA_ARGS__);                            \
+        case 5: return fn<5, SH>(__VA_ARGS__);                            \
+        case 6: return fn<6, SH>(__VA_ARGS__);                            \
+        default: return fn<7, SH>(__VA_ARGS__);                           \
+    }
+#define KB_DISPATCH(shape, U, fn, ...)                                              \
+    switch (shape) {                                                               \
+        case SH_DIRECT: KB_DISPATCH_U(SH_DIRECT, U, fn, __VA_ARGS__)               \
+        case SH_DIRECT_SKIP: KB_DISPATCH_U(SH_DIRECT_SKIP, U, fn, __VA_ARGS__)     \
+        case SH_QUEUE4: KB_DISPATCH_U(SH_QUEUE4, U, fn, __VA_ARGS__)               \
+        default: KB_DISPATCH_U(SH_QUEUE8, U, fn, __VA_ARGS__)                      \
+    }
+
+int grid_of(int U, int shape, size_t smem, unsigned *grid) { KB_DISPATCH(shape, U, kb_grid, smem, grid) }
+
+int pass_of(int U, int shape, cudaStream_t st, bool write, unsigned grid, size_t smem, const BatchArgs &a) {
+    KB_DISPATCH(shape, U, run_pass, st, write, grid, smem, a)
+}
+
+int slots_of(int shape) { return shape == SH_QUEUE4 ? 4 : 8; }  // 32-triple slots per iteration
 
 using Key = std::tuple<int, int32_t, int32_t, int32_t>;  // mask, s, p, o (0 where unbound)
 
@@ -577,103 +644,265 @@ void batch_keys(const tid_pattern *pats, int q, bool empty_store, std::vector<Ke
     }
 }
 
-// One sub-batch on the device: key id k of the plan receives sets[k].
-int run_sub_batch(tid_ctx *ctx, const tid_store *st, const SubPlan &sp, std::vector<tid_set *> &sets) {
-    cudaStream_t stream = ctx->stream;
-    const int kids = (int)sp.keys.size();
-    const int U = sp.U;
-    const uint32_t nb = sp.nb, ns = sp.ns;
-    const std::vector<Entry> &tab = sp.tab;
-    const std::vector<uint16_t> &disp = sp.disp;
-    const std::vector<uint32_t> &filt = sp.filt;
-    const HashParams hp = sp.hp;
-    const size_t smem = kb_smem_bytes(kids, ns, nb);
-    unsigned grid = 0;
-    TID_TRY(grid_of(U, true, smem, &grid));
-    const int64_t GW = (int64_t)grid * KB_WARPS;
-    const int64_t gran = 32 * KB_UNROLL;
-    const int64_t slice = std::max<int64_t>(gran, ceil_div(ceil_div(st->n, GW), gran) * gran);
-
-    SharedBlock *sb = new (std::nothrow) SharedBlock();
-    if (!sb) return fail(TID_ERR_OOM, "host allocation");
-    // the row counts live as long as the lists: both are the sets' shared block
-    int rc = dev_alloc(ctx, &sb->ptr[0], sizeof(int64_t) * kids);
-    if (rc != TID_OK) {
-        delete sb;
-        return rc;
-    }
-    int64_t *d_rows = (int64_t *)sb->ptr[0];
-    auto give_up = [&](int code) {
-        dev_free(ctx, sb->ptr[0]);
-        if (sb->ptr[1]) dev_free(ctx, sb->ptr[1]);
-        delete sb;
-        return code;
-    };
-    Scratch s(ctx);
-    Entry *d_tab = nullptr;
-    uint16_t *d_disp = nullptr;
-    uint32_t *d_filt = nullptr;
+// Device buffers of one sub-batch's table, prefilter and count matrix.
+struct Uploaded {
+    Entry *tab = nullptr;
+    uint16_t *disp = nullptr;
+    uint32_t *filt = nullptr;
     uint32_t *counts = nullptr;
-    int64_t *d_off = nullptr;
-    if ((rc = s.get(&d_tab, ns)) != TID_OK || (rc = s.get(&d_disp, nb)) != TID_OK ||
-        (rc = s.get(&d_filt, 3 * KB_FILTER_WORDS)) != TID_OK ||
-        (rc = s.get(&counts, (size_t)kids * GW)) != TID_OK || (rc = s.get(&d_off, kids)) != TID_OK)
-        return give_up(rc);
-    cudaError_t ce = cudaMemcpyAsync(d_tab, tab.data(), sizeof(Entry) * ns, cudaMemcpyHostToDevice, stream);
-    if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(d_disp, disp.data(), sizeof(uint16_t) * nb, cudaMemcpyHostToDevice, stream);
-    if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(d_filt, filt.data(), sizeof(uint32_t) * 3 * KB_FILTER_WORDS, cudaMemcpyHostToDevice,
-                             stream);
-    if (ce != cudaSuccess) return give_up(fail_cuda(ce, "batch table"));
+    int64_t *off = nullptr;
+};
+
+int upload_plan(tid_ctx *ctx, Scratch &s, const SubPlan &sp, int64_t GW, Uploaded *u) {
+    const int kids = (int)sp.keys.size();
+    TID_TRY(s.get(&u->tab, sp.ns));
+    TID_TRY(s.get(&u->disp, sp.nb));
+    TID_TRY(s.get(&u->filt, 3 * KB_FILTER_WORDS));
+    TID_TRY(s.get(&u->counts, (size_t)kids * GW));
+    TID_TRY(s.get(&u->off, kids));
+    cudaStream_t st = ctx->stream;
+    TID_TRY_CUDA(cudaMemcpyAsync(u->tab, sp.tab.data(), sizeof(Entry) * sp.ns, cudaMemcpyHostToDevice, st),
+                 "batch table");
+    TID_TRY_CUDA(cudaMemcpyAsync(u->disp, sp.disp.data(), sizeof(uint16_t) * sp.nb, cudaMemcpyHostToDevice, st),
+                 "batch table");
+    TID_TRY_CUDA(cudaMemcpyAsync(u->filt, sp.filt.data(), sizeof(uint32_t) * 3 * KB_FILTER_WORDS,
+                                 cudaMemcpyHostToDevice, st),
+                 "batch prefilter");
+    return TID_OK;
+}
+
+BatchArgs batch_args(const tid_store *st, const SubPlan &sp, const Uploaded &u, int64_t slice) {
     BatchArgs a{};
     a.S = st->s;
     a.P = st->p;
     a.O = st->o;
     a.n = st->n;
     a.slice = slice;
-    a.kids = kids;
-    a.hp = hp;
-    a.nb = nb;
-    a.ns = ns;
-    a.table = d_tab;
-    a.disp = d_disp;
-    a.filter = d_filt;
-    a.counts = counts;
-    bool skip = true;
-    if ((rc = tune_skip(ctx, U, kids, smem, grid, a, &skip)) != TID_OK) return give_up(rc);
-    if ((rc = pass_of(U, skip, stream, false, grid, smem, a)) != TID_OK) return give_up(rc);
-    k_batch_scan<<<(unsigned)ceil_div(kids, 32), 256, 0, stream>>>(counts, GW, kids, d_rows);
-    if ((rc = launch_check("k_batch_scan")) != TID_OK) return give_up(rc);
-    std::vector<int64_t> tot(kids), off(kids);
-    ce = cudaMemcpyAsync(tot.data(), d_rows, sizeof(int64_t) * kids, cudaMemcpyDeviceToHost, stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    a.kids = (int)sp.keys.size();
+    a.hp = sp.hp;
+    a.nb = sp.nb;
+    a.ns = sp.ns;
+    a.table = u.tab;
+    a.disp = u.disp;
+    a.filter = u.filt;
+    a.counts = u.counts;
+    return a;
+}
+
+// triples per warp slice: the store split evenly over GW warps, in whole iterations
+int64_t slice_of(int64_t n, int64_t GW, int shape) {
+    const int64_t gran = 32 * slots_of(shape);
+    return std::max<int64_t>(gran, ceil_div(ceil_div(n, GW), gran) * gran);
+}
+
+// ---- autotuner ------------------------------------------------------------------
+//
+// Chooses, per (GPU, store size, masks read, log2 of the distinct keys), the
+// kernel shape (direct lookups of every present mask, with or without warp
+// skips of masks no lane may answer; or the candidate queue with 4 or 8 slots
+// in flight) and the sub-batch size (1920 keys: two CTAs per SM; 1152: three).
+// Each candidate's count pass is timed on a prefix of the store (2^25 triples;
+// CUDA events, best of two) with a table of the batch's first keys, and the
+// candidate with the least (sub-batches x pass time) is kept for the process.
+struct TuneKey {
+    int device, U, kbits, nbits;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(device, U, kbits, nbits) < std::tie(o.device, o.U, o.kbits, o.nbits);
+    }
+};
+struct Choice {
+    int shape = SH_QUEUE8;
+    int max_keys = KB_MAX_KIDS;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, Choice> g_tuned;
+
+constexpr int64_t KB_TUNE_TRIPLES = 1 << 25;
+constexpr int KB_SIZES[2] = {KB_MAX_KIDS, 1152};
+
+int ilog2_ceil(int64_t x) {
+    int b = 0;
+    while (((int64_t)1 << b) < x) ++b;
+    return b;
+}
+
+int tune_batch(tid_ctx *ctx, const tid_store *st, const std::vector<Key> &keys, Choice *out, bool *tuned_now) {
+    *tuned_now = false;
+    int U = 0;
+    for (auto &k : keys) U |= std::get<0>(k);
+    const TuneKey key{ctx->device, U, ilog2_ceil((int64_t)keys.size()), ilog2_ceil(st->n)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            *out = it->second;
+            return TID_OK;
+        }
+    }
+    Choice best;
+    if (st->n >= KB_TUNE_TRIPLES / 4) {
+        cudaStream_t stream = ctx->stream;
+        cudaEvent_t ev[2];
+        for (auto &e : ev) TID_TRY_CUDA(cudaEventCreate(&e), "tuner events");
+        struct EvFree {
+            cudaEvent_t *e;
+            ~EvFree() {
+                cudaEventDestroy(e[0]);
+                cudaEventDestroy(e[1]);
+            }
+        } evf{ev};
+        tid_store pre = *st;
+        pre.n = std::min<int64_t>(st->n, KB_TUNE_TRIPLES);
+        float best_cost = 1e30f;
+        for (int si = 0; si < 2; ++si) {
+            const int size = KB_SIZES[si];
+            if (si > 0 && (int64_t)keys.size() <= KB_SIZES[0] && (int64_t)keys.size() <= size) break;
+            const std::vector<Key> first(keys.begin(), keys.begin() + std::min<size_t>(keys.size(), size));
+            SubPlan sp;
+            int tries = 0;
+            if (!plan_keys(first, KB_SEED, sp, &tries)) continue;
+            const size_t smem = kb_smem_bytes((int)first.size(), sp.ns, sp.nb);
+            const float subs = (float)ceil_div((int64_t)keys.size(), size);
+            for (int shape = 0; shape < SH_COUNT; ++shape) {
+                unsigned grid = 0;
+                if (grid_of(U, shape, smem, &grid) != TID_OK) {
+                    clear_error();
+                    continue;
+                }
+                const int64_t GW = (int64_t)grid * KB_WARPS;
+                Scratch sc(ctx);
+                Uploaded up;
+                TID_TRY(upload_plan(ctx, sc, sp, GW, &up));
+                BatchArgs a = batch_args(&pre, sp, up, slice_of(pre.n, GW, shape));
+                float t = 1e30f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    TID_TRY_CUDA(cudaEventRecord(ev[0], stream), "tuner timing");
+                    TID_TRY(pass_of(U, shape, stream, false, grid, smem, a));
+                    TID_TRY_CUDA(cudaEventRecord(ev[1], stream), "tuner timing");
+                    TID_TRY_CUDA(cudaEventSynchronize(ev[1]), "tuner timing");
+                    float ms = 0.f;
+                    TID_TRY_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]), "tuner timing");
+                    t = std::min(t, ms);
+                }
+                if (subs * t < best_cost) {
+                    best_cost = subs * t;
+                    best.shape = shape;
+                    best.max_keys = size;
+                }
+            }
+        }
+        *tuned_now = true;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+    *out = best;
+    return TID_OK;
+}
+
+// The sub-batches on the device: every count pass and scan first, one
+// synchronisation for all the list sizes, then every write pass.  Key id
+// first[b] + k receives by_kid[first[b] + k].
+int run_batch(tid_ctx *ctx, const tid_store *st, const std::vector<SubPlan> &plans, const std::vector<size_t> &first,
+              int shape, std::vector<tid_set *> &by_kid) {
+    cudaStream_t stream = ctx->stream;
+    const size_t nsub = plans.size();
+    struct Sub {
+        size_t smem = 0;
+        unsigned grid = 0;
+        int64_t GW = 0;
+        Uploaded up;
+        BatchArgs a{};
+        SharedBlock *sb = nullptr;
+        std::vector<int64_t> tot, off;
+    };
+    std::vector<Sub> subs(nsub);
+    Scratch s(ctx);
+    auto give_up = [&](int code) {
+        for (auto &b : subs)
+            if (b.sb) {
+                if (b.sb->ptr[0]) dev_free(ctx, b.sb->ptr[0]);
+                if (b.sb->ptr[1]) dev_free(ctx, b.sb->ptr[1]);
+                delete b.sb;
+                b.sb = nullptr;
+            }
+        return code;
+    };
+    int rc = TID_OK;
+    for (size_t b = 0; b < nsub; ++b) {
+        const SubPlan &sp = plans[b];
+        Sub &x = subs[b];
+        const int kids = (int)sp.keys.size();
+        x.smem = kb_smem_bytes(kids, sp.ns, sp.nb);
+        if ((rc = grid_of(sp.U, shape, x.smem, &x.grid)) != TID_OK) return give_up(rc);
+        x.GW = (int64_t)x.grid * KB_WARPS;
+        x.sb = new (std::nothrow) SharedBlock();
+        if (!x.sb) return give_up(fail(TID_ERR_OOM, "host allocation"));
+        // the row counts live as long as the lists: both are the sets' shared block
+        if ((rc = dev_alloc(ctx, &x.sb->ptr[0], sizeof(int64_t) * kids)) != TID_OK) return give_up(rc);
+        if ((rc = upload_plan(ctx, s, sp, x.GW, &x.up)) != TID_OK) return give_up(rc);
+        x.a = batch_args(st, sp, x.up, slice_of(st->n, x.GW, shape));
+        if ((rc = pass_of(sp.U, shape, stream, false, x.grid, x.smem, x.a)) != TID_OK) return give_up(rc);
+        k_batch_scan<<<(unsigned)ceil_div(kids, 32), 256, 0, stream>>>(x.up.counts, x.GW, kids,
+                                                                       (int64_t *)x.sb->ptr[0]);
+        if ((rc = launch_check("k_batch_scan")) != TID_OK) return give_up(rc);
+        x.tot.resize(kids);
+        cudaError_t ce = cudaMemcpyAsync(x.tot.data(), x.sb->ptr[0], sizeof(int64_t) * kids, cudaMemcpyDeviceToHost,
+                                         stream);
+        if (ce != cudaSuccess) return give_up(fail_cuda(ce, "batch totals"));
+    }
+    cudaError_t ce = cudaStreamSynchronize(stream);
     if (ce != cudaSuccess) return give_up(fail_cuda(ce, "batch totals"));
     if ((rc = check_ctx_error(ctx)) != TID_OK) return give_up(rc);
-    int64_t total = 0;
-    for (int k = 0; k < kids; ++k) {  // lists start on 64-byte boundaries
-        off[k] = total;
-        total += (tot[k] + 15) / 16 * 16;
+    for (size_t b = 0; b < nsub; ++b) {
+        Sub &x = subs[b];
+        const int kids = (int)plans[b].keys.size();
+        x.off.resize(kids);
+        int64_t total = 0;
+        for (int k = 0; k < kids; ++k) {  // lists start on 64-byte boundaries
+            x.off[k] = total;
+            total += (x.tot[k] + 15) / 16 * 16;
+        }
+        if ((rc = dev_alloc(ctx, &x.sb->ptr[1], sizeof(int32_t) * std::max<int64_t>(total, 16))) != TID_OK)
+            return give_up(rc);
+        ce = cudaMemcpyAsync(x.up.off, x.off.data(), sizeof(int64_t) * kids, cudaMemcpyHostToDevice, stream);
+        if (ce != cudaSuccess) return give_up(fail_cuda(ce, "batch offsets"));
+        x.a.arena = (int32_t *)x.sb->ptr[1];
+        x.a.off = x.up.off;
+        x.a.abs32 = total < ((int64_t)1 << 32) ? 1 : 0;
+        if ((rc = pass_of(plans[b].U, shape, stream, true, x.grid, x.smem, x.a)) != TID_OK) return give_up(rc);
     }
-    if ((rc = dev_alloc(ctx, &sb->ptr[1], sizeof(int32_t) * std::max<int64_t>(total, 16))) != TID_OK)
-        return give_up(rc);
-    int32_t *arena = (int32_t *)sb->ptr[1];
-    ce = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * kids, cudaMemcpyHostToDevice, stream);
-    if (ce != cudaSuccess) return give_up(fail_cuda(ce, "batch offsets"));
-    a.arena = arena;
-    a.off = d_off;
-    a.abs32 = total < ((int64_t)1 << 32) ? 1 : 0;
-    if ((rc = pass_of(U, skip, stream, true, grid, smem, a)) != TID_OK) return give_up(rc);
-    for (int k = 0; k < kids; ++k) {
-        rc = set_view(ctx, sb, arena + off[k], d_rows + k, tot[k], &sets[k]);
+    // hand each sub-batch's block to its sets (the last set freed releases it)
+    for (size_t b = 0; b < nsub; ++b) {
+        Sub &x = subs[b];
+        const int kids = (int)plans[b].keys.size();
+        int32_t *arena = (int32_t *)x.sb->ptr[1];
+        int64_t *d_rows = (int64_t *)x.sb->ptr[0];
+        for (int k = 0; k < kids; ++k) {
+            rc = set_view(ctx, x.sb, arena + x.off[k], d_rows + k, x.tot[k], &by_kid[first[b] + k]);
+            if (rc != TID_OK) break;
+        }
         if (rc != TID_OK) {
-            if (k == 0) return give_up(rc);
-            for (int j = 0; j < k; ++j) {  // the last of these frees the shared block
-                set_free(sets[j]);
-                sets[j] = nullptr;
+            int made = 0;
+            for (int k = 0; k < kids; ++k) made += by_kid[first[b] + k] != nullptr;
+            if (made == 0) {  // nothing holds this block yet
+                dev_free(ctx, x.sb->ptr[0]);
+                dev_free(ctx, x.sb->ptr[1]);
+                delete x.sb;
+            }
+            x.sb = nullptr;
+            for (size_t c = b + 1; c < nsub; ++c) {  // blocks no set holds
+                dev_free(ctx, subs[c].sb->ptr[0]);
+                dev_free(ctx, subs[c].sb->ptr[1]);
+                delete subs[c].sb;
+                subs[c].sb = nullptr;
+            }
+            for (auto &h : by_kid) {  // the caller frees nothing: release every set made here
+                if (h) set_free(h);
+                h = nullptr;
             }
             return rc;
         }
+        x.sb = nullptr;
     }
     return TID_OK;
 }
@@ -701,13 +930,12 @@ extern "C" int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_patt
     std::vector<SubPlan> plans;
     std::vector<size_t> first;
     int attempts = 0;
-    int rc = plan_batch(keys, KB_MAX_KIDS, KB_SEED, plans, first, &attempts);
+    Choice ch;
+    bool tuned_now = false;
+    int rc = keys.empty() ? TID_OK : tune_batch(ctx, st, keys, &ch, &tuned_now);
+    if (rc == TID_OK) rc = plan_batch(keys, ch.max_keys, KB_SEED, plans, first, &attempts);
     std::vector<tid_set *> by_kid(keys.size(), nullptr);
-    for (size_t b = 0; b < plans.size() && rc == TID_OK; ++b) {
-        std::vector<tid_set *> sets(plans[b].keys.size(), nullptr);
-        rc = run_sub_batch(ctx, st, plans[b], sets);
-        for (size_t k = 0; k < sets.size(); ++k) by_kid[first[b] + k] = sets[k];
-    }
+    if (rc == TID_OK && !plans.empty()) rc = run_batch(ctx, st, plans, first, ch.shape, by_kid);
     // the first pattern of a key id takes its set, equal patterns get views of the same list
     std::vector<bool> taken(keys.size(), false);
     for (int i = 0; i < q && rc == TID_OK; ++i) {

@@ -18,6 +18,8 @@
 // instruction touches 32 consecutive rows); ranks come from ballots, the
 // tile offset from the decoupled look-back (lookback.cuh).
 
+#include <algorithm>
+
 #include "lookback.cuh"
 #include "ops.cuh"
 
@@ -46,8 +48,9 @@ __device__ __forceinline__ bool pred_ok(const Pred &p, int32_t x) {
 
 // ---- row sources -----------------------------------------------------------
 
-// Row sources write v[0..k) and say whether the row is kept.  Column loops run
-// to TID_MAX_COLS with a guard so v[] stays in registers.
+// A row source says, for a row r < n, whether it is kept (keep: reads only
+// what the test needs) and gives its k output values (values: v[0..k)).
+// Column loops run to TID_MAX_COLS with a guard so v[] stays in registers.
 
 __device__ __forceinline__ bool preds_ok(const Pred *preds, int n_preds, const int32_t *v) {
     bool ok = true;
@@ -74,12 +77,22 @@ struct BindRow {  // triple index -> variable values
     int n_eq;
     Pred preds[MAX_PREDS];
     int n_preds;
-    __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
+    __device__ __forceinline__ void slots(int64_t r, int32_t &t0, int32_t &t1, int32_t &t2) const {
         const int64_t t = idx[r];
         // only the variable slots are read: a bound slot holds the key itself
-        const int32_t t0 = (need & 1) ? S[t] : 0;
-        const int32_t t1 = (need & 2) ? P[t] : 0;
-        const int32_t t2 = (need & 4) ? O[t] : 0;
+        t0 = (need & 1) ? S[t] : 0;
+        t1 = (need & 2) ? P[t] : 0;
+        t2 = (need & 4) ? O[t] : 0;
+    }
+    __device__ __forceinline__ void out_of(int32_t t0, int32_t t1, int32_t t2, int32_t *v) const {
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < k) v[c] = src[c] == 0 ? t0 : (src[c] == 1 ? t1 : t2);
+    }
+    __device__ __forceinline__ bool keep(int64_t r) const {
+        if (n_eq == 0 && n_preds == 0) return true;
+        int32_t t0, t1, t2, v[TID_MAX_COLS];
+        slots(r, t0, t1, t2);
         bool ok = true;
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
@@ -89,10 +102,13 @@ struct BindRow {  // triple index -> variable values
                 ok = ok && a == b;
             }
         }
-#pragma unroll
-        for (int c = 0; c < TID_MAX_COLS; ++c)
-            if (c < k) v[c] = src[c] == 0 ? t0 : (src[c] == 1 ? t1 : t2);
+        out_of(t0, t1, t2, v);
         return ok && preds_ok(preds, n_preds, v);
+    }
+    __device__ __forceinline__ void values(int64_t r, int32_t *v) const {
+        int32_t t0, t1, t2;
+        slots(r, t0, t1, t2);
+        out_of(t0, t1, t2, v);
     }
 };
 
@@ -101,11 +117,24 @@ struct FilterRow {
     int k;
     Pred preds[MAX_PREDS];
     int n_preds;
-    __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
+    __device__ __forceinline__ bool keep(int64_t r) const {  // the predicates' columns only
+        bool ok = true;
+#pragma unroll
+        for (int q = 0; q < MAX_PREDS; ++q) {
+            if (q < n_preds) {
+                const int32_t *cp = col[0];  // selected with constant indices (no local copy of col[])
+#pragma unroll
+                for (int c = 1; c < TID_MAX_COLS; ++c)
+                    if (preds[q].col == c) cp = col[c];
+                ok = ok && pred_ok(preds[q], cp[r]);
+            }
+        }
+        return ok;
+    }
+    __device__ __forceinline__ void values(int64_t r, int32_t *v) const {
 #pragma unroll
         for (int c = 0; c < TID_MAX_COLS; ++c)
             if (c < k) v[c] = col[c][r];
-        return preds_ok(preds, n_preds, v);
     }
 };
 
@@ -113,18 +142,21 @@ struct UniqueRow {  // rows in perm order; keep the first of each run of equal r
     const int32_t *col[TID_MAX_COLS];
     const int32_t *perm;  // may be null (rows already in order)
     int k;
-    __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
-        const int64_t a = perm ? perm[r] : r;
-#pragma unroll
-        for (int c = 0; c < TID_MAX_COLS; ++c)
-            if (c < k) v[c] = col[c][a];
+    __device__ __forceinline__ bool keep(int64_t r) const {
         if (r == 0) return true;
+        const int64_t a = perm ? perm[r] : r;
         const int64_t b = perm ? perm[r - 1] : r - 1;
         bool same = true;
 #pragma unroll
         for (int c = 0; c < TID_MAX_COLS; ++c)
-            if (c < k) same = same && col[c][b] == v[c];
+            if (c < k) same = same && col[c][b] == col[c][a];
         return !same;
+    }
+    __device__ __forceinline__ void values(int64_t r, int32_t *v) const {
+        const int64_t a = perm ? perm[r] : r;
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < k) v[c] = col[c][a];
     }
 };
 
@@ -136,34 +168,32 @@ struct SemiJoinRow {  // store triple r, kept when a slot holds a fixed term and
     int32_t fixed_val;
     int key_slot;
     const int32_t *table;
-    uint32_t tmask;             // table size - 1 (a power of two)
+    int tbits;                  // log2 of the table size
     int k;
     int8_t src[TID_MAX_COLS];   // slot giving output column c
     __device__ __forceinline__ const int32_t *column(int slot) const { return slot == 0 ? S : (slot == 1 ? P : O); }
-    // the fixed and the key column first; the other columns only for rows that pass
-    __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
+    // the fixed column first, the key column and a probe only for rows that pass
+    __device__ __forceinline__ bool keep(int64_t r) const {
         if (fixed_slot >= 0 && column(fixed_slot)[r] != fixed_val) return false;
         const int32_t key = column(key_slot)[r];
         if (key == 0) return false;
-        uint32_t h = ((uint32_t)key * 0x9E3779B1u) & tmask;
-        bool found = false;
+        const uint32_t tmask = (1u << tbits) - 1u;
+        uint32_t h = ((uint32_t)key * 0x9E3779B1u) >> (32 - tbits);  // top bits: all of the key counts
         for (uint32_t probe = 0; probe <= tmask; ++probe) {  // the table is at most half full
             const int32_t e = __ldg(table + h);
-            if (e == key) {
-                found = true;
-                break;
-            }
-            if (e == 0) break;
+            if (e == key) return true;
+            if (e == 0) return false;
             h = (h + 1) & tmask;
         }
-        if (!found) return false;
+        return false;
+    }
+    __device__ __forceinline__ void values(int64_t r, int32_t *v) const {
         const int32_t t0 = (need & 1) ? S[r] : 0;
         const int32_t t1 = (need & 2) ? P[r] : 0;
         const int32_t t2 = (need & 4) ? O[r] : 0;
 #pragma unroll
         for (int c = 0; c < TID_MAX_COLS; ++c)
             if (c < k) v[c] = src[c] == 0 ? t0 : (src[c] == 1 ? t1 : t2);
-        return true;
     }
 };
 
@@ -172,7 +202,8 @@ struct PackedUniqueRow {  // sorted packed keys; keep the first of each run of e
     const K *keys;
     PackSpec ps;
     int k;
-    __device__ __forceinline__ bool load(int64_t r, int32_t *v) const {
+    __device__ __forceinline__ bool keep(int64_t r) const { return r == 0 || keys[r - 1] != keys[r]; }
+    __device__ __forceinline__ void values(int64_t r, int32_t *v) const {
         const K key = keys[r];
 #pragma unroll
         for (int c = 0; c < TID_MAX_COLS; ++c) {
@@ -181,9 +212,30 @@ struct PackedUniqueRow {  // sorted packed keys; keep the first of each run of e
                 v[c] = (int32_t)((f + ps.min[c]) ^ 0x80000000u);
             }
         }
-        return r == 0 || keys[r - 1] != key;
     }
 };
+
+// bounds (sort order) of the values a thread wrote, merged per warp into mm
+__device__ __forceinline__ void merge_bounds(uint32_t *mm, int k_out, const uint32_t *lo, const uint32_t *hi) {
+    const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        if (c < k_out) {
+            uint32_t a = lo[c], b = hi[c];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                a = min(a, __shfl_xor_sync(0xffffffffu, a, d));
+                b = max(b, __shfl_xor_sync(0xffffffffu, b, d));
+            }
+            if (lane == 0 && a <= b) {
+                atomicMin(mm + c, a);
+                atomicMax(mm + TID_MAX_COLS + c, b);
+            }
+        }
+    }
+}
+
+// ---- single-pass compaction (small inputs) ----------------------------------------
 
 template <class Row>
 __global__ void __launch_bounds__(CP_THREADS)
@@ -201,13 +253,16 @@ k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__re
     const unsigned lt = (1u << lane) - 1u;
 
     unsigned keep = 0, wpre[CP_ITEMS];
+    bool kp[CP_ITEMS];
+#pragma unroll
+    for (int j = 0; j < CP_ITEMS; ++j) {  // all tests first: their loads are in flight together
+        const int64_t r = base + j * CP_THREADS + threadIdx.x;
+        kp[j] = row.keep(r < n ? r : n - 1) && r < n;  // rows past n test row n - 1 and are dropped
+    }
 #pragma unroll
     for (int j = 0; j < CP_ITEMS; ++j) {
-        const int64_t r = base + j * CP_THREADS + threadIdx.x;
-        int32_t v[TID_MAX_COLS];
-        const bool kp = r < n && row.load(r, v);
-        keep |= (unsigned)kp << j;
-        const unsigned b = __ballot_sync(0xffffffffu, kp);
+        keep |= (unsigned)kp[j] << j;
+        const unsigned b = __ballot_sync(0xffffffffu, kp[j]);
         wpre[j] = __popc(b & lt);
         if (lane == 0) s_off[j * CP_WARPS + warp] = __popc(b);
     }
@@ -248,7 +303,7 @@ k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__re
         if (!((keep >> j) & 1u)) continue;
         const int64_t r = base + j * CP_THREADS + threadIdx.x;
         int32_t v[TID_MAX_COLS];
-        row.load(r, v);  // second read of a kept row (cached in L1/L2)
+        row.values(r, v);  // the kept row's values (its test read them from L1/L2 at most)
         const long long pos = prefix + s_off[j * CP_WARPS + warp] + wpre[j];
 #pragma unroll
         for (int c = 0; c < TID_MAX_COLS; ++c) {
@@ -260,38 +315,299 @@ k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__re
             }
         }
     }
-    if (mm) {  // column bounds of the kept rows
+    if (mm) merge_bounds(mm, k_out, lo, hi);  // column bounds of the kept rows
+}
+
+// ---- bitmap compaction (large inputs): K1's structure for rows --------------------
+//
+// One cooperative launch.  Phase A: warps draw runs of BC_DRAW steps of 1024
+// rows from one counter; for step j a warp tests rows 1024 j + 32 w + lane
+// (w = 0..31, eight tests in flight per lane), keeps the 32 ballots as the
+// step's keep words and its count, and adds the count to the total of the CTA
+// whose fixed range of steps holds it.  Bounded grid barrier.  Phase C: CTA
+// c's offset is the sum of the earlier CTAs' totals; it block-scans its steps'
+// counts and a warp expands a step: the kept rows' positions in the step go
+// to a shared-memory stage (popc, warp scan, set bits), then the warp reads
+// the kept rows' values in row order and writes them with coalesced stores.
+// A tile never waits for a slower predecessor: the only wait is the barrier.
+
+constexpr int BC_THREADS = 256;
+constexpr int BC_WARPS = BC_THREADS / 32;
+constexpr int BC_STEP = 1024;      // rows per warp step (32 keep words)
+constexpr int BC_DRAW = 8;         // steps per draw from the counter
+constexpr int BC_CHUNK = BC_THREADS;  // steps scanned per round of phase C
+constexpr int BC_TICKET = 32;      // step counter's word in the control block
+constexpr size_t BC_CTL_BYTES = 256;
+constexpr int64_t BC_MIN_ROWS = (int64_t)1 << 18;  // below this, the single-pass kernel
+
+struct BcScratch {
+    uint32_t *bits;      // 32 keep words per step
+    uint32_t *cnt;       // kept rows per step
+    unsigned *ctl;       // [1] grid barrier, [BC_TICKET] step counter
+    unsigned *cta_tot;   // kept rows per CTA range
+    int *err;
+    int64_t steps;
+};
+
+template <class Row>
+__global__ void __launch_bounds__(BC_THREADS)
+k_compact_bitmap(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__restrict__ d_rows,
+                 int64_t *__restrict__ h_rows, BcScratch sc, uint32_t *__restrict__ mm) {
+    __shared__ uint16_t s_stage[BC_WARPS][BC_STEP];
+    __shared__ uint32_t s_cnt[BC_CHUNK], s_off[BC_CHUNK];
+    __shared__ unsigned s_red[BC_WARPS];
+    __shared__ unsigned long long s_pre[BC_WARPS], s_all[BC_WARPS];
+    __shared__ long long s_base;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t per = (sc.steps + gridDim.x - 1) / gridDim.x;  // CTA c owns steps [c per, (c+1) per)
+
+    // ---- phase A: keep words and counts per step
+    {
+        unsigned *ticket = sc.ctl + BC_TICKET;
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(ticket, (unsigned)BC_DRAW);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        unsigned k = 0;
+        while ((int64_t)(t + k) < sc.steps) {
+            const int64_t step = (int64_t)t + k;
+            unsigned nxt = 0;
+            if (lane == 0 && k + 1 == (unsigned)BC_DRAW) nxt = atomicAdd(ticket, (unsigned)BC_DRAW);
+            const int64_t base = step * BC_STEP + lane;
+            uint32_t word = 0;
+            unsigned c = 0;
+#pragma unroll 1
+            for (int w0 = 0; w0 < 32; w0 += 8) {
+                bool kp[8];
 #pragma unroll
-        for (int c = 0; c < TID_MAX_COLS; ++c) {
-            if (c < k_out) {
-                uint32_t a = lo[c], b = hi[c];
+                for (int u = 0; u < 8; ++u) {  // rows past n test row n - 1 (in bounds, no branch) and drop it
+                    const int64_t r = base + (int64_t)(w0 + u) * 32;
+                    kp[u] = row.keep(r < n ? r : n - 1) && r < n;
+                }
 #pragma unroll
-                for (int d = 16; d > 0; d >>= 1) {
-                    a = min(a, __shfl_xor_sync(0xffffffffu, a, d));
-                    b = max(b, __shfl_xor_sync(0xffffffffu, b, d));
+                for (int u = 0; u < 8; ++u) {
+                    const unsigned b = __ballot_sync(0xffffffffu, kp[u]);
+                    if ((int)lane == w0 + u) word = b;
+                    c += __popc(b);
                 }
-                if (lane == 0 && a <= b) {
-                    atomicMin(mm + c, a);
-                    atomicMax(mm + TID_MAX_COLS + c, b);
-                }
+            }
+            __stcg(sc.bits + step * 32 + lane, word);
+            if (lane == 0) {
+                __stcg(sc.cnt + step, c);
+                if (c) atomicAdd(sc.cta_tot + step / per, c);
+            }
+            if (++k == (unsigned)BC_DRAW) {
+                t = __shfl_sync(0xffffffffu, nxt, 0);
+                k = 0;
             }
         }
     }
+    if (!grid_barrier(sc.ctl + 1, gridDim.x, sc.err)) return;
+
+    // ---- phase C: this range's offset, then ordered expansion
+    const int64_t r0 = min((int64_t)blockIdx.x * per, sc.steps), r1 = min(r0 + per, sc.steps);
+    const unsigned mine = __ldcg(sc.cta_tot + blockIdx.x);
+    unsigned long long pre = 0, all = 0;
+    for (unsigned c = threadIdx.x; c < gridDim.x; c += BC_THREADS) {
+        const unsigned v = __ldcg(sc.cta_tot + c);
+        all += v;
+        if (c < blockIdx.x) pre += v;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        pre += __shfl_xor_sync(0xffffffffu, pre, d);
+        all += __shfl_xor_sync(0xffffffffu, all, d);
+    }
+    if (lane == 0) {
+        s_pre[warp] = pre;
+        s_all[warp] = all;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long p = 0, a = 0;
+        for (int w = 0; w < BC_WARPS; ++w) {
+            p += s_pre[w];
+            a += s_all[w];
+        }
+        s_base = (long long)p;
+        if (blockIdx.x == 0) {
+            *d_rows = (int64_t)a;
+            *h_rows = (int64_t)a;
+        }
+    }
+    __syncthreads();
+    if (mine == 0) return;
+    uint32_t lo[TID_MAX_COLS], hi[TID_MAX_COLS];
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        lo[c] = 0xFFFFFFFFu;
+        hi[c] = 0u;
+    }
+    long long run = s_base;
+    for (int64_t q0 = r0; q0 < r1; q0 += BC_CHUNK) {
+        const int64_t j = q0 + threadIdx.x;
+        const unsigned c = j < r1 ? __ldcg(sc.cnt + j) : 0u;
+        unsigned x = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+            if ((int)lane >= d) x += y;
+        }
+        if (lane == 31) s_red[warp] = x;
+        __syncthreads();
+        unsigned wb = 0, rt = 0;
+        for (int w = 0; w < BC_WARPS; ++w) {
+            if (w < (int)warp) wb += s_red[w];
+            rt += s_red[w];
+        }
+        s_cnt[threadIdx.x] = c;
+        s_off[threadIdx.x] = wb + x - c;
+        __syncthreads();
+        uint16_t *stage = s_stage[warp];
+        for (int i = 0; i < 32; ++i) {  // warp w expands steps q0 + 32 w .. + 31
+            const int li = (int)warp * 32 + i;
+            const int64_t step = q0 + li;
+            if (step >= r1) break;
+            const unsigned sn = s_cnt[li];
+            if (sn == 0) continue;
+            // keep word w of a step holds rows 32 w + (0..31): lane w stages its word's rows
+            uint32_t word = __ldcg(sc.bits + step * 32 + lane);
+            const unsigned pc = __popc(word);
+            unsigned xo = pc;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, xo, d);
+                if ((int)lane >= d) xo += y;
+            }
+            unsigned at = xo - pc;
+            while (word) {
+                const int b = __ffs(word) - 1;
+                stage[at++] = (uint16_t)(lane * 32 + b);
+                word &= word - 1;
+            }
+            __syncwarp();
+            const long long o0 = run + s_off[li];
+#pragma unroll 4
+            for (unsigned e = lane; e < sn; e += 32) {
+                int32_t v[TID_MAX_COLS];
+                row.values(step * BC_STEP + stage[e], v);
+                const long long pos = o0 + e;
+#pragma unroll
+                for (int cc = 0; cc < TID_MAX_COLS; ++cc) {
+                    if (cc < k_out) {
+                        if ((unsigned long long)pos < (unsigned long long)cap) out.col[cc][pos] = v[cc];
+                        const uint32_t u = (uint32_t)v[cc] ^ 0x80000000u;
+                        lo[cc] = min(lo[cc], u);
+                        hi[cc] = max(hi[cc], u);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        run += rt;
+        __syncthreads();  // s_red, s_cnt, s_off are reused
+    }
+    if (mm) merge_bounds(mm, k_out, lo, hi);
 }
 
 template <class Row>
+int bitmap_grid(unsigned *grid) {
+    static unsigned cached = 0;
+    if (!cached) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_compact_bitmap<Row>, BC_THREADS, 0) != cudaSuccess ||
+            v <= 0)
+            return fail(TID_ERR_CUDA, "k_compact_bitmap: no resident CTA");
+        cached = (unsigned)(v * sm_count());
+    }
+    *grid = cached;
+    return TID_OK;
+}
+
+// The single-pass kernel reads a kept row's values right after its test, from
+// L1/L2; the bitmap kernel's expansion reads them after the grid barrier,
+// from DRAM once more.  Dense keeps (filters, distinct rows) and random
+// gathers (bind) therefore stay on the single-pass kernel; the bitmap kernel
+// serves sparse keeps over long inputs (the keyed store pass), where the
+// single pass's chain of tiles waiting on their predecessors dominates.
+template <class Row>
 int launch_compact(tid_ctx *ctx, const Row &row, int64_t n, int k_out, const OutCols &out, int64_t cap,
-                   int64_t *d_rows, int64_t *h_rows_dev, uint32_t *mm = nullptr) {
+                   int64_t *d_rows, int64_t *h_rows_dev, uint32_t *mm = nullptr, bool bitmap = false) {
     if (n == 0) {
         TID_TRY_CUDA(cudaMemsetAsync(d_rows, 0, sizeof(int64_t), ctx->stream), "memset rows");
         TID_TRY_CUDA(cudaMemsetAsync(h_rows_dev, 0, sizeof(int64_t), ctx->stream), "memset rows");
         return TID_OK;
     }
-    const unsigned tiles = (unsigned)ceil_div(n, CP_TILE);
-    Lookback lb{};
-    TID_TRY(lookback_scratch(ctx, tiles, &lb));
-    k_compact<Row><<<tiles, CP_THREADS, 0, ctx->stream>>>(row, n, k_out, out, cap, d_rows, h_rows_dev, lb, mm);
-    return launch_check("k_compact");
+    if (n < BC_MIN_ROWS || !bitmap) {
+        const unsigned tiles = (unsigned)ceil_div(n, CP_TILE);
+        Lookback lb{};
+        TID_TRY(lookback_scratch(ctx, tiles, &lb));
+        k_compact<Row><<<tiles, CP_THREADS, 0, ctx->stream>>>(row, n, k_out, out, cap, d_rows, h_rows_dev, lb, mm);
+        return launch_check("k_compact");
+    }
+    unsigned grid = 0;
+    TID_TRY(bitmap_grid<Row>(&grid));
+    const int64_t steps = ceil_div(n, (int64_t)BC_STEP);
+    grid = (unsigned)std::min<int64_t>(grid, steps);
+    const size_t bits_b = (size_t)steps * 32 * 4, cnt_b = ((size_t)steps * 4 + 255) / 256 * 256;
+    const size_t tot_b = (size_t)grid * 4;
+    void *blk = nullptr;
+    TID_TRY(dev_alloc(ctx, &blk, bits_b + cnt_b + BC_CTL_BYTES + tot_b));
+    BcScratch sc{};
+    sc.bits = (uint32_t *)blk;
+    sc.cnt = (uint32_t *)((char *)blk + bits_b);
+    sc.ctl = (unsigned *)((char *)blk + bits_b + cnt_b);
+    sc.cta_tot = (unsigned *)((char *)blk + bits_b + cnt_b + BC_CTL_BYTES);
+    sc.err = ctx->err_dev;
+    sc.steps = steps;
+    int rc = TID_OK;
+    cudaError_t e = cudaMemsetAsync(sc.ctl, 0, BC_CTL_BYTES + tot_b, ctx->stream);
+    if (e != cudaSuccess) rc = fail_cuda(e, "k_compact_bitmap control words");
+    if (rc == TID_OK) {
+        Row r = row;
+        OutCols oc = out;
+        void *args[] = {(void *)&r, (void *)&n, (void *)&k_out, (void *)&oc, (void *)&cap, (void *)&d_rows,
+                        (void *)&h_rows_dev, (void *)&sc, (void *)&mm};
+        e = cudaLaunchCooperativeKernel((const void *)k_compact_bitmap<Row>, dim3(grid), dim3(BC_THREADS), args, 0,
+                                        ctx->stream);
+        if (e != cudaSuccess) rc = fail_cuda(e, "k_compact_bitmap");
+    }
+    dev_free(ctx, blk);
+    return rc;
+}
+
+// Bind with nothing to test (no repeated variable, no predicate): every row is
+// kept in index order, so row r is written at r -- a plain gather, no
+// compaction -- with the column bounds of the output.
+__global__ void __launch_bounds__(256) k_bind_gather(BindRow row, int64_t n, OutCols out, uint32_t *__restrict__ mm,
+                                                     int64_t *__restrict__ d_rows, int64_t *__restrict__ h_rows) {
+    uint32_t lo[TID_MAX_COLS], hi[TID_MAX_COLS];
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        lo[c] = 0xFFFFFFFFu;
+        hi[c] = 0u;
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_iter = ceil_div(n, stride) * stride;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_iter; r += stride) {
+        if (r < n) {
+            int32_t v[TID_MAX_COLS];
+            row.values(r, v);
+#pragma unroll
+            for (int c = 0; c < TID_MAX_COLS; ++c) {
+                if (c < row.k) {
+                    out.col[c][r] = v[c];
+                    const uint32_t u = (uint32_t)v[c] ^ 0x80000000u;
+                    lo[c] = min(lo[c], u);
+                    hi[c] = max(hi[c], u);
+                }
+            }
+        }
+    }
+    if (mm) merge_bounds(mm, row.k, lo, hi);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *d_rows = n;
+        *h_rows = n;
+    }
 }
 
 // ---- exclusive scan of uint32 (look-back) --------------------------------------
@@ -397,11 +713,15 @@ int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, cons
     for (int q = 0; q < n_preds; ++q) r.preds[q] = preds[q];
     OutCols oc{};
     for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
+    if (n > 0 && r.n_eq == 0 && r.n_preds == 0 && n <= out->cap) {
+        k_bind_gather<<<grid_for(n, 256, 8), 256, 0, ctx->stream>>>(r, n, oc, mm, out->d_rows, out->slot.dev);
+        return launch_check("k_bind_gather");
+    }
     return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev, mm);
 }
 
 int compact_semijoin(tid_ctx *ctx, const tid_store *st, int fixed_slot, int32_t fixed_val, int key_slot,
-                     const int32_t *table, uint32_t tmask, const int8_t *src, tid_set *out) {
+                     const int32_t *table, int tbits, const int8_t *src, tid_set *out) {
     SemiJoinRow r{};
     r.S = st->s;
     r.P = st->p;
@@ -410,7 +730,7 @@ int compact_semijoin(tid_ctx *ctx, const tid_store *st, int fixed_slot, int32_t 
     r.fixed_val = fixed_val;
     r.key_slot = key_slot;
     r.table = table;
-    r.tmask = tmask;
+    r.tbits = tbits;
     r.k = out->k;
     r.need = (fixed_slot >= 0 ? 1 << fixed_slot : 0) | (1 << key_slot);
     for (int c = 0; c < out->k; ++c) {
@@ -419,7 +739,7 @@ int compact_semijoin(tid_ctx *ctx, const tid_store *st, int fixed_slot, int32_t 
     }
     OutCols oc{};
     for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
-    return launch_compact(ctx, r, st->n, out->k, oc, out->cap, out->d_rows, out->slot.dev);
+    return launch_compact(ctx, r, st->n, out->k, oc, out->cap, out->d_rows, out->slot.dev, nullptr, true);
 }
 
 int compact_filter(tid_ctx *ctx, const tid_set *in, int64_t n, const Pred *preds, int n_preds, tid_set *out) {

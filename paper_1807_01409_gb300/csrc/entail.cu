@@ -113,12 +113,15 @@ extern "C" int tid_entail(tid_ctx *ctx, const tid_store *st, int rule, const tid
         int64_t got = 0;
         TID_TRY(tid_set_to_host(K, keys.data(), sx.dist1, &got));
     }
-    uint32_t tsize = 16;
-    while (tsize < 2 * (uint64_t)std::max<int64_t>(sx.dist1, 1)) tsize <<= 1;
+    // open addressing, at most half full; the home slot is the top bits of a
+    // multiplicative hash (Knuth), which depend on every bit of the key
+    int tbits = 4;
+    while ((1ull << tbits) < 2 * (uint64_t)std::max<int64_t>(sx.dist1, 1)) ++tbits;
+    const uint32_t tsize = 1u << tbits;
     std::vector<int32_t> table(tsize, 0);
     for (int32_t key : keys) {  // keys are distinct and positive (0 never joins)
         if (key == 0) continue;
-        uint32_t h = ((uint32_t)key * 0x9E3779B1u) & (tsize - 1);
+        uint32_t h = ((uint32_t)key * 0x9E3779B1u) >> (32 - tbits);
         while (table[h] != 0) h = (h + 1) & (tsize - 1);
         table[h] = key;
     }
@@ -152,7 +155,7 @@ extern "C" int tid_entail(tid_ctx *ctx, const tid_store *st, int rule, const tid
     const int fixed_slot = R.data_fixed == NONE ? -1 : 1;
     const int32_t fixed_val = R.data_fixed == NONE ? 0 : term[R.data_fixed];
     if (sx.dist1 > 0) {
-        TID_TRY(compact_semijoin(ctx, st, fixed_slot, fixed_val, R.key_slot, (const int32_t *)d_table, tsize - 1,
+        TID_TRY(compact_semijoin(ctx, st, fixed_slot, fixed_val, R.key_slot, (const int32_t *)d_table, tbits,
                                  bsrc, Braw));
     } else {
         TID_TRY(set_rows_const(Braw, 0));

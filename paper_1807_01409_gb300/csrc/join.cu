@@ -21,7 +21,9 @@
 //    a scan and a scatter); the other side probes it.  A table of at most
 //    2048 slots is copied into shared memory by every probing CTA.
 // A key value 0 (unbound) never matches.  The output is sorted to canonical
-// order; a join of two sets is a set, so no duplicate removal is needed.
+// order unless it is written in that order already (both inputs lead with the
+// shared variables); a join of two sets is a set, so no duplicate removal is
+// needed.
 //
 // Left outer join (OPTIONAL; the library the paper used also offered outer and
 // left joins, Section 4.2): sort-merge only; a left row without a match counts
@@ -68,6 +70,48 @@ __device__ __forceinline__ void block_add_u64(unsigned long long v, unsigned lon
 }
 
 // ---- sort-merge --------------------------------------------------------------
+// [lo, hi) of the right keys equal to left key row l, searched inside [a0, b0)
+__device__ __forceinline__ void eq_range(const Cols &RK, const Cols &LK, int64_t l, int nk, int64_t a0, int64_t b0,
+                                         int64_t *lo, int64_t *hi) {
+    int64_t a = a0, b = b0;  // lower bound
+    while (a < b) {
+        const int64_t m = (a + b) >> 1;
+        if (cmp_rows(RK, m, LK, l, nk) < 0) a = m + 1;
+        else b = m;
+    }
+    int64_t a2 = a, b2 = b0;  // upper bound
+    while (a2 < b2) {
+        const int64_t m = (a2 + b2) >> 1;
+        if (cmp_rows(RK, m, LK, l, nk) <= 0) a2 = m + 1;
+        else b2 = m;
+    }
+    *lo = a;
+    *hi = a2;
+}
+
+// The left keys are sorted, so the right range of every left row of a warp
+// lies between the lower bound of the warp's first row and the upper bound of
+// its last: two searches over all of R per warp (lanes 0 and 31), then each
+// lane searches only that bracket (a few cache lines, not DRAM at every level).
+// first / last: the warp's first and last left rows (valid, first <= last).
+__device__ __forceinline__ void warp_bracket(const Cols &RK, const Cols &LK, int nk, int64_t nr, int64_t first,
+                                             int64_t last, int64_t *a0, int64_t *b0) {
+    const unsigned lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = nr;
+    if (lane == 0) {
+        int64_t x, y;
+        eq_range(RK, LK, first, nk, 0, nr, &x, &y);
+        lo = x;
+    } else if (lane == 31) {
+        int64_t x, y;
+        eq_range(RK, LK, last, nk, 0, nr, &x, &y);
+        hi = y;
+    }
+    *a0 = __shfl_sync(0xffffffffu, lo, 0);
+    *b0 = __shfl_sync(0xffffffffu, hi, 31);
+}
+
+
 
 // per left row: [lo, hi) of equal keys in the sorted right keys
 constexpr uint32_t NO_MATCH = 0xFFFFFFFFu;  // left outer join: a left row written once, padded
@@ -78,21 +122,14 @@ __global__ void k_sm_count(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, boo
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n_iter = ceil_div(nl, stride) * stride;
     for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n_iter; l += stride) {
+        const int64_t w0 = l - (threadIdx.x & 31);  // the warp's rows: w0 .. w0 + 31
+        int64_t a0 = 0, b0 = nr;
+        if (w0 < nl) warp_bracket(RK, LK, nk, nr, w0, min(w0 + 31, nl - 1), &a0, &b0);
         if (l < nl) {
             uint32_t c = 0, lo = 0;
             if (!has_zero(LK, l, nk)) {
-                int64_t a = 0, b = nr;  // lower bound
-                while (a < b) {
-                    const int64_t m = (a + b) >> 1;
-                    if (cmp_rows(RK, m, LK, l, nk) < 0) a = m + 1;
-                    else b = m;
-                }
-                int64_t a2 = a, b2 = nr;  // upper bound
-                while (a2 < b2) {
-                    const int64_t m = (a2 + b2) >> 1;
-                    if (cmp_rows(RK, m, LK, l, nk) <= 0) a2 = m + 1;
-                    else b2 = m;
-                }
+                int64_t a, a2;
+                eq_range(RK, LK, l, nk, a0, b0, &a, &a2);
                 lo = (uint32_t)a;
                 c = (uint32_t)(a2 - a);
             }
@@ -141,6 +178,115 @@ __global__ void k_join_write(const uint32_t *__restrict__ off, int64_t nl, const
         }
         for (int c = 0; c < kl; ++c) out.c[c][o] = L.c[c][lr];
         for (int c = 0; c < nrest; ++c) out.c[kl + c][o] = Rrest.c[c][rr];
+    }
+}
+
+// Single-pass sort-merge join of inputs that both lead with the key (so they
+// are sorted by it) when one side holds only key columns: then every row of
+// the other side matches at most one row, the output has at most
+// (|other side|, + |L| for a left join) rows, and it can be written without a
+// separate count pass.  A CTA takes a tile of MJ_TILE left rows (tickets in
+// order); each thread finds the matching range of its rows in R (two binary
+// searches), the block scans the counts, the decoupled look-back gives the
+// tile's first output row, and the CTA writes its output rows in order --
+// an output row finds its left row by binary search over the tile's scanned
+// counts in shared memory, so a key with many matches is spread over all the
+// CTA's threads.  The output is canonical as written.
+constexpr int MJ_THREADS = 256;
+constexpr int MJ_ITEMS = 4;
+constexpr int MJ_TILE = MJ_THREADS * MJ_ITEMS;
+
+__global__ void __launch_bounds__(MJ_THREADS)
+k_merge_join(Cols LK, Cols Lall, int kl, int64_t nl, Cols RK, Cols Rrest, int nrest, int64_t nr, int nk, bool left,
+             MCols out, int64_t cap, int64_t *__restrict__ d_rows, int64_t *__restrict__ h_rows, Lookback lb) {
+    __shared__ uint32_t s_excl[MJ_TILE + 1], s_lo[MJ_TILE];
+    __shared__ uint32_t s_wsum[MJ_THREADS / 32];
+    __shared__ unsigned s_tile;
+    __shared__ long long s_prefix;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = lb_ticket(lb);
+    __syncthreads();
+    const unsigned tile = s_tile;
+    if (tile >= lb.num_tiles) return;
+    const int64_t l0 = (int64_t)tile * MJ_TILE;
+    const int rows = (int)min((int64_t)MJ_TILE, nl - l0);
+    uint32_t c[MJ_ITEMS], sum = 0;
+    // the warp's left rows are l0 + 128 w .. + 127: bracket their right ranges
+    const int wf = (int)warp * 32 * MJ_ITEMS;
+    int64_t a0 = 0, b0 = nr;
+    if (wf < rows) warp_bracket(RK, LK, nk, nr, l0 + wf, l0 + min(wf + 32 * MJ_ITEMS, rows) - 1, &a0, &b0);
+#pragma unroll
+    for (int i = 0; i < MJ_ITEMS; ++i) {  // thread t: left rows l0 + 4t .. 4t + 3
+        const int li = (int)threadIdx.x * MJ_ITEMS + i;
+        const int64_t l = l0 + li;
+        uint32_t cnt = 0, lo = 0;
+        if (li < rows) {
+            if (!has_zero(LK, l, nk)) {
+                int64_t a, a2;
+                eq_range(RK, LK, l, nk, a0, b0, &a, &a2);
+                lo = (uint32_t)a;
+                cnt = (uint32_t)(a2 - a);
+            }
+            if (left && cnt == 0) {
+                cnt = 1;
+                lo = NO_MATCH;
+            }
+            s_lo[li] = lo;
+        }
+        c[i] = cnt;
+        sum += cnt;
+    }
+    uint32_t x = sum;  // block exclusive scan of the per-thread sums
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if ((int)lane >= d) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    uint32_t wb = 0, tot = 0;
+    for (int w = 0; w < MJ_THREADS / 32; ++w) {
+        if (w < (int)warp) wb += s_wsum[w];
+        tot += s_wsum[w];
+    }
+    uint32_t run = wb + x - sum;
+#pragma unroll
+    for (int i = 0; i < MJ_ITEMS; ++i) {
+        s_excl[threadIdx.x * MJ_ITEMS + i] = run;
+        run += c[i];
+    }
+    if (threadIdx.x == 0) s_excl[MJ_TILE] = tot;
+    if (warp == 0) {
+        const long long excl = lb_exclusive_prefix(lb, tile, tot);
+        if (lane == 0) {
+            s_prefix = excl;
+            if (tile == lb.num_tiles - 1 && excl >= 0) {
+                *d_rows = excl + tot;
+                *h_rows = excl + tot;
+            }
+        }
+    }
+    __syncthreads();
+    const long long base = s_prefix;
+    if (base < 0) return;
+    for (uint32_t o = threadIdx.x; o < tot; o += MJ_THREADS) {
+        int a = 0, b = rows;  // first local row whose exclusive count exceeds o
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (s_excl[m] <= o) a = m + 1;
+            else b = m;
+        }
+        const int li = a - 1;
+        const long long pos = base + o;
+        if (pos >= cap) continue;
+        const int64_t l = l0 + li;
+        for (int cc = 0; cc < kl; ++cc) out.c[cc][pos] = Lall.c[cc][l];
+        if (s_lo[li] == NO_MATCH) {
+            for (int cc = 0; cc < nrest; ++cc) out.c[kl + cc][pos] = 0;
+        } else {
+            const int64_t j = (int64_t)s_lo[li] + (o - s_excl[li]);
+            for (int cc = 0; cc < nrest; ++cc) out.c[kl + cc][pos] = Rrest.c[cc][j];
+        }
     }
 }
 
@@ -365,6 +511,54 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
     if (nk == 0 || left) algo = TID_JOIN_SORT_MERGE;  // cross product; left outer join
 
     cudaStream_t st = ctx->stream;
+    Bounds b{};  // output columns keep their input's bounds
+    for (int c = 0; c < L->k; ++c) {
+        b.lo[c] = L->lo[c];
+        b.hi[c] = L->hi[c];
+    }
+    for (int c = 0; c < nrest; ++c) {
+        b.lo[L->k + c] = left ? std::min(R->lo[rrest[c]], 0x80000000u) : R->lo[rrest[c]];  // 0 pads
+        b.hi[L->k + c] = left ? std::max(R->hi[rrest[c]], 0x80000000u) : R->hi[rrest[c]];
+    }
+    const bool bounded = L->bounded && R->bounded;
+    auto finish = [&](tid_set *res) {
+        res->bounded = bounded;
+        for (int c = 0; c < kout && bounded; ++c) {
+            res->lo[c] = b.lo[c];
+            res->hi[c] = b.hi[c];
+        }
+        *out = res;
+        return TID_OK;
+    };
+    if (algo == TID_JOIN_SORT_MERGE && nk > 0 && lprefix && rprefix && (L->k == nk || R->k == nk)) {
+        // single pass into a result sized by the bound on its rows
+        const int64_t ub = (L->k == nk ? nr : nl) + (left && L->k == nk ? nl : 0);
+        tid_set *res = nullptr;
+        TID_TRY(set_alloc(ctx, kout, ovars, ub, &res));
+        Cols LK{}, RK{}, Lall{}, Rrest{};
+        for (int i = 0; i < nk; ++i) {
+            LK.c[i] = L->col[i];
+            RK.c[i] = R->col[i];
+        }
+        for (int c = 0; c < L->k; ++c) Lall.c[c] = L->col[c];
+        for (int c = 0; c < nrest; ++c) Rrest.c[c] = R->col[rrest[c]];
+        MCols oc{};
+        for (int c = 0; c < kout; ++c) oc.c[c] = res->col[c];
+        const unsigned tiles = (unsigned)ceil_div(nl, (int64_t)MJ_TILE);
+        Lookback lb{};
+        int rc = lookback_scratch(ctx, tiles, &lb);
+        if (rc == TID_OK) {
+            k_merge_join<<<tiles, MJ_THREADS, 0, st>>>(LK, Lall, L->k, nl, RK, Rrest, nrest, nr, nk, left, oc, res->cap,
+                                                      res->d_rows, res->slot.dev, lb);
+            rc = launch_check("k_merge_join");
+        }
+        if (rc == TID_OK) rc = set_ready(res);
+        if (rc != TID_OK) {
+            set_free(res);
+            return rc;
+        }
+        return finish(res);
+    }
     Scratch s(ctx);
     Cols Lall{}, Rrest{};
     for (int c = 0; c < L->k; ++c) Lall.c[c] = L->col[c];
@@ -377,6 +571,13 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
     const int32_t *lperm = nullptr, *rperm = nullptr, *rmap = nullptr;
     int64_t n_probe = nl;
     bool left_is_probe = true;
+    // The rows come out already canonical (sorted, distinct) when both inputs
+    // lead with the shared variables in the same order: a sort-merge join walks
+    // L in its order and each left row's matches in R's order, so the output is
+    // ordered by L's columns, then by R's other columns; a hash join does the
+    // same when its build side holds only the key columns (at most one match
+    // per probe row, the output ordered as the probe side).  Then no output sort.
+    bool canonical_out = false;
 
     if (algo == TID_JOIN_SORT_MERGE) {
         Cols LK{}, RK{};
@@ -413,6 +614,7 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         TID_TRY(s.get(&cnt, nl));
         TID_TRY(s.get(&lo, nl));
         TID_TRY(s.get(&off, nl));
+        canonical_out = lprefix && rprefix;
         k_sm_count<<<grid_for(nl, 256), 256, 0, st>>>(LK, nl, RK, nr, nk, left, cnt, lo, d_total);
         TID_TRY(launch_check("k_sm_count"));
         TID_TRY(scan_exclusive_u32(ctx, cnt, off, nl, nullptr));
@@ -460,12 +662,32 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         rmap = grouped;
         n_probe = nq;
         left_is_probe = !build_left;
+        canonical_out = lprefix && rprefix && B->k == nk;
     }
 
     unsigned long long total = 0;
     TID_TRY(read_u64(ctx, d_total, &total));
     if (total > (unsigned long long)INT32_MAX)
         return fail(TID_ERR_CAPACITY, "tid_join: %llu output rows exceed 2^31-1", total);
+    if (canonical_out) {  // write straight into the result set
+        tid_set *res = nullptr;
+        TID_TRY(set_alloc(ctx, kout, ovars, (int64_t)total, &res));
+        MCols oc{};
+        for (int c = 0; c < kout; ++c) oc.c[c] = res->col[c];
+        int rc = TID_OK;
+        if (total > 0) {
+            k_join_write<<<grid_for((int64_t)total, 256), 256, 0, st>>>(
+                off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, Lall, L->k, Rrest, nrest, oc, left_is_probe);
+            rc = launch_check("k_join_write");
+        }
+        if (rc == TID_OK) rc = set_rows_const(res, (int64_t)total);
+        if (rc == TID_OK) rc = set_ready(res);
+        if (rc != TID_OK) {
+            set_free(res);
+            return rc;
+        }
+        return finish(res);
+    }
     // write, then sort to canonical order
     MCols oc{};
     for (int c = 0; c < kout; ++c) TID_TRY(s.get(&oc.c[c], total > 0 ? total : 1));
@@ -476,17 +698,7 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
     }
     const int32_t *ocols[TID_MAX_COLS];
     for (int c = 0; c < kout; ++c) ocols[c] = oc.c[c];
-    Bounds b{};  // output columns keep their input's bounds
-    for (int c = 0; c < L->k; ++c) {
-        b.lo[c] = L->lo[c];
-        b.hi[c] = L->hi[c];
-    }
-    for (int c = 0; c < nrest; ++c) {
-        b.lo[L->k + c] = left ? std::min(R->lo[rrest[c]], 0x80000000u) : R->lo[rrest[c]];  // 0 pads
-        b.hi[L->k + c] = left ? std::max(R->hi[rrest[c]], 0x80000000u) : R->hi[rrest[c]];
-    }
-    return canonicalize(ctx, ocols, kout, ovars, (int64_t)total, false, (L->bounded && R->bounded) ? &b : nullptr,
-                        out);
+    return canonicalize(ctx, ocols, kout, ovars, (int64_t)total, false, bounded ? &b : nullptr, out);
 }
 
 }  // namespace tid

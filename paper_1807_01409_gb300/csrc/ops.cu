@@ -164,25 +164,6 @@ int union_sets(tid_ctx *ctx, const tid_set *const *in, int k, tid_set **out) {
         total += rows[i];
     }
     if (total > INT32_MAX) return fail(TID_ERR_CAPACITY, "tid_union: %lld rows", (long long)total);
-    // concatenate in the union schema (absent variables = 0), then canonical form
-    void *block = nullptr;
-    const size_t colb = ((size_t)(total > 0 ? total : 1) * 4 + 255) / 256 * 256;
-    TID_TRY(dev_alloc(ctx, &block, colb * nu));
-    int rc = TID_OK;
-    int64_t at = 0;
-    const int32_t *cols[TID_MAX_COLS];
-    for (int u = 0; u < nu; ++u) cols[u] = (const int32_t *)((char *)block + colb * u);
-    for (int i = 0; i < k && rc == TID_OK; ++i) {
-        if (rows[i] == 0) continue;
-        for (int u = 0; u < nu && rc == TID_OK; ++u) {
-            int32_t *dst = (int32_t *)cols[u] + at;
-            const int c = find_col(in[i], uv[u]);
-            cudaError_t e = c >= 0 ? cudaMemcpyAsync(dst, in[i]->col[c], (size_t)rows[i] * 4, cudaMemcpyDeviceToDevice, ctx->stream)
-                                   : cudaMemsetAsync(dst, 0, (size_t)rows[i] * 4, ctx->stream);
-            if (e != cudaSuccess) rc = fail_cuda(e, "tid_union copy");
-        }
-        at += rows[i];
-    }
     // bounds of the union: each input's bounds, or the padding value 0
     Bounds b{};
     bool known = true;
@@ -203,6 +184,82 @@ int union_sets(tid_ctx *ctx, const tid_set *const *in, int k, tid_set **out) {
             b.lo[u] = std::min(b.lo[u], lo);
             b.hi[u] = std::max(b.hi[u], hi);
         }
+    }
+    // Each input is canonical in its own column order; padded to the union
+    // schema it stays sorted when its columns keep their relative order there
+    // (a constant 0 column never reorders rows).  Then the union is a chain of
+    // merges that drop duplicates, with no sort.
+    bool ordered = true;
+    for (int i = 0; i < k && ordered; ++i) {
+        int last = -1;
+        for (int u = 0; u < nu; ++u) {
+            const int c = find_col(in[i], uv[u]);
+            if (c < 0) continue;
+            ordered = ordered && c > last;
+            last = c;
+        }
+    }
+    if (ordered) {
+        tid_set *cur = nullptr;  // union of the inputs merged so far (null: only in[0])
+        int rc = TID_OK;
+        for (int i = 1; i < k && rc == TID_OK; ++i) {
+            const int32_t *ac[TID_MAX_COLS], *bc[TID_MAX_COLS];
+            const tid_set *A = cur ? cur : in[0];
+            for (int u = 0; u < nu; ++u) {
+                const int ca = find_col(A, uv[u]), cb = find_col(in[i], uv[u]);
+                ac[u] = ca >= 0 ? A->col[ca] : nullptr;
+                bc[u] = cb >= 0 ? in[i]->col[cb] : nullptr;
+            }
+            int64_t na = 0;
+            rc = set_rows_host(A, &na);
+            tid_set *m = nullptr;
+            if (rc == TID_OK) rc = set_alloc(ctx, nu, uv, na + rows[i], &m);
+            if (rc == TID_OK) rc = merge_unique(ctx, ac, na, bc, rows[i], nu, m);
+            if (rc == TID_OK) rc = set_ready(m);
+            if (cur) set_free(cur);
+            cur = m;
+            if (rc != TID_OK) {
+                if (cur) set_free(cur);
+                return rc;
+            }
+        }
+        if (!cur) {  // one input: its rows in the union schema (already canonical)
+            const int32_t *ac[TID_MAX_COLS], *none[TID_MAX_COLS] = {nullptr};
+            for (int u = 0; u < nu; ++u) ac[u] = in[0]->col[find_col(in[0], uv[u])];
+            rc = set_alloc(ctx, nu, uv, rows[0], &cur);
+            if (rc == TID_OK) rc = merge_unique(ctx, ac, rows[0], none, 0, nu, cur);
+            if (rc == TID_OK) rc = set_ready(cur);
+            if (rc != TID_OK) {
+                if (cur) set_free(cur);
+                return rc;
+            }
+        }
+        cur->bounded = known && total > 0;
+        for (int u = 0; u < nu && cur->bounded; ++u) {
+            cur->lo[u] = b.lo[u];
+            cur->hi[u] = b.hi[u];
+        }
+        *out = cur;
+        return TID_OK;
+    }
+    // otherwise: concatenate in the union schema (absent variables = 0), then canonical form
+    void *block = nullptr;
+    const size_t colb = ((size_t)(total > 0 ? total : 1) * 4 + 255) / 256 * 256;
+    TID_TRY(dev_alloc(ctx, &block, colb * nu));
+    int rc = TID_OK;
+    int64_t at = 0;
+    const int32_t *cols[TID_MAX_COLS];
+    for (int u = 0; u < nu; ++u) cols[u] = (const int32_t *)((char *)block + colb * u);
+    for (int i = 0; i < k && rc == TID_OK; ++i) {
+        if (rows[i] == 0) continue;
+        for (int u = 0; u < nu && rc == TID_OK; ++u) {
+            int32_t *dst = (int32_t *)cols[u] + at;
+            const int c = find_col(in[i], uv[u]);
+            cudaError_t e = c >= 0 ? cudaMemcpyAsync(dst, in[i]->col[c], (size_t)rows[i] * 4, cudaMemcpyDeviceToDevice, ctx->stream)
+                                   : cudaMemsetAsync(dst, 0, (size_t)rows[i] * 4, ctx->stream);
+            if (e != cudaSuccess) rc = fail_cuda(e, "tid_union copy");
+        }
+        at += rows[i];
     }
     if (rc == TID_OK) rc = canonicalize(ctx, cols, nu, uv, total, true, known && total > 0 ? &b : nullptr, out);
     dev_free(ctx, block);
@@ -229,6 +286,28 @@ int project_set(tid_ctx *ctx, const tid_set *in, const int8_t *vars, int n_vars,
         const int c = find_col(in, vars[i]);
         b.lo[i] = in->lo[c];
         b.hi[i] = in->hi[c];
+    }
+    // a leading prefix of a canonical set's columns is sorted already, its
+    // duplicates adjacent: one pass drops them
+    bool prefix = !identity;
+    for (int i = 0; i < n_vars && prefix; ++i) prefix = in->vars[i] == vars[i];
+    if (prefix) {
+        tid_set *o = nullptr;
+        const int32_t *none[TID_MAX_COLS] = {nullptr};
+        TID_TRY(set_alloc(ctx, n_vars, vars, n, &o));
+        int rc = merge_unique(ctx, cols, n, none, 0, n_vars, o);
+        if (rc == TID_OK) rc = set_ready(o);
+        if (rc != TID_OK) {
+            set_free(o);
+            return rc;
+        }
+        o->bounded = in->bounded;
+        for (int i = 0; i < n_vars && o->bounded; ++i) {
+            o->lo[i] = b.lo[i];
+            o->hi[i] = b.hi[i];
+        }
+        *out = o;
+        return TID_OK;
     }
     return canonicalize(ctx, cols, n_vars, vars, n, !identity, in->bounded ? &b : nullptr, out);
 }

@@ -45,9 +45,11 @@ int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, cons
                  const Pred *preds, int n_preds, tid_set *out, uint32_t *mm);
 int compact_filter(tid_ctx *ctx, const tid_set *in, int64_t n, const Pred *preds, int n_preds, tid_set *out);
 // store triples (in store order) whose fixed_slot holds fixed_val (fixed_slot -1:
-// any) and whose key_slot term is in the key table; output column c = slot src[c]
+// any) and whose key_slot term is in the key table (2^tbits slots, home slot =
+// top tbits bits of key * 0x9E3779B1, linear probing, 0 = empty); output column
+// c = slot src[c]
 int compact_semijoin(tid_ctx *ctx, const tid_store *st, int fixed_slot, int32_t fixed_val, int key_slot,
-                     const int32_t *table, uint32_t tmask, const int8_t *src, tid_set *out);
+                     const int32_t *table, int tbits, const int8_t *src, tid_set *out);
 int compact_unique(tid_ctx *ctx, const int32_t *const *cols, int k, const int32_t *perm, int64_t n,
                    tid_set *out);
 // sorted packed keys (64-bit if wide, else 32-bit) -> distinct rows of k columns
@@ -77,6 +79,12 @@ int set_rows_host(const tid_set *set, int64_t *rows);
 // joins (join.cu); right and full outer joins composed from the left join (ops.cu)
 int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out);
 int outer_join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out);
+
+// merge (merge.cu): the distinct rows of two sets each sorted in the same nu
+// columns (acols / bcols, null = absent column, read as 0) into out (capacity
+// >= na + nb), in order; writes the row count
+int merge_unique(tid_ctx *ctx, const int32_t *const *acols, int64_t na, const int32_t *const *bcols, int64_t nb,
+                 int nu, tid_set *out);
 
 // set operators (ops.cu)
 int filter_set(tid_ctx *ctx, const tid_set *in, const tid_pred *preds, int n_preds, tid_set **out);

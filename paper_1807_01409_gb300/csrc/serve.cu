@@ -38,6 +38,7 @@ struct Request {
     std::vector<tid_plan_node> nodes;
     int64_t arrival_ns = 0;
     int64_t est_bytes = 0;
+    bool waited = false;  // held at the queue's head by the budget
     // result
     bool done = false;
     int status = TID_OK;
@@ -144,7 +145,11 @@ void admit(tid_server *S, std::vector<Request *> &wave) {
     while (!S->queue.empty() && (int)wave.size() < S->cfg.max_wave) {
         Request *r = S->queue.front();
         const bool alone = S->admitted_reqs == 0 && wave.empty();
-        if (S->cfg.budget_bytes > 0 && !alone && S->admitted_bytes + r->est_bytes > S->cfg.budget_bytes) break;
+        if (S->cfg.budget_bytes > 0 && !alone && S->admitted_bytes + r->est_bytes > S->cfg.budget_bytes) {
+            if (!r->waited) S->stats.budget_waits++;
+            r->waited = true;
+            break;
+        }
         S->queue.pop_front();
         S->admitted_bytes += r->est_bytes;
         S->admitted_reqs++;

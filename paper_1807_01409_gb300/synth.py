@@ -643,25 +643,34 @@ def batch_queries(s, p, o, m: int = 4096, seed: int = QUERY_SEED, lo: float = 1.
 # a served request stream: Poisson arrivals of three query classes
 # ----------------------------------------------------------------------------
 
-SERVE_MIX = (0.7, 0.15, 0.15)  # index lookups, two-pattern star joins, unions / filters
+# index lookups, two-pattern star joins, unions / filters, wide scans, typed star joins
+SERVE_MIX = (0.68, 0.14, 0.14, 0.02, 0.02)
 
 
 def serving_requests(s, p, o, m: int = 4000, seed: int = QUERY_SEED, mix=SERVE_MIX, hi_index: float = 1e5,
                      rate: float = 20000.0):
     """m requests over a university store held as torch columns, with Poisson
     arrival offsets (seconds, mean rate `rate`).  Returns (kinds, payloads,
-    arrivals): kind "index" carries a Pattern (the answer is its index list; result
-    sizes log-uniform on [1, hi_index] as batch_queries draws them); kind "plan"
-    carries a plan (list of node dicts):
-      * star: (?X p1 o1) JOIN (?X p2 o2), two triples of one random subject whose
+    arrivals): kind "index" carries a Pattern (the answer is its index list); kind
+    "plan" carries a plan (list of node dicts).  The classes, drawn with
+    probabilities `mix` (a shorter mix leaves the later classes out):
+      0 index lookups: result sizes log-uniform on [1, hi_index] (as batch_queries);
+      1 star: (?X p1 o1) JOIN (?X p2 o2), two triples of one random subject whose
         predicates are entity-valued or fine-grained literals (both selective);
-      * union: (s p_j ?Y) for 2-4 predicates of one random subject, UNION;
-      * filter: (s ?P ?V) of one random subject, FILTER ?V in a literal range.
+      2 union: (s p_j ?Y) for 2-4 predicates of one random subject, UNION; or
+        filter: (s ?P ?V) of one random subject, FILTER ?V in a literal range;
+      3 wide scans (the large-scan class): one pattern whose result size is
+        log-uniform on [1e5, 0.3 n];
+      4 typed star joins (the multi-pattern class): (?X type C) JOIN (?X p ?Y),
+        C one of the four most frequent subclasses of a top class in p's domain
+        and p entity-valued with frequency <= 0.02, so the intermediates hold
+        0.1-20M rows at 1B triples.
     Inputs only: subjects and their triples are looked up by sorting the subject
     column (no query evaluation)."""
     import torch
     rng = np.random.default_rng(seed + 20000)
-    kinds = rng.choice(3, size=m, p=np.asarray(mix) / np.sum(mix))
+    mix = np.asarray(mix, np.float64)
+    kinds = rng.choice(len(mix), size=m, p=mix / mix.sum())
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=m))
     n = int(s.shape[0])
     lay = uni_layout(uni_subjects(n))
@@ -672,6 +681,9 @@ def serving_requests(s, p, o, m: int = 4000, seed: int = QUERY_SEED, mix=SERVE_M
             selective.add(pred_base + j)
     n_index = int((kinds == 0).sum())
     idx_q = iter(batch_queries(s, p, o, m=n_index, seed=seed + 1, lo=1.0, hi=hi_index) if n_index else [])
+    n_wide = int((kinds == 3).sum())
+    wide_q = iter(batch_queries(s, p, o, m=n_wide, seed=seed + 2, lo=1e5, hi=max(2e5, 0.3 * n)) if n_wide else [])
+    heavy_preds = [(j, dom) for j, (kind, dom, _) in enumerate(PRED_KIND) if kind == "ent" and PRED_FREQ[j] <= 0.02]
     s_sorted, order = torch.sort(s)
 
     def triples_of(s0):
@@ -687,6 +699,17 @@ def serving_requests(s, p, o, m: int = 4000, seed: int = QUERY_SEED, mix=SERVE_M
     for kd in kinds:
         if kd == 0:
             payloads.append(next(idx_q)[0])
+            continue
+        if kd == 3:
+            payloads.append(next(wide_q)[0])
+            continue
+        if kd == 4:
+            j, dom = heavy_preds[int(rng.integers(0, len(heavy_preds)))]
+            cls = int(rng.choice(np.asarray(list(dom))))
+            c_id = int(lay["class_base"]) + cls * SUBCLASSES + int(rng.integers(0, 4))
+            payloads.append([{"op": "match", "pattern": Pattern(0, pred_base, c_id, var=(X, -1, -1))},
+                             {"op": "match", "pattern": Pattern(0, pred_base + j, 0, var=(X, -1, Y))},
+                             {"op": "join", "inputs": [0, 1], "algo": "auto"}])
             continue
         while True:
             s0 = random_subject()
@@ -719,7 +742,7 @@ def serving_requests(s, p, o, m: int = 4000, seed: int = QUERY_SEED, mix=SERVE_M
             payloads.append(plan)
             break
     del s_sorted, order
-    return ["index" if k == 0 else "plan" for k in kinds], payloads, arrivals
+    return ["index" if k in (0, 3) else "plan" for k in kinds], payloads, arrivals
 
 
 # ----------------------------------------------------------------------------

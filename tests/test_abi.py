@@ -92,7 +92,8 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
         "tid_server_config": (tb.tid_server_config, ["workers", "max_wave", "batch_scans", "reserved",
                                                       "budget_bytes"]),
         "tid_server_stats": (tb.tid_server_stats, ["submitted", "completed", "failed", "waves",
-                                                    "max_wave_seen", "peak_admitted_bytes", "scan_patterns"]),
+                                                    "max_wave_seen", "peak_admitted_bytes", "scan_patterns",
+                                                    "budget_waits"]),
     }
     consts = {
         "TID_OK": tb.TID_OK, "TID_ERR_ARG": tb.TID_ERR_ARG, "TID_ERR_ID": tb.TID_ERR_ID,

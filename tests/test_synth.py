@@ -110,15 +110,30 @@ def test_batch_queries_sizes_and_shapes():
 
 
 def test_serving_requests_stream():
-    """Poisson arrivals at the stated rate, the three classes in their proportions,
-    and every plan well formed (bound slots anonymous, joins on a shared variable)."""
+    """Poisson arrivals at the stated rate, the classes in their proportions
+    (lookups and wide scans are index requests), wide scans and typed star joins
+    present, and every plan well formed (bound slots anonymous, joins on a
+    shared variable)."""
     torch = pytest.importorskip("torch")
     s, p, o = synth.university_store_torch(300_000, device="cpu")
     kinds, payloads, arr = synth.serving_requests(s, p, o, m=2000, rate=20000.0)
     assert np.all(np.diff(arr) > 0)
     assert abs(2000 / arr[-1] - 20000.0) < 2000.0
     frac_index = kinds.count("index") / len(kinds)
-    assert abs(frac_index - synth.SERVE_MIX[0]) < 0.04
+    assert abs(frac_index - synth.SERVE_MIX[0] - synth.SERVE_MIX[3]) < 0.04
+    type_pred = int(synth.uni_layout(synth.uni_subjects(300_000))["pred_ids"][0])
+    typed = [x for k, x in zip(kinds, payloads) if k == "plan" and x[0]["pattern"].p == type_pred]
+    assert len(typed) >= 10
+    sizes = []
+    for k, x in zip(kinds, payloads):
+        if k == "index":
+            key = x.key()
+            msk = torch.ones(s.shape[0], dtype=torch.bool)
+            for col, v in zip((s, p, o), key):
+                if v:
+                    msk &= col == v
+            sizes.append(int(msk.sum()))
+    assert max(sizes) > 0.05 * s.shape[0]  # the wide scans reach large selectivities
     for k, x in zip(kinds, payloads):
         if k == "index":
             assert any(x.key())
