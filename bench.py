@@ -279,9 +279,10 @@ def measure_rows(tb, ctx, store, st, stream, peak, with_oracle=True, reps=3):
     algorithms), union and plan execution on the university store.  For each:
     GPU time of the C-ABI call (CUDA events on the context stream, best of reps),
     algorithmic bytes (the bytes the operation must move at least: inputs read once,
-    outputs written once, one read+write pass for a sort), achieved GB/s against
-    the measured peak, and the oracle's time on the same input (or a stated
-    bounded sample)."""
+    outputs written once, plus one read+write pass where the result must be sorted
+    -- bind and the reordering projection; joins and unions of canonical inputs
+    need none), achieved GB/s against the measured peak, and the oracle's time on
+    the same input (or a stated bounded sample)."""
     import torch
     orc = None
     if with_oracle:
@@ -394,7 +395,7 @@ def measure_rows(tb, ctx, store, st, stream, peak, with_oracle=True, reps=3):
         ms, j = timed(lambda: tb.tid_join(ctx, L, R, algo))
         mj = rows_of(j)
         cpu_ms = cpu_join
-        out[f"a6_join_{algo}"] = entry(ms, 4 * nl + 8 * nr + 8 * mj + 16 * mj, cpu_ms, rows_l=nl, rows_r=nr,
+        out[f"a6_join_{algo}"] = entry(ms, 4 * nl + 8 * nr + 8 * mj, cpu_ms, rows_l=nl, rows_r=nr,
                                        rows_out=mj, oracle_sample="full inputs (oracle sort-merge join)")
 
     # the outer joins on the same inputs: left (OPTIONAL), and right and full composed from it;
@@ -423,7 +424,7 @@ def measure_rows(tb, ctx, store, st, stream, peak, with_oracle=True, reps=3):
         a_s = orc.TupleSet((X, V), tb.tid_set_to_host(full)[:su])
         b_s = orc.TupleSet((X, Y), Rh[:su])
         cpu_ms = cpu(lambda: orc.union([a_s, b_s]), scale=(nf + nr) / (2 * su))
-    out["a7_union"] = entry(ms, 8 * nf + 8 * nr + 12 * mu + 24 * (nf + nr), cpu_ms, rows_in=nf + nr,
+    out["a7_union"] = entry(ms, 8 * nf + 8 * nr + 12 * mu, cpu_ms, rows_in=nf + nr,
                             rows_out=mu, oracle_sample="bounded sample of both inputs, time scaled")
     for h_ in live:
         tb.tid_set_free(h_)
@@ -674,6 +675,7 @@ def measure_batch(tb, ctx, stream, peak, n=BATCH_TRIPLES, m=BATCH_QUERIES, with_
 
     for h in tb.tid_match_batch(ctx, store, pats):
         tb.tid_set_free(h)
+    tuning = tb.tid_batch_tuning(ctx)
     batch_ms, hits_ok = [], True
     for _ in range(reps):
         torch.cuda.synchronize()
@@ -733,6 +735,7 @@ def measure_batch(tb, ctx, stream, peak, n=BATCH_TRIPLES, m=BATCH_QUERIES, with_
         "sub_batches": (len(dk) + tb.TID_BATCH_KEYS - 1) // tb.TID_BATCH_KEYS,
         "result_rows": int(sizes.sum()), "result_rows_distinct_keys": int(sum(distinct.values())),
         "results_match_tallies": hits_ok,
+        "autotuner": tuning,
         "batched": {"ms": bms, "calls": len(batch_ms), "ms_all": [round(x, 3) for x in batch_ms],
                     "queries_per_s": m / (bms / 1e3),
                     "p50_ms": _pct(batch_ms, 50), "p99_ms": _pct(batch_ms, 99),

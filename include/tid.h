@@ -187,6 +187,21 @@ int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_pattern *pats, 
  * for bad patterns; TID_ERR_CAPACITY if a check fails (a defect). */
 int tid_batch_table_check(const tid_pattern *pats, int q, uint32_t seed, int *attempts, int *sub_batches);
 
+/* What the autotuner of tid_match_batch chose for the last call on this
+ * context that searched the store (the paper has no counterpart): the kernel
+ * shape (TID_BATCH_DIRECT: every present mask looked up for every triple;
+ * TID_BATCH_DIRECT_SKIP: the same, skipping masks no lane of a warp may answer;
+ * TID_BATCH_QUEUE4 / TID_BATCH_QUEUE8: only the prefilter's candidates looked
+ * up, 4 or 8 slots of 32 triples in flight), the keys per sub-batch and the
+ * number of sub-batches; -1, 0, 0 before any such call.  Any pointer may be
+ * NULL.  The choice is timed on the first call for each (GPU, store size, masks
+ * read, log2 of the distinct keys) and kept for the process. */
+#define TID_BATCH_DIRECT      0
+#define TID_BATCH_DIRECT_SKIP 1
+#define TID_BATCH_QUEUE4      2
+#define TID_BATCH_QUEUE8      3
+int tid_batch_tuning(const tid_ctx *ctx, int32_t *shape, int32_t *keys_per_sub_batch, int32_t *sub_batches);
+
 /* A variant of tid_match that allocates nothing, for callers that may not
  * allocate device memory when they scan (for example a server that gave all
  * free device memory to its own pool at start-up, or a latency-critical loop

@@ -134,6 +134,7 @@ def lib():
         "tid_set_from_host": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, C.POINTER(C.c_int8), C.POINTER(_vp)]),
         "tid_exec": (C.c_int, [_vp, _vp, C.POINTER(tid_plan_node), C.c_int, C.POINTER(_vp)]),
         "tid_plan_check": (C.c_int, [C.POINTER(tid_plan_node), C.c_int]),
+        "tid_batch_tuning": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "tid_batch_table_check": (C.c_int, [C.POINTER(tid_pattern), C.c_int, C.c_uint32, C.POINTER(C.c_int),
                                             C.POINTER(C.c_int)]),
         "tid_match_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, C.c_int64, tid_pattern, _vp, C.c_int64,
@@ -359,6 +360,16 @@ def tid_match_batch(ctx, st, patterns):
     ptr = arr.ctypes.data_as(C.POINTER(tid_pattern)) if q else None
     _check(lib().tid_match_batch(ctx, st, ptr, q, outs), "tid_match_batch")
     return [_vp(outs[i]) for i in range(q)]
+
+
+BATCH_SHAPES = {0: "direct", 1: "direct_skip", 2: "queue4", 3: "queue8"}
+
+
+def tid_batch_tuning(ctx):
+    """The autotuner's choice for the context's last batched search (see tid.h)."""
+    sh, keys, subs = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().tid_batch_tuning(ctx, C.byref(sh), C.byref(keys), C.byref(subs)), "tid_batch_tuning")
+    return {"shape": BATCH_SHAPES.get(sh.value, None), "keys_per_sub_batch": keys.value, "sub_batches": subs.value}
 
 
 def tid_batch_table_check(patterns, seed):

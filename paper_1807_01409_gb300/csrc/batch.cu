@@ -409,7 +409,13 @@ __global__ void __launch_bounds__(256) k_batch_scan(uint32_t *counts, int64_t GW
 }
 
 // Kernel shapes the autotuner chooses among.
-enum Shape { SH_DIRECT = 0, SH_DIRECT_SKIP = 1, SH_QUEUE4 = 2, SH_QUEUE8 = 3, SH_COUNT = 4 };
+enum Shape {
+    SH_DIRECT = TID_BATCH_DIRECT,
+    SH_DIRECT_SKIP = TID_BATCH_DIRECT_SKIP,
+    SH_QUEUE4 = TID_BATCH_QUEUE4,
+    SH_QUEUE8 = TID_BATCH_QUEUE8,
+    SH_COUNT = 4
+};
 
 template <int U, bool WRITE, int SH>
 void *kernel_of() {
@@ -935,7 +941,12 @@ extern "C" int tid_match_batch(tid_ctx *ctx, const tid_store *st, const tid_patt
     int rc = keys.empty() ? TID_OK : tune_batch(ctx, st, keys, &ch, &tuned_now);
     if (rc == TID_OK) rc = plan_batch(keys, ch.max_keys, KB_SEED, plans, first, &attempts);
     std::vector<tid_set *> by_kid(keys.size(), nullptr);
-    if (rc == TID_OK && !plans.empty()) rc = run_batch(ctx, st, plans, first, ch.shape, by_kid);
+    if (rc == TID_OK && !plans.empty()) {
+        ctx->batch_shape = ch.shape;
+        ctx->batch_keys = ch.max_keys;
+        ctx->batch_subs = (int)plans.size();
+        rc = run_batch(ctx, st, plans, first, ch.shape, by_kid);
+    }
     // the first pattern of a key id takes its set, equal patterns get views of the same list
     std::vector<bool> taken(keys.size(), false);
     for (int i = 0; i < q && rc == TID_OK; ++i) {
@@ -1013,5 +1024,15 @@ extern "C" int tid_batch_table_check(const tid_pattern *pats, int q, uint32_t se
     if (covered != keys.size()) return fail(TID_ERR_CAPACITY, "sub-batches hold %zu of %zu keys", covered, keys.size());
     if (attempts) *attempts = tries;
     if (sub_batches) *sub_batches = (int)plans.size();
+    return TID_OK;
+}
+
+extern "C" int tid_batch_tuning(const tid_ctx *ctx, int32_t *shape, int32_t *keys_per_sub_batch,
+                                int32_t *sub_batches) {
+    clear_error();
+    if (!ctx) return fail(TID_ERR_ARG, "tid_batch_tuning: null context");
+    if (shape) *shape = ctx->batch_shape;
+    if (keys_per_sub_batch) *keys_per_sub_batch = ctx->batch_keys;
+    if (sub_batches) *sub_batches = ctx->batch_subs;
     return TID_OK;
 }

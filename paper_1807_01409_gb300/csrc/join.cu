@@ -48,19 +48,40 @@ struct MCols {
     int32_t *c[TID_MAX_COLS];
 };
 
+// Column loops run to TID_MAX_COLS with a guard: constant indices keep the
+// column pointers in registers (a loop bounded by nk would copy the parameter
+// arrays to local memory).
 __device__ __forceinline__ int cmp_rows(const Cols &A, int64_t a, const Cols &B, int64_t b, int nk) {
-    for (int c = 0; c < nk; ++c) {
-        const int32_t x = A.c[c][a], y = B.c[c][b];
-        if (x < y) return -1;
-        if (x > y) return 1;
+    int r = 0;
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        if (c < nk && r == 0) {
+            const int32_t x = A.c[c][a], y = B.c[c][b];
+            r = x < y ? -1 : (x > y ? 1 : 0);
+        }
     }
-    return 0;
+    return r;
 }
 
 __device__ __forceinline__ bool has_zero(const Cols &A, int64_t a, int nk) {
-    for (int c = 0; c < nk; ++c)
-        if (A.c[c][a] == 0) return true;
-    return false;
+    bool z = false;
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c)
+        if (c < nk) z = z || A.c[c][a] == 0;
+    return z;
+}
+
+// Output row o of a join: column c is src.c[c] at the left row lr, or, when
+// bit c of from_r is set, at the right row rr (rr < 0: unbound, 0).
+__device__ __forceinline__ void write_out(const Cols &src, uint32_t from_r, int kout, int64_t lr, int64_t rr,
+                                          const MCols &dst, int64_t o) {
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        if (c < kout) {
+            const bool r = (from_r >> c) & 1u;
+            dst.c[c][o] = r ? (rr < 0 ? 0 : src.c[c][rr]) : src.c[c][lr];
+        }
+    }
 }
 
 __device__ __forceinline__ void block_add_u64(unsigned long long v, unsigned long long *total) {
@@ -149,8 +170,8 @@ __global__ void k_sm_count(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, boo
 // one thread per output row
 __global__ void k_join_write(const uint32_t *__restrict__ off, int64_t nl, const uint32_t *__restrict__ lo,
                              const int32_t *__restrict__ lperm, const int32_t *__restrict__ rmap,
-                             const int32_t *__restrict__ rperm, int64_t total, Cols L, int kl, Cols Rrest,
-                             int nrest, MCols out, bool left_is_probe) {
+                             const int32_t *__restrict__ rperm, int64_t total, Cols src, uint32_t from_r, int kout,
+                             MCols out, bool left_is_probe) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
          o += (int64_t)gridDim.x * blockDim.x) {
         int64_t a = 0, b = nl;  // first l with off[l] > o
@@ -161,9 +182,7 @@ __global__ void k_join_write(const uint32_t *__restrict__ off, int64_t nl, const
         }
         const int64_t l = a - 1;
         if (lo[l] == NO_MATCH) {  // left outer join: the left row alone, right columns unbound
-            const int64_t lr = lperm ? lperm[l] : l;
-            for (int c = 0; c < kl; ++c) out.c[c][o] = L.c[c][lr];
-            for (int c = 0; c < nrest; ++c) out.c[kl + c][o] = 0;
+            write_out(src, from_r, kout, lperm ? lperm[l] : l, -1, out, o);
             continue;
         }
         const int64_t j = (int64_t)lo[l] + (o - (int64_t)off[l]);
@@ -176,8 +195,7 @@ __global__ void k_join_write(const uint32_t *__restrict__ off, int64_t nl, const
             rr = l;
             lr = rmap[j];
         }
-        for (int c = 0; c < kl; ++c) out.c[c][o] = L.c[c][lr];
-        for (int c = 0; c < nrest; ++c) out.c[kl + c][o] = Rrest.c[c][rr];
+        write_out(src, from_r, kout, lr, rr, out, o);
     }
 }
 
@@ -197,7 +215,7 @@ constexpr int MJ_ITEMS = 4;
 constexpr int MJ_TILE = MJ_THREADS * MJ_ITEMS;
 
 __global__ void __launch_bounds__(MJ_THREADS)
-k_merge_join(Cols LK, Cols Lall, int kl, int64_t nl, Cols RK, Cols Rrest, int nrest, int64_t nr, int nk, bool left,
+k_merge_join(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, bool left, Cols src, uint32_t from_r, int kout,
              MCols out, int64_t cap, int64_t *__restrict__ d_rows, int64_t *__restrict__ h_rows, Lookback lb) {
     __shared__ uint32_t s_excl[MJ_TILE + 1], s_lo[MJ_TILE];
     __shared__ uint32_t s_wsum[MJ_THREADS / 32];
@@ -279,14 +297,8 @@ k_merge_join(Cols LK, Cols Lall, int kl, int64_t nl, Cols RK, Cols Rrest, int nr
         const int li = a - 1;
         const long long pos = base + o;
         if (pos >= cap) continue;
-        const int64_t l = l0 + li;
-        for (int cc = 0; cc < kl; ++cc) out.c[cc][pos] = Lall.c[cc][l];
-        if (s_lo[li] == NO_MATCH) {
-            for (int cc = 0; cc < nrest; ++cc) out.c[kl + cc][pos] = 0;
-        } else {
-            const int64_t j = (int64_t)s_lo[li] + (o - s_excl[li]);
-            for (int cc = 0; cc < nrest; ++cc) out.c[kl + cc][pos] = Rrest.c[cc][j];
-        }
+        const int64_t j = s_lo[li] == NO_MATCH ? -1 : (int64_t)s_lo[li] + (o - s_excl[li]);
+        write_out(src, from_r, kout, l0 + li, j, out, pos);
     }
 }
 
@@ -297,12 +309,15 @@ constexpr int SMEM_SLOTS = 2048;
 
 __device__ __forceinline__ unsigned long long hash_key(const Cols &K, int64_t r, int nk) {
     unsigned long long h = 0x9E3779B97F4A7C15ull;
-    for (int c = 0; c < nk; ++c) {
-        h ^= (unsigned long long)(uint32_t)K.c[c][r];
-        h *= 0xFF51AFD7ED558CCDull;
-        h ^= h >> 33;
-        h *= 0xC4CEB9FE1A85EC53ull;
-        h ^= h >> 29;
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        if (c < nk) {
+            h ^= (unsigned long long)(uint32_t)K.c[c][r];
+            h *= 0xFF51AFD7ED558CCDull;
+            h ^= h >> 33;
+            h *= 0xC4CEB9FE1A85EC53ull;
+            h ^= h >> 29;
+        }
     }
     return h;
 }
@@ -535,20 +550,24 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         const int64_t ub = (L->k == nk ? nr : nl) + (left && L->k == nk ? nl : 0);
         tid_set *res = nullptr;
         TID_TRY(set_alloc(ctx, kout, ovars, ub, &res));
-        Cols LK{}, RK{}, Lall{}, Rrest{};
+        Cols LK{}, RK{}, src{};
         for (int i = 0; i < nk; ++i) {
             LK.c[i] = L->col[i];
             RK.c[i] = R->col[i];
         }
-        for (int c = 0; c < L->k; ++c) Lall.c[c] = L->col[c];
-        for (int c = 0; c < nrest; ++c) Rrest.c[c] = R->col[rrest[c]];
+        uint32_t from_r = 0;
+        for (int c = 0; c < L->k; ++c) src.c[c] = L->col[c];
+        for (int c = 0; c < nrest; ++c) {
+            src.c[L->k + c] = R->col[rrest[c]];
+            from_r |= 1u << (L->k + c);
+        }
         MCols oc{};
         for (int c = 0; c < kout; ++c) oc.c[c] = res->col[c];
         const unsigned tiles = (unsigned)ceil_div(nl, (int64_t)MJ_TILE);
         Lookback lb{};
         int rc = lookback_scratch(ctx, tiles, &lb);
         if (rc == TID_OK) {
-            k_merge_join<<<tiles, MJ_THREADS, 0, st>>>(LK, Lall, L->k, nl, RK, Rrest, nrest, nr, nk, left, oc, res->cap,
+            k_merge_join<<<tiles, MJ_THREADS, 0, st>>>(LK, nl, RK, nr, nk, left, src, from_r, kout, oc, res->cap,
                                                       res->d_rows, res->slot.dev, lb);
             rc = launch_check("k_merge_join");
         }
@@ -560,9 +579,13 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         return finish(res);
     }
     Scratch s(ctx);
-    Cols Lall{}, Rrest{};
-    for (int c = 0; c < L->k; ++c) Lall.c[c] = L->col[c];
-    for (int c = 0; c < nrest; ++c) Rrest.c[c] = R->col[rrest[c]];
+    Cols wsrc{};  // output column c comes from L (row lr) or, bit c of from_r, from R (row rr)
+    uint32_t from_r = 0;
+    for (int c = 0; c < L->k; ++c) wsrc.c[c] = L->col[c];
+    for (int c = 0; c < nrest; ++c) {
+        wsrc.c[L->k + c] = R->col[rrest[c]];
+        from_r |= 1u << (L->k + c);
+    }
     unsigned long long *d_total = nullptr;
     TID_TRY(s.get(&d_total, 1));
     TID_TRY_CUDA(cudaMemsetAsync(d_total, 0, 8, st), "memset");
@@ -677,7 +700,7 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         int rc = TID_OK;
         if (total > 0) {
             k_join_write<<<grid_for((int64_t)total, 256), 256, 0, st>>>(
-                off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, Lall, L->k, Rrest, nrest, oc, left_is_probe);
+                off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, wsrc, from_r, kout, oc, left_is_probe);
             rc = launch_check("k_join_write");
         }
         if (rc == TID_OK) rc = set_rows_const(res, (int64_t)total);
@@ -693,7 +716,7 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
     for (int c = 0; c < kout; ++c) TID_TRY(s.get(&oc.c[c], total > 0 ? total : 1));
     if (total > 0) {
         k_join_write<<<grid_for((int64_t)total, 256), 256, 0, st>>>(
-            off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, Lall, L->k, Rrest, nrest, oc, left_is_probe);
+            off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, wsrc, from_r, kout, oc, left_is_probe);
         TID_TRY(launch_check("k_join_write"));
     }
     const int32_t *ocols[TID_MAX_COLS];

@@ -36,13 +36,18 @@ struct PadCols {  // a set's columns in union-schema order; null = absent (reads
 
 __device__ __forceinline__ int32_t pval(const PadCols &A, int c, int64_t i) { return A.c[c] ? A.c[c][i] : 0; }
 
-// a row of A vs a row of B: -1, 0, 1 in lexicographic int32 order
+// a row of A vs a row of B: -1, 0, 1 in lexicographic int32 order (column loops
+// run to TID_MAX_COLS with a guard so the pointers stay in registers)
 __device__ __forceinline__ int cmp_pad(const PadCols &A, int64_t i, const PadCols &B, int64_t j, int nu) {
-    for (int c = 0; c < nu; ++c) {
-        const int32_t x = pval(A, c, i), y = pval(B, c, j);
-        if (x != y) return x < y ? -1 : 1;
+    int r = 0;
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        if (c < nu && r == 0) {
+            const int32_t x = pval(A, c, i), y = pval(B, c, j);
+            r = x == y ? 0 : (x < y ? -1 : 1);
+        }
     }
-    return 0;
+    return r;
 }
 
 __global__ void k_merge_split(PadCols A, int64_t na, PadCols B, int64_t nb, int nu, int64_t tiles,
@@ -93,19 +98,19 @@ k_merge_unique(PadCols A, int64_t na, PadCols B, int64_t nb, int nu, const int64
     const int64_t a0 = split[tile], a1 = split[tile + 1];
     const int64_t b0 = d0 - a0, b1 = d1 - a1;
     const int la = (int)(a1 - a0), lb_ = (int)(b1 - b0), len = la + lb_;
-    for (int c = 0; c < nu; ++c) {
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        if (c >= nu) continue;
         int32_t *col = s_rows + c * (MG_TILE + 1);
         for (int r = threadIdx.x; r < len; r += MG_THREADS)
             col[r] = r < la ? pval(A, c, a0 + r) : pval(B, c, b0 + (r - la));
     }
     // the merged row before the tile: the later (larger) of A[a0 - 1] and B[b0 - 1]
-    if (threadIdx.x < (unsigned)nu && d0 > 0) {
-        const int c = threadIdx.x;
-        int32_t v;
-        if (a0 == 0) v = pval(B, c, b0 - 1);
-        else if (b0 == 0) v = pval(A, c, a0 - 1);
-        else v = cmp_pad(A, a0 - 1, B, b0 - 1, nu) <= 0 ? pval(B, c, b0 - 1) : pval(A, c, a0 - 1);
-        s_rows[c * (MG_TILE + 1) + MG_TILE] = v;
+    if (threadIdx.x == 0 && d0 > 0) {
+        const bool from_b = a0 == 0 || (b0 > 0 && cmp_pad(A, a0 - 1, B, b0 - 1, nu) <= 0);
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < nu) s_rows[c * (MG_TILE + 1) + MG_TILE] = from_b ? pval(B, c, b0 - 1) : pval(A, c, a0 - 1);
     }
     __syncthreads();
     // this thread's diagonal: local merged rows [dt, dt + 8)
@@ -170,7 +175,9 @@ k_merge_unique(PadCols A, int64_t na, PadCols B, int64_t nb, int nu, const int64
         const long long pos = prefix + s_off[q * MG_WARPS + warp] + wpre[q];
         if (pos >= cap) continue;
         const int r = s_order[p];
-        for (int c = 0; c < nu; ++c) out.col[c][pos] = s_rows[c * (MG_TILE + 1) + r];
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < nu) out.col[c][pos] = s_rows[c * (MG_TILE + 1) + r];
     }
 }
 

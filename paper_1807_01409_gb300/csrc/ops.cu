@@ -309,7 +309,16 @@ int project_set(tid_ctx *ctx, const tid_set *in, const int8_t *vars, int n_vars,
         *out = o;
         return TID_OK;
     }
-    return canonicalize(ctx, cols, n_vars, vars, n, !identity, in->bounded ? &b : nullptr, out);
+    // The input is sorted by its leading columns; when the requested order ends
+    // with them (e.g. (x, v) -> (v, x)) the rows are already in order of that
+    // tail and only the leading requested columns need sorting.
+    int tail = 0;
+    for (int t = n_vars; t >= 1 && tail == 0; --t) {
+        bool ok = true;
+        for (int i = 0; i < t && ok; ++i) ok = in->vars[i] == vars[n_vars - t + i];
+        if (ok) tail = t;
+    }
+    return canonicalize(ctx, cols, n_vars, vars, n, !identity, in->bounded ? &b : nullptr, out, tail);
 }
 
 // Right and full outer joins (Section 4.2 lists the outer joins of the library

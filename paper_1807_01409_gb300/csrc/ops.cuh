@@ -66,8 +66,10 @@ int gather_cols(tid_ctx *ctx, const int32_t *const *in, int k, const int32_t *pe
 // canonical form (rows sorted in column order; duplicates dropped if dedupe);
 // bounds of the input columns if known (else they are computed); the output
 // set records the bounds used
+// sorted_tail: the rows are already sorted by their last sorted_tail columns
+// (lexicographically, in that order), so only the leading columns are sorted
 int canonicalize(tid_ctx *ctx, const int32_t *const *cols, int k, const int8_t *vars, int64_t n,
-                 bool dedupe, const Bounds *bounds, tid_set **out);
+                 bool dedupe, const Bounds *bounds, tid_set **out, int sorted_tail = 0);
 
 // write a known row count into a set (device count and host mirror)
 int set_rows_const(tid_set *set, int64_t n);

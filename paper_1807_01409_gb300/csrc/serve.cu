@@ -7,9 +7,11 @@
 //  * each worker owns a context (stream + memory pool) and a borrowed view of
 //    the store, so waves of different workers overlap on the device;
 //  * a wave: (batch_scans) every MATCH node of the wave -> one tid_match_batch;
-//    then index requests are copied to host together (one pinned staging
-//    buffer, one synchronisation), then each plan runs the rest of its nodes
-//    (exec_plan) and is copied to host;
+//    then the index requests' lists go to host, smallest first, in chunks
+//    through two fixed pinned buffers (the copy of one chunk overlaps the host
+//    copy of the previous one) and each request finishes as soon as its rows
+//    are on the host; then each plan runs the rest of its nodes (exec_plan)
+//    and is copied to host;
 //  * estimates come from sorted value samples of the three columns.
 #include <algorithm>
 #include <chrono>
@@ -30,6 +32,7 @@ namespace {
 using namespace tid;
 
 constexpr int MAX_WORKERS = 16;
+constexpr size_t STAGE_ROWS = (size_t)1 << 24;  // rows per pinned staging buffer (64 MB)
 constexpr int64_t SAMPLE_MAX = 1 << 20;
 
 struct Request {
@@ -45,7 +48,7 @@ struct Request {
     int cols = 0;
     int8_t vars[TID_MAX_COLS] = {0};
     int64_t rows = 0;
-    std::vector<int32_t> data;
+    std::unique_ptr<int32_t[]> data;  // rows x cols, row-major (not zero-filled before it is written)
     int64_t latency_ns = 0;
 };
 
@@ -53,8 +56,8 @@ struct Worker {
     tid_ctx *ctx = nullptr;
     tid_store *st = nullptr;
     std::thread th;
-    int32_t *staging = nullptr;  // pinned host buffer for index results
-    size_t staging_rows = 0;
+    int32_t *staging[2] = {nullptr, nullptr};  // pinned host buffers for index results, STAGE_ROWS each
+    cudaEvent_t copied[2] = {nullptr, nullptr};
 };
 
 int64_t now_ns() {
@@ -180,22 +183,37 @@ int set_to_request(tid_set *set, Request *r) {
     r->cols = set->k;
     for (int c = 0; c < set->k; ++c) r->vars[c] = set->vars[c];
     r->rows = rows;
-    r->data.resize((size_t)rows * set->k);
+    r->data.reset(new (std::nothrow) int32_t[std::max<size_t>(1, (size_t)rows * set->k)]);
+    if (!r->data) return fail(TID_ERR_OOM, "host allocation of a result");
     if (rows == 0) return TID_OK;
     int64_t got = 0;
-    return tid_set_to_host(set, r->data.data(), rows, &got);
+    return tid_set_to_host(set, r->data.get(), rows, &got);
 }
 
-int grow_staging(Worker &W, size_t rows) {
-    if (rows <= W.staging_rows) return TID_OK;
-    if (W.staging) cudaFreeHost(W.staging);
-    W.staging = nullptr;
-    W.staging_rows = 0;
-    const size_t want = std::max(rows, (size_t)1 << 20) * 3 / 2;
-    void *h = nullptr;
-    TID_TRY_CUDA(cudaHostAlloc(&h, want * sizeof(int32_t), cudaHostAllocDefault), "staging buffer");
-    W.staging = (int32_t *)h;
-    W.staging_rows = want;
+// An index list (n rows on the device) into dst on the host, in chunks through
+// the worker's two pinned buffers: the copy into one buffer runs while the
+// previous chunk is copied out of the other.
+int list_to_host(Worker &W, cudaStream_t st, const int32_t *src, size_t n, int32_t *dst) {
+    size_t prev_off = 0, prev_len = 0;
+    int prev_buf = -1;
+    for (size_t off = 0, k = 0; off < n; off += STAGE_ROWS, ++k) {
+        const int b = (int)(k & 1);
+        const size_t len = std::min(STAGE_ROWS, n - off);
+        TID_TRY_CUDA(cudaMemcpyAsync(W.staging[b], src + off, len * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
+                     "index result copy");
+        TID_TRY_CUDA(cudaEventRecord(W.copied[b], st), "index result copy");
+        if (prev_buf >= 0) {
+            TID_TRY_CUDA(cudaEventSynchronize(W.copied[prev_buf]), "index result copy");
+            std::memcpy(dst + prev_off, W.staging[prev_buf], prev_len * sizeof(int32_t));
+        }
+        prev_buf = b;
+        prev_off = off;
+        prev_len = len;
+    }
+    if (prev_buf >= 0) {
+        TID_TRY_CUDA(cudaEventSynchronize(W.copied[prev_buf]), "index result copy");
+        std::memcpy(dst + prev_off, W.staging[prev_buf], prev_len * sizeof(int32_t));
+    }
     return TID_OK;
 }
 
@@ -237,10 +255,10 @@ void run_wave(tid_server *S, Worker &W, std::vector<Request *> &wave) {
             for (auto &nd : r->nodes) S->stats.scan_patterns += nd.op == TID_OP_MATCH;
     }
 
-    // 2) index requests: their lists to host through one staging buffer
+    // 2) index requests: their lists to host, smallest first, each request
+    //    finished as soon as its rows are there
     std::vector<int> idx_reqs;
     std::vector<tid_set *> idx_sets;
-    size_t total = 0;
     for (int i = 0; i < nw; ++i) {
         Request *r = wave[i];
         if (r->kind != TID_REQ_INDEX) continue;
@@ -260,34 +278,24 @@ void run_wave(tid_server *S, Worker &W, std::vector<Request *> &wave) {
         r->rows = rows;
         idx_reqs.push_back(i);
         idx_sets.push_back(set);
-        total += (size_t)rows;
     }
-    if (!idx_reqs.empty()) {
-        int rc = grow_staging(W, total);
-        size_t off = 0;
-        for (size_t q = 0; q < idx_reqs.size() && rc == TID_OK; ++q) {
-            Request *r = wave[idx_reqs[q]];
-            if (r->rows > 0) {
-                cudaError_t e = cudaMemcpyAsync(W.staging + off, idx_sets[q]->col[0], (size_t)r->rows * 4,
-                                                cudaMemcpyDeviceToHost, ctx->stream);
-                if (e != cudaSuccess) rc = fail_cuda(e, "index result copy");
-            }
-            off += (size_t)r->rows;
-        }
+    std::vector<size_t> order(idx_reqs.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return wave[idx_reqs[a]]->rows < wave[idx_reqs[b]]->rows; });
+    int copy_rc = check_ctx_error(ctx);
+    for (size_t q : order) {
+        Request *r = wave[idx_reqs[q]];
+        int rc = copy_rc;
         if (rc == TID_OK) {
-            cudaError_t e = cudaStreamSynchronize(ctx->stream);
-            if (e != cudaSuccess) rc = fail_cuda(e, "index result copy");
+            r->data.reset(new (std::nothrow) int32_t[std::max<int64_t>(1, r->rows)]);
+            rc = r->data ? TID_OK : fail(TID_ERR_OOM, "host allocation of a result");
         }
-        if (rc == TID_OK) rc = check_ctx_error(ctx);
-        off = 0;
-        for (size_t q = 0; q < idx_reqs.size(); ++q) {
-            Request *r = wave[idx_reqs[q]];
-            if (rc == TID_OK) r->data.assign(W.staging + off, W.staging + off + r->rows);
-            off += (size_t)r->rows;
-            set_free(idx_sets[q]);
-            r->status = rc;
-            finish(S, r);
-        }
+        if (rc == TID_OK) rc = list_to_host(W, ctx->stream, idx_sets[q]->col[0], (size_t)r->rows, r->data.get());
+        if (rc != TID_OK) copy_rc = rc;
+        set_free(idx_sets[q]);
+        r->status = rc;
+        finish(S, r);
     }
 
     // 3) plans: the rest of each plan, then its result to host
@@ -346,7 +354,10 @@ void destroy_workers(tid_server *S) {
     for (auto &W : S->workers) {
         if (W.st) tid_store_free(W.st);
         if (W.ctx) tid_ctx_destroy(W.ctx);
-        if (W.staging) cudaFreeHost(W.staging);
+        for (int b = 0; b < 2; ++b) {
+            if (W.staging[b]) cudaFreeHost(W.staging[b]);
+            if (W.copied[b]) cudaEventDestroy(W.copied[b]);
+        }
         W = Worker();
     }
 }
@@ -377,6 +388,16 @@ extern "C" int tid_server_create(int device, const int32_t *s, const int32_t *p,
         Worker &W = S->workers[w];
         int rc = tid_ctx_create(device, nullptr, &W.ctx);
         if (rc == TID_OK) rc = tid_load(W.ctx, s, p, o, n, TID_DEVICE, 0, &W.st);
+        for (int b = 0; b < 2 && rc == TID_OK; ++b) {
+            DeviceGuard g(device);
+            void *h = nullptr;
+            cudaError_t e = cudaHostAlloc(&h, STAGE_ROWS * sizeof(int32_t), cudaHostAllocDefault);
+            if (e == cudaSuccess) {
+                W.staging[b] = (int32_t *)h;
+                e = cudaEventCreateWithFlags(&W.copied[b], cudaEventDisableTiming);
+            }
+            if (e != cudaSuccess) rc = fail_cuda(e, "tid_server_create: staging buffers");
+        }
         if (rc != TID_OK) {
             destroy_workers(S.get());
             return rc;
@@ -466,7 +487,7 @@ extern "C" int tid_server_result(tid_server *S, int64_t id, int *status, int *co
     if (vars)
         for (int c = 0; c < r->cols; ++c) vars[c] = r->vars[c];
     if (rows) *rows = r->rows;
-    if (data) *data = r->data.data();
+    if (data) *data = r->data.get();
     if (latency_ns) *latency_ns = r->latency_ns;
     return TID_OK;
 }

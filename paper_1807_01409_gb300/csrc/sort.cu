@@ -53,18 +53,23 @@ __device__ __forceinline__ uint32_t order_key(int32_t x) { return (uint32_t)x ^ 
 // per-column min and max in sort order (flipped sign bit)
 __global__ void k_minmax(ColPtrs cols, int k, int64_t n, uint32_t *__restrict__ mn, uint32_t *__restrict__ mx) {
     uint32_t lo[TID_MAX_COLS], hi[TID_MAX_COLS];
-    for (int c = 0; c < k; ++c) {
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
         lo[c] = 0xFFFFFFFFu;
         hi[c] = 0u;
     }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        for (int c = 0; c < k; ++c) {
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c) {
+            if (c >= k) continue;
             const uint32_t v = order_key(cols.c[c][i]);
             lo[c] = min(lo[c], v);
             hi[c] = max(hi[c], v);
         }
     }
-    for (int c = 0; c < k; ++c) {
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        if (c >= k) continue;
         uint32_t a = lo[c], b = hi[c];
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
@@ -78,31 +83,42 @@ __global__ void k_minmax(ColPtrs cols, int k, int64_t n, uint32_t *__restrict__ 
     }
 }
 
-// Histograms of the 8-bit digits 0 .. ndig-1 of keys, accumulated in shared
-// memory (one add per group of lanes holding the same digit, grouped with
-// match_any; a whole warp on one digit -- the common case for high digits --
-// is one add) and added to hist[p * 256 + b].  Called by whole warps.
+// Histograms of the 8-bit digits p = 0 .. ndig-1 of keys (digit p = bits
+// shift0 + 8p ..), accumulated with plain shared-memory atomics in
+// HIST_COPIES copies (warp w adds to copy w % HIST_COPIES, so warps seldom
+// meet on one counter; a whole warp on one digit -- the common case for high
+// digits -- is one add) and added to hist[p * 256 + b].  Called by whole warps.
 constexpr int RS_MAX_DIGITS = 8;
+constexpr int HIST_COPIES = 4;
 
 template <typename K>
-__device__ __forceinline__ void hist_add(uint32_t *s_hist, K key, bool valid, int ndig) {
+__device__ __forceinline__ void hist_add(uint32_t *s_hist, K key, bool valid, int shift0, int ndig) {
     const unsigned lane = threadIdx.x & 31;
+    uint32_t *h = s_hist + ((threadIdx.x >> 5) % HIST_COPIES) * (RS_MAX_DIGITS * RS_BINS);
     for (int p = 0; p < ndig; ++p) {
-        const unsigned d = valid ? (unsigned)(key >> (8 * p)) & 0xFFu : 0x100u;
+        const unsigned d = valid ? (unsigned)(key >> (shift0 + 8 * p)) & 0xFFu : 0x100u;
         const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
         if (__all_sync(0xffffffffu, d == d0)) {
-            if (lane == 0 && d0 < 0x100u) atomicAdd(&s_hist[p * RS_BINS + d0], 32u);
-            continue;
+            if (lane == 0 && d0 < 0x100u) atomicAdd(&h[p * RS_BINS + d0], 32u);
+        } else if (valid) {
+            atomicAdd(&h[p * RS_BINS + d], 1u);
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&s_hist[p * RS_BINS + d], (uint32_t)__popc(peers));
     }
+}
+
+__device__ __forceinline__ void hist_clear(uint32_t *s_hist) {
+    for (int i = threadIdx.x; i < HIST_COPIES * RS_MAX_DIGITS * RS_BINS; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
 }
 
 __device__ __forceinline__ void hist_flush(uint32_t *s_hist, int ndig, uint32_t *__restrict__ hist) {
     __syncthreads();
-    for (int i = threadIdx.x; i < ndig * RS_BINS; i += blockDim.x)
-        if (s_hist[i]) atomicAdd(hist + i, s_hist[i]);
+    for (int i = threadIdx.x; i < ndig * RS_BINS; i += blockDim.x) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int c = 0; c < HIST_COPIES; ++c) v += s_hist[c * RS_MAX_DIGITS * RS_BINS + i];
+        if (v) atomicAdd(hist + i, v);
+    }
 }
 
 // keys[i] = order_key(col[src(i)]) - base, vals[i] = src(i), src = perm ? perm[i] : i;
@@ -110,9 +126,8 @@ __device__ __forceinline__ void hist_flush(uint32_t *s_hist, int ndig, uint32_t 
 __global__ void __launch_bounds__(256) k_prep(const int32_t *__restrict__ col, const int32_t *__restrict__ perm,
                                               int64_t n, uint32_t base, uint32_t *__restrict__ keys,
                                               int32_t *__restrict__ vals, int ndig, uint32_t *__restrict__ hist) {
-    __shared__ uint32_t s_hist[4 * RS_BINS];
-    for (int i = threadIdx.x; i < ndig * RS_BINS; i += blockDim.x) s_hist[i] = 0;
-    __syncthreads();
+    __shared__ uint32_t s_hist[HIST_COPIES * RS_MAX_DIGITS * RS_BINS];
+    hist_clear(s_hist);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n_iter = ceil_div(n, stride) * stride;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_iter; i += stride) {
@@ -123,7 +138,7 @@ __global__ void __launch_bounds__(256) k_prep(const int32_t *__restrict__ col, c
             keys[i] = key;
             vals[i] = s;
         }
-        hist_add(s_hist, key, i < n, ndig);
+        hist_add(s_hist, key, i < n, 0, ndig);
     }
     hist_flush(s_hist, ndig, hist);
 }
@@ -327,20 +342,20 @@ k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__rest
 // order_key(col_c) - min_c in bits [shift_c, shift_c + bits_c)
 template <typename K>
 __global__ void __launch_bounds__(256) k_pack(ColPtrs cols, int k, int64_t n, PackSpec ps, K *__restrict__ keys,
-                                              int ndig, uint32_t *__restrict__ hist) {
-    __shared__ uint32_t s_hist[RS_MAX_DIGITS * RS_BINS];
-    for (int i = threadIdx.x; i < ndig * RS_BINS; i += blockDim.x) s_hist[i] = 0;
-    __syncthreads();
+                                              int shift0, int ndig, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_hist[HIST_COPIES * RS_MAX_DIGITS * RS_BINS];
+    hist_clear(s_hist);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t n_iter = ceil_div(n, stride) * stride;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_iter; i += stride) {
         K key = 0;
         if (i < n) {
-            for (int c = 0; c < k; ++c)  // a constant column (mask 0) has no field
-                if (ps.mask[c]) key |= (K)(order_key(cols.c[c][i]) - ps.min[c]) << ps.shift[c];
+#pragma unroll
+            for (int c = 0; c < TID_MAX_COLS; ++c)  // a constant column (mask 0) has no field
+                if (c < k && ps.mask[c]) key |= (K)(order_key(cols.c[c][i]) - ps.min[c]) << ps.shift[c];
             keys[i] = key;
         }
-        hist_add(s_hist, key, i < n, ndig);
+        hist_add(s_hist, key, i < n, shift0, ndig);
     }
     hist_flush(s_hist, ndig, hist);
 }
@@ -350,7 +365,9 @@ template <typename K>
 __global__ void k_unpack(const K *__restrict__ keys, int k, int64_t n, PackSpec ps, MutColPtrs out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const K key = keys[i];
-        for (int c = 0; c < k; ++c) {
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c) {
+            if (c >= k) continue;
             const uint32_t f = ps.mask[c] ? (uint32_t)((key >> ps.shift[c]) & ps.mask[c]) : 0u;
             out.c[c][i] = (int32_t)((f + ps.min[c]) ^ 0x80000000u);
         }
@@ -377,8 +394,9 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_canonical(ColPtrs cols,
         K key = ~(K)0;
         if (i < n) {
             key = 0;
-            for (int c = 0; c < k; ++c)
-                if (ps.mask[c]) key |= (K)(order_key(cols.c[c][i]) - ps.min[c]) << ps.shift[c];
+#pragma unroll
+            for (int c = 0; c < TID_MAX_COLS; ++c)
+                if (c < k && ps.mask[c]) key |= (K)(order_key(cols.c[c][i]) - ps.min[c]) << ps.shift[c];
         }
         sk[i] = key;
     }
@@ -425,7 +443,9 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_canonical(ColPtrs cols,
     for (int q = 0; q < PER; ++q) {
         if (!keep[q]) continue;
         const K key = sk[b + q];
-        for (int c = 0; c < k; ++c) {
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c) {
+            if (c >= k) continue;
             const uint32_t f = ps.mask[c] ? (uint32_t)((key >> ps.shift[c]) & ps.mask[c]) : 0u;
             out.c[c][pos] = (int32_t)((f + ps.min[c]) ^ 0x80000000u);
         }
@@ -440,7 +460,9 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_canonical(ColPtrs cols,
 __global__ void k_gather(ColPtrs in, int k, const int32_t *__restrict__ perm, int64_t n, MutColPtrs out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = perm[i];
-        for (int c = 0; c < k; ++c) out.c[c][i] = in.c[c][s];
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < k) out.c[c][i] = in.c[c][s];
     }
 }
 
@@ -509,14 +531,14 @@ static int onesweep_lookback(tid_ctx *ctx, unsigned tiles, Lookback *lb) {
 // every digit (k_digit_starts); keys (and values) ping-pong between a and b;
 // on return a holds the sorted keys.
 template <typename K, bool HAS_VAL>
-static int onesweep_passes(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *&pb, int64_t n, int passes,
-                           const uint32_t *hist) {
+static int onesweep_passes(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *&pb, int64_t n, int shift0,
+                           int passes, const uint32_t *hist) {
     const unsigned tiles = (unsigned)ceil_div(n, RS_TILE);
     for (int p = 0; p < passes; ++p) {
         Lookback lb{};
         TID_TRY(onesweep_lookback(ctx, tiles, &lb));
-        k_onesweep<K, HAS_VAL><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, pa, kb, pb, n, 8 * p, hist + p * RS_BINS,
-                                                                     lb);
+        k_onesweep<K, HAS_VAL><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, pa, kb, pb, n, shift0 + 8 * p,
+                                                                     hist + p * RS_BINS, lb);
         TID_TRY(launch_check("k_onesweep"));
         std::swap(ka, kb);
         if (HAS_VAL) std::swap(pa, pb);
@@ -524,15 +546,18 @@ static int onesweep_passes(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *
     return TID_OK;
 }
 
-// Stable LSD sort of a row permutation by key columns, given their ranges.
+// Stable LSD sort of a row permutation by key columns, given their ranges.  The
+// rows are already in order of the last `sorted_tail` key columns (taken in
+// their order), so those passes are skipped: stable passes over the leading
+// columns keep them in order within equal leading values.
 static int sort_perm_ranges(tid_ctx *ctx, const int32_t *const *keys, int nk, int64_t n, const uint32_t *hmin,
-                            const uint32_t *hmax, int32_t *perm) {
+                            const uint32_t *hmax, int32_t *perm, int sorted_tail = 0) {
     cudaStream_t st = ctx->stream;
     Scratch s(ctx);
     uint32_t *ka = nullptr, *kb = nullptr, *hist = nullptr;
     int32_t *pa = nullptr, *pb = nullptr;
     bool have_perm = false;  // pa holds the current permutation
-    for (int c = nk - 1; c >= 0; --c) {
+    for (int c = nk - 1 - sorted_tail; c >= 0; --c) {
         const int bits = range_bits(hmin[c], hmax[c]);
         if (bits == 0) continue;  // constant column: order unchanged
         const int passes = (bits + 7) / 8;
@@ -549,7 +574,7 @@ static int sort_perm_ranges(tid_ctx *ctx, const int32_t *const *keys, int nk, in
         TID_TRY(launch_check("k_prep"));
         k_digit_starts<<<1, RS_BINS, 0, st>>>(hist, passes);
         TID_TRY(launch_check("k_digit_starts"));
-        TID_TRY((onesweep_passes<uint32_t, true>(ctx, ka, kb, pa, pb, n, passes, hist)));
+        TID_TRY((onesweep_passes<uint32_t, true>(ctx, ka, kb, pa, pb, n, 0, passes, hist)));
         have_perm = true;
     }
     if (have_perm) {
@@ -571,9 +596,12 @@ int sort_perm(tid_ctx *ctx, const int32_t *const *keys, int nk, int64_t n, int32
 
 // Canonical form by sorting packed keys (all fields fit K): pack, keys-only
 // digit passes over the occupied bits, then unpack (with distinct rows kept).
+// The rows are already ordered by the low `sorted_bits` bits of their keys
+// (the fields of trailing columns they are sorted by): the digit passes start
+// above them.
 template <typename K>
 static int canonical_packed(tid_ctx *ctx, const int32_t *const *cols, int k, int64_t n, bool dedupe,
-                            const PackSpec &ps, int total_bits, tid_set *set) {
+                            const PackSpec &ps, int total_bits, int sorted_bits, tid_set *set) {
     cudaStream_t st = ctx->stream;
     if (n <= SMALL_N) {
         ColPtrs cp{};
@@ -592,18 +620,18 @@ static int canonical_packed(tid_ctx *ctx, const int32_t *const *cols, int k, int
     K *ka = nullptr, *kb = nullptr;
     uint32_t *hist = nullptr;
     int32_t *none_a = nullptr, *none_b = nullptr;
-    const int passes = (total_bits + 7) / 8;
+    const int passes = (total_bits - sorted_bits + 7) / 8;
     TID_TRY(s.get(&ka, n));
     TID_TRY(s.get(&kb, n));
     TID_TRY(s.get(&hist, (size_t)RS_BINS * RS_MAX_DIGITS));
-    TID_TRY_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * RS_BINS * passes, st), "memset histogram");
+    TID_TRY_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * RS_BINS * RS_MAX_DIGITS, st), "memset histogram");
     ColPtrs cp{};
     for (int c = 0; c < k; ++c) cp.c[c] = cols[c];
-    k_pack<K><<<grid_for(n, 256, 8), 256, 0, st>>>(cp, k, n, ps, ka, passes, hist);
+    k_pack<K><<<grid_for(n, 256, 8), 256, 0, st>>>(cp, k, n, ps, ka, sorted_bits, passes, hist);
     TID_TRY(launch_check("k_pack"));
     k_digit_starts<<<1, RS_BINS, 0, st>>>(hist, passes);
     TID_TRY(launch_check("k_digit_starts"));
-    TID_TRY((onesweep_passes<K, false>(ctx, ka, kb, none_a, none_b, n, passes, hist)));
+    TID_TRY((onesweep_passes<K, false>(ctx, ka, kb, none_a, none_b, n, sorted_bits, passes, hist)));
     if (dedupe) return compact_unique_packed(ctx, ka, sizeof(K) == 8, k, n, ps, set);
     MutColPtrs op{};
     for (int c = 0; c < k; ++c) op.c[c] = set->col[c];
@@ -626,7 +654,7 @@ int gather_cols(tid_ctx *ctx, const int32_t *const *in, int k, const int32_t *pe
 }
 
 int canonicalize(tid_ctx *ctx, const int32_t *const *cols, int k, const int8_t *vars, int64_t n, bool dedupe,
-                 const Bounds *bounds, tid_set **out) {
+                 const Bounds *bounds, tid_set **out, int sorted_tail) {
     *out = nullptr;
     tid_set *set = nullptr;
     TID_TRY(set_alloc(ctx, k, vars, n, &set));
@@ -661,14 +689,17 @@ int canonicalize(tid_ctx *ctx, const int32_t *const *cols, int k, const int8_t *
                 total += bits;
             }
         }
+        // the trailing columns the rows are sorted by occupy the key bits below
+        // the field of the last column before them
+        const int sorted_bits = sorted_tail <= 0 ? 0 : (sorted_tail >= k ? total : (int)ps.shift[k - sorted_tail - 1]);
         if (rc == TID_OK && total <= 32) {
-            rc = canonical_packed<uint32_t>(ctx, cols, k, n, dedupe, ps, total, set);
+            rc = canonical_packed<uint32_t>(ctx, cols, k, n, dedupe, ps, total, sorted_bits, set);
         } else if (rc == TID_OK && total <= 64) {
-            rc = canonical_packed<unsigned long long>(ctx, cols, k, n, dedupe, ps, total, set);
+            rc = canonical_packed<unsigned long long>(ctx, cols, k, n, dedupe, ps, total, sorted_bits, set);
         } else if (rc == TID_OK) {
             int32_t *perm = nullptr;
             rc = dev_alloc(ctx, (void **)&perm, (size_t)n * 4);
-            if (rc == TID_OK) rc = sort_perm_ranges(ctx, cols, k, n, hmin, hmax, perm);
+            if (rc == TID_OK) rc = sort_perm_ranges(ctx, cols, k, n, hmin, hmax, perm, sorted_tail);
             if (rc == TID_OK) {
                 if (dedupe) {
                     rc = compact_unique(ctx, cols, k, perm, n, set);

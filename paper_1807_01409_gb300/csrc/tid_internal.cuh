@@ -108,6 +108,8 @@ struct tid_ctx {
     std::vector<std::pair<int, int>> free_slots;
     std::vector<tid::PendingSlot> pending;
     std::mutex mu;
+    // the batched search's last plan on this context (tid_batch_tuning)
+    int batch_shape = -1, batch_keys = 0, batch_subs = 0;
     // testing aid (tid_ctx_inject_alloc_failure): allocations left before they fail
     std::atomic<int64_t> fail_after{-1};
     std::atomic<int64_t> allocs{0};

@@ -101,6 +101,7 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
         "TID_ERR_TIMEOUT": tb.TID_ERR_TIMEOUT, "TID_ERR_CUDA": tb.TID_ERR_CUDA,
         "TID_HOST": tb.TID_HOST, "TID_DEVICE": tb.TID_DEVICE, "TID_MAX_COLS": tb.TID_MAX_COLS,
         "TID_MAX_MULTI": tb.TID_MAX_MULTI, "TID_BATCH_KEYS": tb.TID_BATCH_KEYS,
+        **{f"TID_BATCH_{v.upper()}": k for k, v in tb.BATCH_SHAPES.items()},
         "TID_REQ_INDEX": tb.TID_REQ_INDEX, "TID_REQ_PLAN": tb.TID_REQ_PLAN,
         "TID_JOIN_AUTO": tb.JOIN["auto"], "TID_JOIN_SORT_MERGE": tb.JOIN["sort_merge"],
         "TID_JOIN_HASH": tb.JOIN["hash"], "TID_JOIN_LEFT": tb.TID_JOIN_LEFT,

@@ -139,3 +139,24 @@ def test_concurrent_submitters(store, requests, orc):
         for (kind, x), (gv, gr) in list(zip(chunks[j], results[j]))[::5]:
             wv, wr = _want(orc, st, kind, x)
             assert gv == wv and np.array_equal(gr, wr)
+
+
+def test_large_index_results_in_chunks(orc):
+    """Index results longer than one pinned staging buffer (16M rows) reach the
+    host in several chunks, in a wave with small requests, each equal to the
+    oracle's list."""
+    rng = np.random.default_rng(77)
+    n = 40_000_003
+    S = rng.integers(1, 50_000, n, dtype=np.int32)
+    P = rng.integers(1, 3, n, dtype=np.int32)  # two predicates: (?, 1, ?) holds ~20M rows
+    O = rng.integers(1, 1000, n, dtype=np.int32)
+    cols = tuple(torch.from_numpy(c).cuda() for c in (S, P, O))
+    torch.cuda.synchronize()
+    keys = [(0, 1, 0), (int(S[5]), 0, 0), (0, 2, int(O[7])), (0, 2, 0), (int(S[9]), int(P[9]), 0)]
+    with tb.Server(*cols, workers=1, max_wave=64) as srv:
+        got = _run_all(srv, [("index", k) for k in keys])
+    for k, (gv, gr) in zip(keys, got):
+        want = orc.match(S, P, O, k)
+        assert gv == (-1,) and gr.shape == (want.shape[0], 1), k
+        assert np.array_equal(gr[:, 0], want), k
+    assert max(g[1].shape[0] for g in got) > 16_000_000
