@@ -237,11 +237,16 @@ __device__ __forceinline__ void merge_bounds(uint32_t *mm, int k_out, const uint
 
 // ---- single-pass compaction (small inputs) ----------------------------------------
 
+// The tile's kept rows are staged in shared memory at their place in the tile
+// (the block's own scan gives it) while warp 0 looks back for the tile's
+// offset, so the value reads overlap that wait; the tile is then written with
+// coalesced stores.  Dynamic shared memory: k_out x CP_TILE int32.
 template <class Row>
 __global__ void __launch_bounds__(CP_THREADS)
 k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__restrict__ d_rows,
           int64_t *__restrict__ h_rows, Lookback lb, uint32_t *__restrict__ mm) {
-    __shared__ unsigned s_tile;
+    extern __shared__ int32_t s_vals[];  // column c of staged row i at s_vals[c * CP_TILE + i]
+    __shared__ unsigned s_tile, s_total;
     __shared__ unsigned s_off[CP_ITEMS * CP_WARPS];
     __shared__ long long s_prefix;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -267,8 +272,7 @@ k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__re
         if (lane == 0) s_off[j * CP_WARPS + warp] = __popc(b);
     }
     __syncthreads();
-    if (warp == 0) {
-        // 64 (item, warp) counts in order; each lane scans two consecutive entries
+    if (warp == 0) {  // 64 (item, warp) counts in order; each lane scans two consecutive entries
         const unsigned a0 = s_off[2 * lane], a1 = s_off[2 * lane + 1];
         unsigned x = a0 + a1;
 #pragma unroll
@@ -279,7 +283,23 @@ k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__re
         const unsigned ex = x - a0 - a1;
         s_off[2 * lane] = ex;
         s_off[2 * lane + 1] = ex + a0;
-        const unsigned total = __shfl_sync(0xffffffffu, x, 31);
+        if (lane == 31) s_total = x;
+    }
+    __syncthreads();
+    const unsigned total = s_total;
+    auto stage = [&]() {  // this thread's kept rows to their place in the tile
+#pragma unroll
+        for (int j = 0; j < CP_ITEMS; ++j) {
+            if (!((keep >> j) & 1u)) continue;
+            int32_t v[TID_MAX_COLS];
+            row.values(base + j * CP_THREADS + threadIdx.x, v);
+            const unsigned at = s_off[j * CP_WARPS + warp] + wpre[j];
+#pragma unroll
+            for (int c = 0; c < TID_MAX_COLS; ++c)
+                if (c < k_out) s_vals[c * CP_TILE + at] = v[c];
+        }
+    };
+    if (warp == 0) {
         const long long excl = lb_exclusive_prefix(lb, tile, total);
         if (lane == 0) {
             s_prefix = excl;
@@ -289,6 +309,7 @@ k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__re
             }
         }
     }
+    stage();  // warps 1.. stage while warp 0 waits for the tile's offset
     __syncthreads();
     const long long prefix = s_prefix;
     if (prefix < 0) return;
@@ -298,24 +319,131 @@ k_compact(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__re
         lo[c] = 0xFFFFFFFFu;
         hi[c] = 0u;
     }
-#pragma unroll
-    for (int j = 0; j < CP_ITEMS; ++j) {
-        if (!((keep >> j) & 1u)) continue;
-        const int64_t r = base + j * CP_THREADS + threadIdx.x;
-        int32_t v[TID_MAX_COLS];
-        row.values(r, v);  // the kept row's values (its test read them from L1/L2 at most)
-        const long long pos = prefix + s_off[j * CP_WARPS + warp] + wpre[j];
+    for (unsigned i = threadIdx.x; i < total; i += CP_THREADS) {  // coalesced: row prefix + i
+        const long long pos = prefix + i;
 #pragma unroll
         for (int c = 0; c < TID_MAX_COLS; ++c) {
             if (c < k_out) {
-                if (pos < cap) out.col[c][pos] = v[c];
-                const uint32_t u = (uint32_t)v[c] ^ 0x80000000u;
+                const int32_t v = s_vals[c * CP_TILE + i];
+                if (pos < cap) out.col[c][pos] = v;
+                const uint32_t u = (uint32_t)v ^ 0x80000000u;
                 lo[c] = min(lo[c], u);
                 hi[c] = max(hi[c], u);
             }
         }
     }
     if (mm) merge_bounds(mm, k_out, lo, hi);  // column bounds of the kept rows
+}
+
+// ---- two-kernel compaction (dense keeps over long inputs) -------------------------
+//
+// k_tile_counts: every CTA tests its 2048-row tile and writes the tile's count;
+// the counts are scanned (k_scan_u32); k_tile_write tests the tile again, ranks
+// its kept rows (ballots and a block scan), stages their values in shared memory
+// and writes them at the tile's offset with coalesced stores.  No CTA waits for
+// another; the test columns are read twice.
+
+template <class Row>
+__global__ void __launch_bounds__(CP_THREADS) k_tile_counts(Row row, int64_t n, uint32_t *__restrict__ counts) {
+    __shared__ unsigned s_w[CP_WARPS];
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * CP_TILE;
+    bool kp[CP_ITEMS];
+#pragma unroll
+    for (int j = 0; j < CP_ITEMS; ++j) {
+        const int64_t r = base + j * CP_THREADS + threadIdx.x;
+        kp[j] = row.keep(r < n ? r : n - 1) && r < n;
+    }
+    unsigned c = 0;
+#pragma unroll
+    for (int j = 0; j < CP_ITEMS; ++j) c += __popc(__ballot_sync(0xffffffffu, kp[j]));
+    if (lane == 0) s_w[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < CP_WARPS; ++w) t += s_w[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+template <class Row>
+__global__ void __launch_bounds__(CP_THREADS)
+k_tile_write(Row row, int64_t n, int k_out, OutCols out, int64_t cap, const uint32_t *__restrict__ offs,
+             const uint32_t *__restrict__ counts, unsigned tiles, int64_t *__restrict__ d_rows,
+             int64_t *__restrict__ h_rows, uint32_t *__restrict__ mm) {
+    extern __shared__ int32_t s_vals[];  // column c of staged row i at s_vals[c * CP_TILE + i]
+    __shared__ unsigned s_off[CP_ITEMS * CP_WARPS];
+    __shared__ unsigned s_total;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * CP_TILE;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // the result's row count
+        const int64_t total = (int64_t)offs[tiles - 1] + counts[tiles - 1];
+        *d_rows = total;
+        *h_rows = total;
+    }
+    bool kp[CP_ITEMS];
+#pragma unroll
+    for (int j = 0; j < CP_ITEMS; ++j) {
+        const int64_t r = base + j * CP_THREADS + threadIdx.x;
+        kp[j] = row.keep(r < n ? r : n - 1) && r < n;
+    }
+    unsigned keep = 0, wpre[CP_ITEMS];
+#pragma unroll
+    for (int j = 0; j < CP_ITEMS; ++j) {
+        keep |= (unsigned)kp[j] << j;
+        const unsigned b = __ballot_sync(0xffffffffu, kp[j]);
+        wpre[j] = __popc(b & lt);
+        if (lane == 0) s_off[j * CP_WARPS + warp] = __popc(b);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned a0 = s_off[2 * lane], a1 = s_off[2 * lane + 1];
+        unsigned x = a0 + a1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+            if ((int)lane >= d) x += y;
+        }
+        const unsigned ex = x - a0 - a1;
+        s_off[2 * lane] = ex;
+        s_off[2 * lane + 1] = ex + a0;
+        if (lane == 31) s_total = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < CP_ITEMS; ++j) {
+        if (!((keep >> j) & 1u)) continue;
+        int32_t v[TID_MAX_COLS];
+        row.values(base + j * CP_THREADS + threadIdx.x, v);
+        const unsigned at = s_off[j * CP_WARPS + warp] + wpre[j];
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c)
+            if (c < k_out) s_vals[c * CP_TILE + at] = v[c];
+    }
+    __syncthreads();
+    const unsigned total = s_total;
+    const long long o0 = offs[blockIdx.x];
+    uint32_t lo[TID_MAX_COLS], hi[TID_MAX_COLS];
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c) {
+        lo[c] = 0xFFFFFFFFu;
+        hi[c] = 0u;
+    }
+    for (unsigned i = threadIdx.x; i < total; i += CP_THREADS) {
+        const long long pos = o0 + i;
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c) {
+            if (c < k_out) {
+                const int32_t v = s_vals[c * CP_TILE + i];
+                if (pos < cap) out.col[c][pos] = v;
+                const uint32_t u = (uint32_t)v ^ 0x80000000u;
+                lo[c] = min(lo[c], u);
+                hi[c] = max(hi[c], u);
+            }
+        }
+    }
+    if (mm) merge_bounds(mm, k_out, lo, hi);
 }
 
 // ---- bitmap compaction (large inputs): K1's structure for rows --------------------
@@ -523,25 +651,62 @@ int bitmap_grid(unsigned *grid) {
     return TID_OK;
 }
 
-// The single-pass kernel reads a kept row's values right after its test, from
-// L1/L2; the bitmap kernel's expansion reads them after the grid barrier,
-// from DRAM once more.  Dense keeps (filters, distinct rows) and random
-// gathers (bind) therefore stay on the single-pass kernel; the bitmap kernel
-// serves sparse keeps over long inputs (the keyed store pass), where the
-// single pass's chain of tiles waiting on their predecessors dominates.
+// Which kernel compacts a long input.  Single pass: a tile's offset comes from
+// the decoupled look-back, and profiles show tiles waiting there for their
+// predecessors far longer than their own work takes; it serves short inputs
+// and bind with tests (its tests are random gathers: two kernels would gather
+// them twice, and measured no faster).  Two kernels (filters, distinct rows):
+// the test columns are read twice and no CTA waits for another.  Bitmap
+// (sparse keeps over the store: the keyed pass): one cooperative launch, the
+// kept rows' values read once after the grid barrier.
+enum CompactMode { CP_SINGLE, CP_TWO, CP_BITMAP };
+
 template <class Row>
 int launch_compact(tid_ctx *ctx, const Row &row, int64_t n, int k_out, const OutCols &out, int64_t cap,
-                   int64_t *d_rows, int64_t *h_rows_dev, uint32_t *mm = nullptr, bool bitmap = false) {
+                   int64_t *d_rows, int64_t *h_rows_dev, uint32_t *mm = nullptr, CompactMode mode = CP_TWO) {
     if (n == 0) {
         TID_TRY_CUDA(cudaMemsetAsync(d_rows, 0, sizeof(int64_t), ctx->stream), "memset rows");
         TID_TRY_CUDA(cudaMemsetAsync(h_rows_dev, 0, sizeof(int64_t), ctx->stream), "memset rows");
         return TID_OK;
     }
-    if (n < BC_MIN_ROWS || !bitmap) {
+    if (n >= BC_MIN_ROWS && mode == CP_TWO) {
+        static bool opted = false;
+        if (!opted) {
+            TID_TRY_CUDA(cudaFuncSetAttribute(k_tile_write<Row>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(sizeof(int32_t) * TID_MAX_COLS * CP_TILE)),
+                         "k_tile_write smem");
+            opted = true;
+        }
+        const unsigned tiles = (unsigned)ceil_div(n, CP_TILE);
+        void *blk = nullptr;
+        TID_TRY(dev_alloc(ctx, &blk, sizeof(uint32_t) * 2 * (size_t)tiles + 256));
+        uint32_t *counts = (uint32_t *)blk, *offs = counts + tiles;
+        int rc = TID_OK;
+        k_tile_counts<Row><<<tiles, CP_THREADS, 0, ctx->stream>>>(row, n, counts);
+        rc = launch_check("k_tile_counts");
+        if (rc == TID_OK) rc = scan_exclusive_u32(ctx, counts, offs, tiles, nullptr);
+        if (rc == TID_OK) {
+            const size_t smem = sizeof(int32_t) * (size_t)std::max(1, k_out) * CP_TILE;
+            k_tile_write<Row><<<tiles, CP_THREADS, smem, ctx->stream>>>(row, n, k_out, out, cap, offs, counts, tiles,
+                                                                        d_rows, h_rows_dev, mm);
+            rc = launch_check("k_tile_write");
+        }
+        dev_free(ctx, blk);
+        return rc;
+    }
+    if (n < BC_MIN_ROWS || mode == CP_SINGLE) {
+        static bool opted = false;  // staging of up to TID_MAX_COLS columns of a tile
+        if (!opted) {
+            TID_TRY_CUDA(cudaFuncSetAttribute(k_compact<Row>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(sizeof(int32_t) * TID_MAX_COLS * CP_TILE)),
+                         "k_compact smem");
+            opted = true;
+        }
         const unsigned tiles = (unsigned)ceil_div(n, CP_TILE);
         Lookback lb{};
         TID_TRY(lookback_scratch(ctx, tiles, &lb));
-        k_compact<Row><<<tiles, CP_THREADS, 0, ctx->stream>>>(row, n, k_out, out, cap, d_rows, h_rows_dev, lb, mm);
+        const size_t smem = sizeof(int32_t) * (size_t)std::max(1, k_out) * CP_TILE;
+        k_compact<Row><<<tiles, CP_THREADS, smem, ctx->stream>>>(row, n, k_out, out, cap, d_rows, h_rows_dev, lb, mm);
         return launch_check("k_compact");
     }
     unsigned grid = 0;
@@ -614,17 +779,20 @@ __global__ void __launch_bounds__(256) k_bind_gather(BindRow row, int64_t n, Out
 
 constexpr int SC_THREADS = 256, SC_ITEMS = 16, SC_TILE = SC_THREADS * SC_ITEMS;
 
+// Exclusive scan of one 4096-item tile; the tile's first output is `prefix`
+// (from offs[tile] when offs is given, else by decoupled look-back -- used for a
+// single tile, where nothing waits).  total_out: the sum of all items.
 __global__ void __launch_bounds__(SC_THREADS)
 k_scan_u32(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
-           unsigned long long *__restrict__ total_out, Lookback lb) {
+           unsigned long long *__restrict__ total_out, Lookback lb, const uint32_t *__restrict__ offs) {
     __shared__ unsigned s_tile;
     __shared__ uint32_t s_w[SC_THREADS / 32];
     __shared__ long long s_prefix;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = lb_ticket(lb);
+    if (threadIdx.x == 0) s_tile = offs ? blockIdx.x : lb_ticket(lb);
     __syncthreads();
     const unsigned tile = s_tile;
-    if (tile >= lb.num_tiles) return;
+    if (!offs && tile >= lb.num_tiles) return;
     // blocked: thread t owns items base + t*16 .. +15
     const int64_t base = (int64_t)tile * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
     uint32_t v[SC_ITEMS];
@@ -652,10 +820,14 @@ k_scan_u32(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t 
         }
         if (lane < SC_THREADS / 32) s_w[lane] = y - w;
         const uint32_t total = __shfl_sync(0xffffffffu, y, 31);
-        const long long excl = lb_exclusive_prefix(lb, tile, total);
-        if (lane == 0) {
-            s_prefix = excl;
-            if (tile == lb.num_tiles - 1 && excl >= 0 && total_out) *total_out = excl + total;
+        if (offs) {
+            if (lane == 0) s_prefix = offs[tile];
+        } else {
+            const long long excl = lb_exclusive_prefix(lb, tile, total);
+            if (lane == 0) {
+                s_prefix = excl;
+                if (tile == lb.num_tiles - 1 && excl >= 0 && total_out) *total_out = excl + total;
+            }
         }
     }
     __syncthreads();
@@ -668,6 +840,29 @@ k_scan_u32(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t 
     }
 }
 
+// sums[t] = sum of the items of tile t (SC_TILE items)
+__global__ void __launch_bounds__(SC_THREADS) k_tile_sums(const uint32_t *__restrict__ in, int64_t n,
+                                                          uint32_t *__restrict__ sums) {
+    __shared__ uint32_t s_w[SC_THREADS / 32];
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * SC_TILE;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; ++i) {  // striped: coalesced
+        const int64_t j = base + i * SC_THREADS + threadIdx.x;
+        sum += j < n ? in[j] : 0u;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    if (lane == 0) s_w[warp] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < SC_THREADS / 32; ++w) t += s_w[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
 }  // namespace
 
 int scan_exclusive_u32(tid_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
@@ -677,10 +872,26 @@ int scan_exclusive_u32(tid_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t 
         return TID_OK;
     }
     const unsigned tiles = (unsigned)ceil_div(n, SC_TILE);
-    Lookback lb{};
-    TID_TRY(lookback_scratch(ctx, tiles, &lb));
-    k_scan_u32<<<tiles, SC_THREADS, 0, ctx->stream>>>(in, out, n, total_dev, lb);
-    return launch_check("k_scan_u32");
+    if (tiles == 1) {  // one tile: nothing to wait for
+        Lookback lb{};
+        TID_TRY(lookback_scratch(ctx, 1, &lb));
+        k_scan_u32<<<1, SC_THREADS, 0, ctx->stream>>>(in, out, n, total_dev, lb, nullptr);
+        return launch_check("k_scan_u32");
+    }
+    // reduce, scan the tile sums (recursively), scan each tile from its offset:
+    // no tile waits for another
+    uint32_t *sums = nullptr;
+    TID_TRY(dev_alloc(ctx, (void **)&sums, sizeof(uint32_t) * 2 * (size_t)tiles + 256));
+    uint32_t *offs = sums + tiles;
+    k_tile_sums<<<tiles, SC_THREADS, 0, ctx->stream>>>(in, n, sums);
+    int rc = launch_check("k_tile_sums");
+    if (rc == TID_OK) rc = scan_exclusive_u32(ctx, sums, offs, tiles, total_dev);
+    if (rc == TID_OK) {
+        k_scan_u32<<<tiles, SC_THREADS, 0, ctx->stream>>>(in, out, n, nullptr, Lookback{}, offs);
+        rc = launch_check("k_scan_u32");
+    }
+    dev_free(ctx, sums);
+    return rc;
 }
 
 int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, const int32_t *idx, int64_t n,
@@ -717,7 +928,7 @@ int compact_bind(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, cons
         k_bind_gather<<<grid_for(n, 256, 8), 256, 0, ctx->stream>>>(r, n, oc, mm, out->d_rows, out->slot.dev);
         return launch_check("k_bind_gather");
     }
-    return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev, mm);
+    return launch_compact(ctx, r, n, out->k, oc, out->cap, out->d_rows, out->slot.dev, mm, CP_SINGLE);
 }
 
 int compact_semijoin(tid_ctx *ctx, const tid_store *st, int fixed_slot, int32_t fixed_val, int key_slot,
@@ -739,7 +950,7 @@ int compact_semijoin(tid_ctx *ctx, const tid_store *st, int fixed_slot, int32_t 
     }
     OutCols oc{};
     for (int c = 0; c < out->k; ++c) oc.col[c] = out->col[c];
-    return launch_compact(ctx, r, st->n, out->k, oc, out->cap, out->d_rows, out->slot.dev, nullptr, true);
+    return launch_compact(ctx, r, st->n, out->k, oc, out->cap, out->d_rows, out->slot.dev, nullptr, CP_BITMAP);
 }
 
 int compact_filter(tid_ctx *ctx, const tid_set *in, int64_t n, const Pred *preds, int n_preds, tid_set *out) {

@@ -162,22 +162,40 @@ extern "C" int tid_entail(tid_ctx *ctx, const tid_store *st, int rule, const tid
     }
     TID_TRY(set_ready(Braw));
     TID_TRY(rows_of(Braw, &sx.res2));
-    TID_TRY(canonicalize(ctx, Braw->col, kb, bvars, sx.res2, true, nullptr, &B));
-    hold.keep(B);
+    // the distinct join terms among them (the paper's #Dist2)
+    int kcol = 0;
+    for (int c = 0; c < kb; ++c)
+        if (bvars[c] == R.on) kcol = c;
     tid_set *K2 = nullptr;
-    TID_TRY(project_set(ctx, B, &R.on, 1, &K2));
+    const int32_t *kcols[1] = {Braw->col[kcol]};
+    TID_TRY(canonicalize(ctx, kcols, 1, &R.on, sx.res2, true, nullptr, &K2));
     hold.keep(K2);
     TID_TRY(rows_of(K2, &sx.dist2));
+    B = Braw;  // rows in store order: the join below needs no order
 
-    // 4) join on the shared term; the conclusion's variables with DISTINCT
+    // 4) join on the shared term (the schema side is the small one: a hash join
+    //    with it as the table, rows left in the order written), then the
+    //    conclusion's variables put in canonical order with DISTINCT -- the one
+    //    sort of the rule
     tid_set *J = nullptr, *C = nullptr;
-    TID_TRY(join_sets(ctx, A, B, TID_JOIN_AUTO, &J));
+    TID_TRY(join_sets(ctx, A, B, TID_JOIN_HASH, &J, false));
     hold.keep(J);
     int8_t cvars[3];
     int kc = 0;
+    const int32_t *ccols[3];
+    Bounds cb{};
     for (int slot = 0; slot < 3; ++slot)
-        if (R.then_var[slot] >= 0) cvars[kc++] = R.then_var[slot];
-    TID_TRY(project_set(ctx, J, cvars, kc, &C));
+        if (R.then_var[slot] >= 0) {
+            int c = 0;
+            while (J->vars[c] != R.then_var[slot]) ++c;
+            ccols[kc] = J->col[c];
+            cb.lo[kc] = J->lo[c];
+            cb.hi[kc] = J->hi[c];
+            cvars[kc++] = R.then_var[slot];
+        }
+    int64_t nj = 0;
+    TID_TRY(rows_of(J, &nj));
+    TID_TRY(canonicalize(ctx, ccols, kc, cvars, nj, true, J->bounded ? &cb : nullptr, &C));
     hold.keep(C);
     int64_t rows = 0;
     TID_TRY(rows_of(C, &rows));

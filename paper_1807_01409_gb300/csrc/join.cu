@@ -52,15 +52,13 @@ struct MCols {
 // column pointers in registers (a loop bounded by nk would copy the parameter
 // arrays to local memory).
 __device__ __forceinline__ int cmp_rows(const Cols &A, int64_t a, const Cols &B, int64_t b, int nk) {
-    int r = 0;
 #pragma unroll
     for (int c = 0; c < TID_MAX_COLS; ++c) {
-        if (c < nk && r == 0) {
-            const int32_t x = A.c[c][a], y = B.c[c][b];
-            r = x < y ? -1 : (x > y ? 1 : 0);
-        }
+        if (c >= nk) break;
+        const int32_t x = A.c[c][a], y = B.c[c][b];
+        if (x != y) return x < y ? -1 : 1;
     }
-    return r;
+    return 0;
 }
 
 __device__ __forceinline__ bool has_zero(const Cols &A, int64_t a, int nk) {
@@ -71,17 +69,17 @@ __device__ __forceinline__ bool has_zero(const Cols &A, int64_t a, int nk) {
     return z;
 }
 
-// Output row o of a join: column c is src.c[c] at the left row lr, or, when
-// bit c of from_r is set, at the right row rr (rr < 0: unbound, 0).
-__device__ __forceinline__ void write_out(const Cols &src, uint32_t from_r, int kout, int64_t lr, int64_t rr,
-                                          const MCols &dst, int64_t o) {
+// Output row o of a join: L's kl columns of row lr, then R's other columns of
+// row rr (rr < 0: unbound, 0).  outL / outR point at the output columns of
+// each part, so every index here is a constant.
+__device__ __forceinline__ void write_out(const Cols &L, int kl, const Cols &Rrest, int nrest, int64_t lr, int64_t rr,
+                                          const MCols &outL, const MCols &outR, int64_t o) {
 #pragma unroll
-    for (int c = 0; c < TID_MAX_COLS; ++c) {
-        if (c < kout) {
-            const bool r = (from_r >> c) & 1u;
-            dst.c[c][o] = r ? (rr < 0 ? 0 : src.c[c][rr]) : src.c[c][lr];
-        }
-    }
+    for (int c = 0; c < TID_MAX_COLS; ++c)
+        if (c < kl) outL.c[c][o] = L.c[c][lr];
+#pragma unroll
+    for (int c = 0; c < TID_MAX_COLS; ++c)
+        if (c < nrest) outR.c[c][o] = rr < 0 ? 0 : Rrest.c[c][rr];
 }
 
 __device__ __forceinline__ void block_add_u64(unsigned long long v, unsigned long long *total) {
@@ -170,8 +168,8 @@ __global__ void k_sm_count(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, boo
 // one thread per output row
 __global__ void k_join_write(const uint32_t *__restrict__ off, int64_t nl, const uint32_t *__restrict__ lo,
                              const int32_t *__restrict__ lperm, const int32_t *__restrict__ rmap,
-                             const int32_t *__restrict__ rperm, int64_t total, Cols src, uint32_t from_r, int kout,
-                             MCols out, bool left_is_probe) {
+                             const int32_t *__restrict__ rperm, int64_t total, Cols L, int kl, Cols Rrest,
+                             int nrest, MCols outL, MCols outR, bool left_is_probe) {
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
          o += (int64_t)gridDim.x * blockDim.x) {
         int64_t a = 0, b = nl;  // first l with off[l] > o
@@ -182,7 +180,7 @@ __global__ void k_join_write(const uint32_t *__restrict__ off, int64_t nl, const
         }
         const int64_t l = a - 1;
         if (lo[l] == NO_MATCH) {  // left outer join: the left row alone, right columns unbound
-            write_out(src, from_r, kout, lperm ? lperm[l] : l, -1, out, o);
+            write_out(L, kl, Rrest, nrest, lperm ? lperm[l] : l, -1, outL, outR, o);
             continue;
         }
         const int64_t j = (int64_t)lo[l] + (o - (int64_t)off[l]);
@@ -195,7 +193,7 @@ __global__ void k_join_write(const uint32_t *__restrict__ off, int64_t nl, const
             rr = l;
             lr = rmap[j];
         }
-        write_out(src, from_r, kout, lr, rr, out, o);
+        write_out(L, kl, Rrest, nrest, lr, rr, outL, outR, o);
     }
 }
 
@@ -215,8 +213,9 @@ constexpr int MJ_ITEMS = 4;
 constexpr int MJ_TILE = MJ_THREADS * MJ_ITEMS;
 
 __global__ void __launch_bounds__(MJ_THREADS)
-k_merge_join(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, bool left, Cols src, uint32_t from_r, int kout,
-             MCols out, int64_t cap, int64_t *__restrict__ d_rows, int64_t *__restrict__ h_rows, Lookback lb) {
+k_merge_join(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, bool left, Cols L, int kl, Cols Rrest, int nrest,
+             MCols outL, MCols outR, int64_t cap, int64_t *__restrict__ d_rows, int64_t *__restrict__ h_rows,
+             Lookback lb) {
     __shared__ uint32_t s_excl[MJ_TILE + 1], s_lo[MJ_TILE];
     __shared__ uint32_t s_wsum[MJ_THREADS / 32];
     __shared__ unsigned s_tile;
@@ -298,7 +297,7 @@ k_merge_join(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, bool left, Cols s
         const long long pos = base + o;
         if (pos >= cap) continue;
         const int64_t j = s_lo[li] == NO_MATCH ? -1 : (int64_t)s_lo[li] + (o - s_excl[li]);
-        write_out(src, from_r, kout, l0 + li, j, out, pos);
+        write_out(L, kl, Rrest, nrest, l0 + li, j, outL, outR, pos);
     }
 }
 
@@ -448,7 +447,7 @@ int read_u64(tid_ctx *ctx, const unsigned long long *d, unsigned long long *h) {
 
 }  // namespace
 
-int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out) {
+int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out, bool sorted_out) {
     *out = nullptr;
     if (algo & TID_JOIN_RIGHT) return outer_join_sets(ctx, L, R, algo, out);
     const bool left = (algo & TID_JOIN_LEFT) != 0;
@@ -524,6 +523,8 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
     }
     if (algo == TID_JOIN_AUTO) algo = (nk == 0 || (lprefix && rprefix)) ? TID_JOIN_SORT_MERGE : TID_JOIN_HASH;
     if (nk == 0 || left) algo = TID_JOIN_SORT_MERGE;  // cross product; left outer join
+    if (!sorted_out && (algo != TID_JOIN_HASH || nk == 0 || left))
+        return fail(TID_ERR_ARG, "join: unsorted output is for inner hash joins");
 
     cudaStream_t st = ctx->stream;
     Bounds b{};  // output columns keep their input's bounds
@@ -545,30 +546,31 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         *out = res;
         return TID_OK;
     };
-    if (algo == TID_JOIN_SORT_MERGE && nk > 0 && lprefix && rprefix && (L->k == nk || R->k == nk)) {
+    if (sorted_out && algo == TID_JOIN_SORT_MERGE && nk > 0 && lprefix && rprefix && (L->k == nk || R->k == nk)) {
         // single pass into a result sized by the bound on its rows
         const int64_t ub = (L->k == nk ? nr : nl) + (left && L->k == nk ? nl : 0);
         tid_set *res = nullptr;
         TID_TRY(set_alloc(ctx, kout, ovars, ub, &res));
-        Cols LK{}, RK{}, src{};
+        Cols LK{}, RK{}, Lc{}, Rc{};
         for (int i = 0; i < nk; ++i) {
             LK.c[i] = L->col[i];
             RK.c[i] = R->col[i];
         }
-        uint32_t from_r = 0;
-        for (int c = 0; c < L->k; ++c) src.c[c] = L->col[c];
-        for (int c = 0; c < nrest; ++c) {
-            src.c[L->k + c] = R->col[rrest[c]];
-            from_r |= 1u << (L->k + c);
+        MCols oL{}, oR{};
+        for (int c = 0; c < L->k; ++c) {
+            Lc.c[c] = L->col[c];
+            oL.c[c] = res->col[c];
         }
-        MCols oc{};
-        for (int c = 0; c < kout; ++c) oc.c[c] = res->col[c];
+        for (int c = 0; c < nrest; ++c) {
+            Rc.c[c] = R->col[rrest[c]];
+            oR.c[c] = res->col[L->k + c];
+        }
         const unsigned tiles = (unsigned)ceil_div(nl, (int64_t)MJ_TILE);
         Lookback lb{};
         int rc = lookback_scratch(ctx, tiles, &lb);
         if (rc == TID_OK) {
-            k_merge_join<<<tiles, MJ_THREADS, 0, st>>>(LK, nl, RK, nr, nk, left, src, from_r, kout, oc, res->cap,
-                                                      res->d_rows, res->slot.dev, lb);
+            k_merge_join<<<tiles, MJ_THREADS, 0, st>>>(LK, nl, RK, nr, nk, left, Lc, L->k, Rc, nrest, oL, oR,
+                                                      res->cap, res->d_rows, res->slot.dev, lb);
             rc = launch_check("k_merge_join");
         }
         if (rc == TID_OK) rc = set_ready(res);
@@ -579,13 +581,9 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         return finish(res);
     }
     Scratch s(ctx);
-    Cols wsrc{};  // output column c comes from L (row lr) or, bit c of from_r, from R (row rr)
-    uint32_t from_r = 0;
-    for (int c = 0; c < L->k; ++c) wsrc.c[c] = L->col[c];
-    for (int c = 0; c < nrest; ++c) {
-        wsrc.c[L->k + c] = R->col[rrest[c]];
-        from_r |= 1u << (L->k + c);
-    }
+    Cols Lall{}, Rrest{};
+    for (int c = 0; c < L->k; ++c) Lall.c[c] = L->col[c];
+    for (int c = 0; c < nrest; ++c) Rrest.c[c] = R->col[rrest[c]];
     unsigned long long *d_total = nullptr;
     TID_TRY(s.get(&d_total, 1));
     TID_TRY_CUDA(cudaMemsetAsync(d_total, 0, 8, st), "memset");
@@ -685,7 +683,7 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         rmap = grouped;
         n_probe = nq;
         left_is_probe = !build_left;
-        canonical_out = lprefix && rprefix && B->k == nk;
+        canonical_out = (lprefix && rprefix && B->k == nk) || !sorted_out;
     }
 
     unsigned long long total = 0;
@@ -695,12 +693,13 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
     if (canonical_out) {  // write straight into the result set
         tid_set *res = nullptr;
         TID_TRY(set_alloc(ctx, kout, ovars, (int64_t)total, &res));
-        MCols oc{};
-        for (int c = 0; c < kout; ++c) oc.c[c] = res->col[c];
+        MCols oL{}, oR{};
+        for (int c = 0; c < L->k; ++c) oL.c[c] = res->col[c];
+        for (int c = 0; c < nrest; ++c) oR.c[c] = res->col[L->k + c];
         int rc = TID_OK;
         if (total > 0) {
             k_join_write<<<grid_for((int64_t)total, 256), 256, 0, st>>>(
-                off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, wsrc, from_r, kout, oc, left_is_probe);
+                off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, Lall, L->k, Rrest, nrest, oL, oR, left_is_probe);
             rc = launch_check("k_join_write");
         }
         if (rc == TID_OK) rc = set_rows_const(res, (int64_t)total);
@@ -712,11 +711,13 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         return finish(res);
     }
     // write, then sort to canonical order
-    MCols oc{};
+    MCols oc{}, oL{}, oR{};
     for (int c = 0; c < kout; ++c) TID_TRY(s.get(&oc.c[c], total > 0 ? total : 1));
+    for (int c = 0; c < L->k; ++c) oL.c[c] = oc.c[c];
+    for (int c = 0; c < nrest; ++c) oR.c[c] = oc.c[L->k + c];
     if (total > 0) {
         k_join_write<<<grid_for((int64_t)total, 256), 256, 0, st>>>(
-            off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, wsrc, from_r, kout, oc, left_is_probe);
+            off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, Lall, L->k, Rrest, nrest, oL, oR, left_is_probe);
         TID_TRY(launch_check("k_join_write"));
     }
     const int32_t *ocols[TID_MAX_COLS];

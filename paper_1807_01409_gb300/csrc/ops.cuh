@@ -79,7 +79,9 @@ int set_rows_host(tid_set *set, int64_t *rows);
 int set_rows_host(const tid_set *set, int64_t *rows);
 
 // joins (join.cu); right and full outer joins composed from the left join (ops.cu)
-int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out);
+// sorted_out = false (internal use, hash join of inputs in any row order): the
+// joined rows in the order written, not canonical (the caller sorts what it keeps)
+int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out, bool sorted_out = true);
 int outer_join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_set **out);
 
 // merge (merge.cu): the distinct rows of two sets each sorted in the same nu

@@ -11,15 +11,17 @@
 // (key, row) pairs are radix sorted stably, so the final permutation orders
 // rows lexicographically; again only the bits that vary are sorted.
 //
-// One-sweep LSD passes (Adinets and Merrill, "Onesweep: A Faster Least
-// Significant Digit Radix Sort for GPUs", 2022): the pass that packs (or
-// prepares) the keys also histograms all their 8-bit digits, one small kernel
-// turns the histograms into bin starts, and then each digit is ONE launch:
-// tiles of 4096 keys, in ticket order, rank their keys stably (warp match_any),
-// find each bin's offset among earlier tiles by decoupled look-back per bin
-// and scatter through shared memory so runs of equal digits are written
-// contiguously.  Bytes per digit: w n read + w n written, w = key bytes (4 or
-// 8; 4 + 4 with the permutation), plus one read of the columns for packing.
+// One digit pass = per-tile histograms (k_tile_hist) + a scan of the (digit,
+// tile) counts + one ranking-and-scatter launch (k_onesweep): tiles of 4096
+// keys rank stably (warp match_any groups, the first lane of a group adding
+// its size to a shared counter) and scatter through shared memory so runs of
+// equal digits are written contiguously, at the scanned offsets.  No tile
+// waits for another: a one-launch form whose tiles took each bin's offset by a
+// decoupled look-back over earlier tiles (Adinets and Merrill, "Onesweep",
+// 2022) waited there longer than its tiles worked, every tile walking back
+// through all the tiles in flight.  Bytes per digit: w n read twice (the
+// histogram read mostly from L2) + w n written, w = key bytes (4 or 8; 4 + 4
+// with the permutation), plus one read of the columns for packing.
 //
 // Sets of at most 4096 packed rows skip the passes: one CTA loads the keys into
 // shared memory, bitonic-sorts them, flags and block-scans the distinct ones
@@ -27,7 +29,7 @@
 
 #include <algorithm>
 
-#include "lookback.cuh"
+#include "tid_internal.cuh"
 #include "ops.cuh"
 
 namespace tid {
@@ -83,64 +85,15 @@ __global__ void k_minmax(ColPtrs cols, int k, int64_t n, uint32_t *__restrict__ 
     }
 }
 
-// Histograms of the 8-bit digits p = 0 .. ndig-1 of keys (digit p = bits
-// shift0 + 8p ..), accumulated with plain shared-memory atomics in
-// HIST_COPIES copies (warp w adds to copy w % HIST_COPIES, so warps seldom
-// meet on one counter; a whole warp on one digit -- the common case for high
-// digits -- is one add) and added to hist[p * 256 + b].  Called by whole warps.
-constexpr int RS_MAX_DIGITS = 8;
-constexpr int HIST_COPIES = 4;
 
-template <typename K>
-__device__ __forceinline__ void hist_add(uint32_t *s_hist, K key, bool valid, int shift0, int ndig) {
-    const unsigned lane = threadIdx.x & 31;
-    uint32_t *h = s_hist + ((threadIdx.x >> 5) % HIST_COPIES) * (RS_MAX_DIGITS * RS_BINS);
-    for (int p = 0; p < ndig; ++p) {
-        const unsigned d = valid ? (unsigned)(key >> (shift0 + 8 * p)) & 0xFFu : 0x100u;
-        const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
-        if (__all_sync(0xffffffffu, d == d0)) {
-            if (lane == 0 && d0 < 0x100u) atomicAdd(&h[p * RS_BINS + d0], 32u);
-        } else if (valid) {
-            atomicAdd(&h[p * RS_BINS + d], 1u);
-        }
+// keys[i] = order_key(col[src(i)]) - base, vals[i] = src(i), src = perm ? perm[i] : i
+__global__ void k_prep(const int32_t *__restrict__ col, const int32_t *__restrict__ perm, int64_t n, uint32_t base,
+                       uint32_t *__restrict__ keys, int32_t *__restrict__ vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = perm ? perm[i] : (int32_t)i;
+        keys[i] = order_key(col[s]) - base;
+        vals[i] = s;
     }
-}
-
-__device__ __forceinline__ void hist_clear(uint32_t *s_hist) {
-    for (int i = threadIdx.x; i < HIST_COPIES * RS_MAX_DIGITS * RS_BINS; i += blockDim.x) s_hist[i] = 0;
-    __syncthreads();
-}
-
-__device__ __forceinline__ void hist_flush(uint32_t *s_hist, int ndig, uint32_t *__restrict__ hist) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < ndig * RS_BINS; i += blockDim.x) {
-        uint32_t v = 0;
-#pragma unroll
-        for (int c = 0; c < HIST_COPIES; ++c) v += s_hist[c * RS_MAX_DIGITS * RS_BINS + i];
-        if (v) atomicAdd(hist + i, v);
-    }
-}
-
-// keys[i] = order_key(col[src(i)]) - base, vals[i] = src(i), src = perm ? perm[i] : i;
-// with the digit histograms of the keys
-__global__ void __launch_bounds__(256) k_prep(const int32_t *__restrict__ col, const int32_t *__restrict__ perm,
-                                              int64_t n, uint32_t base, uint32_t *__restrict__ keys,
-                                              int32_t *__restrict__ vals, int ndig, uint32_t *__restrict__ hist) {
-    __shared__ uint32_t s_hist[HIST_COPIES * RS_MAX_DIGITS * RS_BINS];
-    hist_clear(s_hist);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n_iter = ceil_div(n, stride) * stride;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_iter; i += stride) {
-        uint32_t key = 0;
-        if (i < n) {
-            const int32_t s = perm ? perm[i] : (int32_t)i;
-            key = order_key(col[s]) - base;
-            keys[i] = key;
-            vals[i] = s;
-        }
-        hist_add(s_hist, key, i < n, 0, ndig);
-    }
-    hist_flush(s_hist, ndig, hist);
 }
 
 __global__ void k_iota32(int32_t *__restrict__ out, int64_t n) {
@@ -148,113 +101,60 @@ __global__ void k_iota32(int32_t *__restrict__ out, int64_t n) {
         out[i] = (int32_t)i;
 }
 
-// hist[p][b] -> exclusive start of bin b of digit p (one CTA, a thread per bin)
-__global__ void __launch_bounds__(RS_BINS) k_digit_starts(uint32_t *__restrict__ hist, int ndig) {
-    __shared__ uint32_t s_w[RS_BINS / 32];
+// Per-tile histogram of one digit: hist[d * tiles + t] = keys of tile t (RS_TILE
+// keys) whose digit at `shift` is d.  Per-warp counters in shared memory (a
+// whole warp on one digit is one add).
+template <typename K>
+__global__ void __launch_bounds__(RS_THREADS) k_tile_hist(const K *__restrict__ keys, int64_t n, int shift,
+                                                          uint32_t *__restrict__ hist, unsigned tiles) {
+    __shared__ uint32_t s_h[RS_WARPS][RS_BINS];
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int p = 0; p < ndig; ++p) {
-        const uint32_t c = hist[p * RS_BINS + threadIdx.x];
-        uint32_t x = c;
+    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    K k[RS_ITEMS];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-            if ((int)lane >= d) x += y;
-        }
-        if (lane == 31) s_w[warp] = x;
-        __syncthreads();
-        uint32_t wb = 0;
-        for (unsigned w = 0; w < warp; ++w) wb += s_w[w];
-        hist[p * RS_BINS + threadIdx.x] = wb + x - c;
-        __syncthreads();
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        const int64_t i = base + j * RS_THREADS + threadIdx.x;
+        k[j] = i < n ? keys[i] : (K)0;
     }
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        const int64_t i = base + j * RS_THREADS + threadIdx.x;
+        const bool valid = i < n;
+        const unsigned d = valid ? (unsigned)(k[j] >> shift) & 0xFFu : 0x100u;
+        const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
+        if (__all_sync(0xffffffffu, d == d0)) {
+            if (lane == 0 && d0 < 0x100u) s_h[warp][d0] += 32u;
+        } else if (valid) {
+            atomicAdd(&s_h[warp][d], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) c += s_h[w][threadIdx.x];
+    hist[(size_t)threadIdx.x * tiles + blockIdx.x] = c;
 }
 
-// Thread d of a tile: the count of digit d in the tiles before this one, by
-// decoupled look-back over status words [tile][bin] (epoch, flag, count),
-// reading BL_WINDOW predecessors per round trip; -1 if a wait gave up.
-constexpr int BL_WINDOW = 16;
-
-__device__ __forceinline__ long long bin_lookback(const Lookback &lb, unsigned tile, unsigned d, unsigned total) {
-    unsigned long long *st = lb.status;
-    if (tile == 0) {
-        lb_store(st + d, lb_word(lb.epoch, LB_FLAG_PREFIX, total));
-        return 0;
-    }
-    lb_store(st + (size_t)tile * RS_BINS + d, lb_word(lb.epoch, LB_FLAG_AGG, total));
-    long long excl = 0;
-    long long j = (long long)tile - 1;  // nearest predecessor not yet summed
-    unsigned polls = 0;
-    while (true) {
-        unsigned long long w[BL_WINDOW];
-#pragma unroll
-        for (int i = 0; i < BL_WINDOW; ++i)
-            w[i] = j - i >= 0 ? lb_load(st + (size_t)(j - i) * RS_BINS + d) : lb_word(lb.epoch, LB_FLAG_PREFIX, 0);
-        // nearest first: sum aggregates up to the first inclusive prefix; stop at a gap
-        int used = 0;
-        bool done = false, gap = false, aborted = false;
-#pragma unroll
-        for (int i = 0; i < BL_WINDOW; ++i) {
-            if (done || gap || aborted) continue;
-            const unsigned f = ((unsigned)(w[i] >> 34) == lb.epoch) ? (unsigned)(w[i] >> 32) & 3u : 0u;
-            if (f == 0) {
-                gap = true;
-            } else if (f == LB_FLAG_ABORT) {
-                aborted = true;
-            } else {
-                excl += (unsigned)w[i];
-                ++used;
-                done = f == LB_FLAG_PREFIX;
-            }
-        }
-        if (aborted) {
-            excl = -1;
-            break;
-        }
-        if (done) break;
-        j -= used;
-        if (gap) {
-            if (++polls > LB_SPIN_LIMIT) {
-                atomicExch(lb.err, TID_ERR_TIMEOUT);
-                excl = -1;
-                break;
-            }
-            __nanosleep(polls < 64 ? 32 : 256);
-        }
-    }
-    lb_store(st + (size_t)tile * RS_BINS + d,
-             excl < 0 ? lb_word(lb.epoch, LB_FLAG_ABORT, 0) : lb_word(lb.epoch, LB_FLAG_PREFIX, (unsigned)(excl + total)));
-    return excl;
-}
-
-// One digit pass of the one-sweep LSD sort: tiles in ticket order rank their
-// keys stably by digit (warp match_any ranks in row order, warps in order),
-// take each digit's global start from the digit's bin start plus the counts of
-// earlier tiles (per-bin look-back), and scatter through shared memory so runs
-// of equal digits are written contiguously.  Keys (and, with HAS_VAL, a 32-bit
-// value per key) move from kin/vin to kout/vout.
+// The offset of (digit d, tile t) is offs[d * tiles + t]: the scanned per-tile
+// histograms (k_tile_hist), so no tile waits for another.
 template <typename K, bool HAS_VAL>
 __global__ void __launch_bounds__(RS_THREADS, 3)
 k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__restrict__ kout, int32_t *__restrict__ vout,
-           int64_t n, int shift, const uint32_t *__restrict__ bin_start, Lookback lb) {
+           int64_t n, int shift, const uint32_t *__restrict__ offs, unsigned tiles) {
     __shared__ uint32_t s_wcnt[RS_WARPS][RS_BINS];
     __shared__ uint32_t s_tdig[RS_BINS];
     __shared__ uint32_t s_gbase[RS_BINS];
     __shared__ uint32_t s_wsum[RS_WARPS];
     __shared__ K s_k[RS_TILE];
     __shared__ int32_t s_v[HAS_VAL ? RS_TILE : 1];
-    __shared__ unsigned s_tile;
-    __shared__ int s_abort;
 
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    if (threadIdx.x == 0) {
-        s_tile = lb_ticket(lb);
-        s_abort = 0;
-    }
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
-    const unsigned tile = s_tile;
-    if (tile >= lb.num_tiles) return;
+    const unsigned tile = blockIdx.x;
     const int64_t base = (int64_t)tile * RS_TILE;
     const int64_t wbase = base + (int64_t)warp * (RS_ITEMS * 32);
     K k[RS_ITEMS];
@@ -267,18 +167,21 @@ k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__rest
         k[j] = valid ? kin[i] : (K)0;
         if (HAS_VAL) v[j] = valid ? vin[i] : 0;
     }
-    // stable rank among this warp's rows with the same digit, in row order
+    // stable rank among this warp's rows with the same digit, in row order: the
+    // first lane of each group of equal digits adds the group's size to the
+    // warp's counter (the shared-memory atomic returns the count before it) and
+    // the group reads that base from it -- no warp-wide wait between items,
+    // so the items' counter updates overlap
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
         const int64_t i = wbase + j * 32 + lane;
         const bool valid = i < n;
         const unsigned d = valid ? (unsigned)(k[j] >> shift) & 0xFFu : 0x100u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
         uint32_t b = 0;
-        if (valid) b = s_wcnt[warp][d];
-        __syncwarp();
-        if (valid && lane == (unsigned)(__ffs(peers) - 1)) s_wcnt[warp][d] = b + __popc(peers);
-        __syncwarp();
+        if (valid && lane == (unsigned)leader) b = atomicAdd(&s_wcnt[warp][d], (uint32_t)__popc(peers));
+        b = __shfl_sync(0xffffffffu, b, leader);
         r[j] = b + __popc(peers & lt);
     }
     __syncthreads();
@@ -311,12 +214,9 @@ k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__rest
         }
         __syncthreads();
         s_tdig[d] = x - run + s_wsum[warp];
-        const long long before = bin_lookback(lb, tile, d, run);  // digit d in earlier tiles
-        if (before < 0) s_abort = 1;
-        s_gbase[d] = bin_start[d] + (uint32_t)(before < 0 ? 0 : before);
+        s_gbase[d] = offs[(size_t)d * tiles + tile];
     }
     __syncthreads();
-    if (s_abort) return;
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
         const int64_t i = wbase + j * 32 + lane;
@@ -341,23 +241,14 @@ k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__rest
 // packed key of a row: column 0 most significant; field c holds
 // order_key(col_c) - min_c in bits [shift_c, shift_c + bits_c)
 template <typename K>
-__global__ void __launch_bounds__(256) k_pack(ColPtrs cols, int k, int64_t n, PackSpec ps, K *__restrict__ keys,
-                                              int shift0, int ndig, uint32_t *__restrict__ hist) {
-    __shared__ uint32_t s_hist[HIST_COPIES * RS_MAX_DIGITS * RS_BINS];
-    hist_clear(s_hist);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n_iter = ceil_div(n, stride) * stride;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_iter; i += stride) {
+__global__ void k_pack(ColPtrs cols, int k, int64_t n, PackSpec ps, K *__restrict__ keys) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         K key = 0;
-        if (i < n) {
 #pragma unroll
-            for (int c = 0; c < TID_MAX_COLS; ++c)  // a constant column (mask 0) has no field
-                if (c < k && ps.mask[c]) key |= (K)(order_key(cols.c[c][i]) - ps.min[c]) << ps.shift[c];
-            keys[i] = key;
-        }
-        hist_add(s_hist, key, i < n, shift0, ndig);
+        for (int c = 0; c < TID_MAX_COLS; ++c)  // a constant column (mask 0) has no field
+            if (c < k && ps.mask[c]) key |= (K)(order_key(cols.c[c][i]) - ps.min[c]) << ps.shift[c];
+        keys[i] = key;
     }
-    hist_flush(s_hist, ndig, hist);
 }
 
 // sorted packed keys -> k columns (no duplicate removal)
@@ -520,30 +411,29 @@ static int column_ranges(tid_ctx *ctx, const int32_t *const *cols, int k, int64_
 
 static int range_bits(uint32_t lo, uint32_t hi) { return hi == lo ? 0 : 32 - __builtin_clz(hi - lo); }
 
-// Look-back state of one digit pass: status words for tiles x 256 bins.
-static int onesweep_lookback(tid_ctx *ctx, unsigned tiles, Lookback *lb) {
-    LbScratch sc{};
-    TID_TRY(ctx_scratch(ctx, (size_t)tiles * RS_BINS, &sc));
-    return make_lookback(sc, tiles, lb);
-}
-
-// The digit passes of a one-sweep sort: hist holds the exclusive bin starts of
-// every digit (k_digit_starts); keys (and values) ping-pong between a and b;
-// on return a holds the sorted keys.
+// Each digit: per-tile histograms, one scan of the (digit, tile) counts, then
+// the ranking and scatter at the scanned offsets.
 template <typename K, bool HAS_VAL>
-static int onesweep_passes(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *&pb, int64_t n, int shift0,
-                           int passes, const uint32_t *hist) {
+static int radix_passes(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *&pb, int64_t n, int shift0,
+                        int passes) {
     const unsigned tiles = (unsigned)ceil_div(n, RS_TILE);
-    for (int p = 0; p < passes; ++p) {
-        Lookback lb{};
-        TID_TRY(onesweep_lookback(ctx, tiles, &lb));
-        k_onesweep<K, HAS_VAL><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, pa, kb, pb, n, shift0 + 8 * p,
-                                                                     hist + p * RS_BINS, lb);
-        TID_TRY(launch_check("k_onesweep"));
+    uint32_t *offs = nullptr;
+    TID_TRY(dev_alloc(ctx, (void **)&offs, sizeof(uint32_t) * (size_t)RS_BINS * tiles + 256));
+    int rc = TID_OK;
+    for (int p = 0; p < passes && rc == TID_OK; ++p) {
+        const int shift = shift0 + 8 * p;
+        k_tile_hist<K><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, n, shift, offs, tiles);
+        rc = launch_check("k_tile_hist");
+        if (rc == TID_OK) rc = scan_exclusive_u32(ctx, offs, offs, (int64_t)RS_BINS * tiles, nullptr);
+        if (rc == TID_OK) {
+            k_onesweep<K, HAS_VAL><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, pa, kb, pb, n, shift, offs, tiles);
+            rc = launch_check("k_onesweep");
+        }
         std::swap(ka, kb);
         if (HAS_VAL) std::swap(pa, pb);
     }
-    return TID_OK;
+    dev_free(ctx, offs);
+    return rc;
 }
 
 // Stable LSD sort of a row permutation by key columns, given their ranges.  The
@@ -554,7 +444,7 @@ static int sort_perm_ranges(tid_ctx *ctx, const int32_t *const *keys, int nk, in
                             const uint32_t *hmax, int32_t *perm, int sorted_tail = 0) {
     cudaStream_t st = ctx->stream;
     Scratch s(ctx);
-    uint32_t *ka = nullptr, *kb = nullptr, *hist = nullptr;
+    uint32_t *ka = nullptr, *kb = nullptr;
     int32_t *pa = nullptr, *pb = nullptr;
     bool have_perm = false;  // pa holds the current permutation
     for (int c = nk - 1 - sorted_tail; c >= 0; --c) {
@@ -566,15 +456,10 @@ static int sort_perm_ranges(tid_ctx *ctx, const int32_t *const *keys, int nk, in
             TID_TRY(s.get(&kb, n));
             TID_TRY(s.get(&pa, n));
             TID_TRY(s.get(&pb, n));
-            TID_TRY(s.get(&hist, (size_t)RS_BINS * 4));
         }
-        TID_TRY_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * RS_BINS * passes, st), "memset histogram");
-        k_prep<<<grid_for(n, 256, 8), 256, 0, st>>>(keys[c], have_perm ? pa : nullptr, n, hmin[c], ka, pa, passes,
-                                                    hist);
+        k_prep<<<grid_for(n, 256), 256, 0, st>>>(keys[c], have_perm ? pa : nullptr, n, hmin[c], ka, pa);
         TID_TRY(launch_check("k_prep"));
-        k_digit_starts<<<1, RS_BINS, 0, st>>>(hist, passes);
-        TID_TRY(launch_check("k_digit_starts"));
-        TID_TRY((onesweep_passes<uint32_t, true>(ctx, ka, kb, pa, pb, n, 0, passes, hist)));
+        TID_TRY((radix_passes<uint32_t, true>(ctx, ka, kb, pa, pb, n, 0, passes)));
         have_perm = true;
     }
     if (have_perm) {
@@ -618,20 +503,15 @@ static int canonical_packed(tid_ctx *ctx, const int32_t *const *cols, int k, int
     }
     Scratch s(ctx);
     K *ka = nullptr, *kb = nullptr;
-    uint32_t *hist = nullptr;
     int32_t *none_a = nullptr, *none_b = nullptr;
     const int passes = (total_bits - sorted_bits + 7) / 8;
     TID_TRY(s.get(&ka, n));
     TID_TRY(s.get(&kb, n));
-    TID_TRY(s.get(&hist, (size_t)RS_BINS * RS_MAX_DIGITS));
-    TID_TRY_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * RS_BINS * RS_MAX_DIGITS, st), "memset histogram");
     ColPtrs cp{};
     for (int c = 0; c < k; ++c) cp.c[c] = cols[c];
-    k_pack<K><<<grid_for(n, 256, 8), 256, 0, st>>>(cp, k, n, ps, ka, sorted_bits, passes, hist);
+    k_pack<K><<<grid_for(n, 256), 256, 0, st>>>(cp, k, n, ps, ka);
     TID_TRY(launch_check("k_pack"));
-    k_digit_starts<<<1, RS_BINS, 0, st>>>(hist, passes);
-    TID_TRY(launch_check("k_digit_starts"));
-    TID_TRY((onesweep_passes<K, false>(ctx, ka, kb, none_a, none_b, n, sorted_bits, passes, hist)));
+    TID_TRY((radix_passes<K, false>(ctx, ka, kb, none_a, none_b, n, sorted_bits, passes)));
     if (dedupe) return compact_unique_packed(ctx, ka, sizeof(K) == 8, k, n, ps, set);
     MutColPtrs op{};
     for (int c = 0; c < k; ++c) op.c[c] = set->col[c];
