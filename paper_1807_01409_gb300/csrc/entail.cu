@@ -10,7 +10,11 @@
 //     at the join position is in the table (K3 with a hash probe per triple,
 //     in store order) and extracts their variables;
 //  4. the two result vectors are joined on the shared term (K5/K6) and the
-//     conclusion's terms kept with DISTINCT.
+//     conclusion's terms kept with DISTINCT.  When the conclusion is a pair of
+//     terms, one from each premise, this is done without materialising the
+//     join: each data row sets the bits of its pairs in a bit matrix indexed
+//     by (rank of the schema term, data term - min), and the set bits, read
+//     in order, are the distinct pairs already in canonical order.
 #include <algorithm>
 #include <vector>
 
@@ -58,6 +62,284 @@ __global__ void k_fill_i32(int32_t *__restrict__ out, int64_t n, int32_t v) {
         out[i] = v;
 }
 
+constexpr int BM_THREADS = 256;
+constexpr int BM_WORDS = 8;                     // bit-matrix words per thread
+constexpr int BM_TILE = BM_THREADS * BM_WORDS;  // words per tile
+constexpr uint32_t KEY_HASH = 0x9E3779B1u;      // multiplicative (Knuth) hash of the key table
+
+__host__ __device__ __forceinline__ uint32_t home_slot(int32_t key, int tbits) {
+    return ((uint32_t)key * KEY_HASH) >> (32 - tbits);
+}
+
+// slot of `key` in the open-addressing key table, or -1 (0 is the empty slot
+// and never a key); at most one sweep of the table
+__device__ __forceinline__ int find_slot(const int32_t *__restrict__ table, int tbits, int32_t key) {
+    if (key == 0) return -1;
+    const uint32_t mask = (1u << tbits) - 1u;
+    uint32_t h = home_slot(key, tbits);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const int32_t t = table[h];
+        if (t == key) return (int)h;
+        if (t == 0) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ uint32_t sort_order(int32_t x) { return (uint32_t)x ^ 0x80000000u; }
+
+constexpr int BM_RUN = 16;  // consecutive rows per thread in the marking kernels
+
+// flags gets one bit per table slot whose key occurs in key[0, n): the distinct
+// join terms of the data premise's rows.  Each thread takes runs of BM_RUN
+// consecutive rows and sets a slot's bit only when the row's slot differs
+// from its previous row's and the bit is still clear, so rows of a repeated
+// term cost a read.  Bits collect in shared memory when SMEM, else in global
+// memory directly.
+template <bool SMEM>
+__global__ void __launch_bounds__(BM_THREADS) k_mark_keys(const int32_t *__restrict__ key, int64_t n,
+                                                          const int32_t *__restrict__ table, int tbits,
+                                                          uint32_t *__restrict__ flags) {
+    extern __shared__ uint32_t s_f[];
+    const uint32_t words = ((1u << tbits) + 31u) >> 5;
+    if (SMEM) {
+        for (uint32_t w = threadIdx.x; w < words; w += BM_THREADS) s_f[w] = 0;
+        __syncthreads();
+    }
+    volatile uint32_t *f = SMEM ? s_f : flags;
+    const int64_t runs = (n + BM_RUN - 1) / BM_RUN;
+    for (int64_t q = (int64_t)blockIdx.x * BM_THREADS + threadIdx.x; q < runs; q += (int64_t)gridDim.x * BM_THREADS) {
+        int last = -1;
+        const int64_t e = min(n, (q + 1) * BM_RUN);
+        for (int64_t i = q * BM_RUN; i < e; ++i) {
+            const int h = find_slot(table, tbits, key[i]);
+            if (h < 0 || h == last) continue;
+            last = h;
+            const uint32_t b = 1u << (h & 31);
+            if (!(f[h >> 5] & b)) atomicOr((uint32_t *)f + (h >> 5), b);
+        }
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (uint32_t w = threadIdx.x; w < words; w += BM_THREADS)
+            if (s_f[w]) atomicOr(flags + w, s_f[w]);
+    }
+}
+
+// The conclusion's distinct pairs as the set bits of a matrix.  A data-premise
+// row (join term, term t) joined with the schema rows of that join term gives
+// the pairs (r, t) for A's other terms r.  r is ranked among A's distinct
+// values of that term (ascending) and t is taken as d = order(t) - vmin.  The
+// pair is bit r * w + d when A's term comes first in the conclusion, d * na + r
+// when t does.  Matrix rows thus follow the first term, bits within a row the
+// second, and the set bits in ascending order are the canonical distinct rows.
+struct PairBits {
+    const int32_t *key, *val;  // data-premise rows: join term, conclusion term
+    int64_t n;
+    const int32_t *table;  // the join terms (open addressing)
+    int tbits;
+    const uint32_t *off;    // slot h: A's ranks are rank[off[h] .. off[h + 1])
+    const uint32_t *rank;
+    const uint32_t *kmask;  // slot h: the same ranks as a mask (t first, na <= 32)
+    uint32_t vmin;
+    uint64_t na, w;  // A's distinct terms; width of t's range
+    int a_first;
+    uint32_t *bits;
+};
+
+// General form: one atomic OR per (row, rank).  A thread takes BM_RUN
+// consecutive rows and skips a row whose pairs repeat the previous row's.
+__global__ void __launch_bounds__(BM_THREADS) k_pair_bits_list(PairBits P) {
+    const int64_t runs = (P.n + BM_RUN - 1) / BM_RUN;
+    for (int64_t q = (int64_t)blockIdx.x * BM_THREADS + threadIdx.x; q < runs; q += (int64_t)gridDim.x * BM_THREADS) {
+        int last_h = -1;
+        uint64_t last_d = 0;
+        const int64_t e = min(P.n, (q + 1) * BM_RUN);
+        for (int64_t i = q * BM_RUN; i < e; ++i) {
+            const int h = find_slot(P.table, P.tbits, P.key[i]);
+            if (h < 0) continue;
+            const uint64_t d = sort_order(P.val[i]) - P.vmin;
+            if (h == last_h && d == last_d) continue;
+            last_h = h;
+            last_d = d;
+            for (uint32_t j = P.off[h]; j < P.off[h + 1]; ++j) {
+                const uint64_t r = P.rank[j];
+                const uint64_t g = P.a_first ? r * P.w + d : d * P.na + r;
+                atomicOr(P.bits + (g >> 5), 1u << (g & 31));
+            }
+        }
+    }
+}
+
+// t first and na <= 32: a row's ranks are one mask, shifted to bit d * na (at
+// most two words).  A thread ORs the masks of its run's consecutive rows that
+// fall in the same word pair and writes each pair once.
+__global__ void __launch_bounds__(BM_THREADS) k_pair_bits_mask(PairBits P) {
+    const int64_t runs = (P.n + BM_RUN - 1) / BM_RUN;
+    for (int64_t q = (int64_t)blockIdx.x * BM_THREADS + threadIdx.x; q < runs; q += (int64_t)gridDim.x * BM_THREADS) {
+        uint64_t cur = ~0ull, acc = 0;  // word index and the bits of words cur, cur + 1
+        const int64_t e = min(P.n, (q + 1) * BM_RUN);
+        for (int64_t i = q * BM_RUN; i < e; ++i) {
+            const int h = find_slot(P.table, P.tbits, P.key[i]);
+            if (h < 0) continue;
+            const uint64_t g = (uint64_t)(sort_order(P.val[i]) - P.vmin) * P.na;
+            const uint64_t word = g >> 5;
+            const uint64_t m = (uint64_t)P.kmask[h] << (g & 31);
+            if (word != cur) {
+                if (acc & 0xFFFFFFFFull) atomicOr(P.bits + cur, (uint32_t)acc);
+                if (acc >> 32) atomicOr(P.bits + cur + 1, (uint32_t)(acc >> 32));
+                cur = word;
+                acc = 0;
+            }
+            acc |= m;
+        }
+        if (acc & 0xFFFFFFFFull) atomicOr(P.bits + cur, (uint32_t)acc);
+        if (acc >> 32) atomicOr(P.bits + cur + 1, (uint32_t)(acc >> 32));
+    }
+}
+
+// counts[t] = set bits of tile t (BM_TILE words; thread i owns words
+// [i * BM_WORDS, (i + 1) * BM_WORDS) of the tile)
+__global__ void __launch_bounds__(BM_THREADS) k_tile_bits(const uint32_t *__restrict__ bits, int64_t nwords,
+                                                          uint32_t *__restrict__ counts) {
+    __shared__ uint32_t s_w[BM_THREADS / 32];
+    const int64_t w0 = (int64_t)blockIdx.x * BM_TILE + (int64_t)threadIdx.x * BM_WORDS;
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < BM_WORDS; ++j)
+        if (w0 + j < nwords) c += __popc(bits[w0 + j]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < BM_THREADS / 32; ++w) t += s_w[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// offs[t] = sum of counts[0, t) (64-bit), *total = sum of all (one CTA: each
+// thread scans a contiguous share)
+__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *__restrict__ counts, int64_t tiles,
+                                                     unsigned long long *__restrict__ offs,
+                                                     unsigned long long *__restrict__ total) {
+    __shared__ unsigned long long s_w[32];
+    const int64_t per = (tiles + 1023) / 1024;
+    const int64_t b = min(tiles, (int64_t)threadIdx.x * per), e = min(tiles, b + per);
+    unsigned long long s = 0;
+    for (int64_t t = b; t < e; ++t) s += counts[t];
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+        if ((int)lane >= d) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long v = s_w[lane];
+        unsigned long long y = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long z = __shfl_up_sync(0xffffffffu, y, d);
+            if ((int)lane >= d) y += z;
+        }
+        s_w[lane] = y - v;
+        if (lane == 31) *total = y;
+    }
+    __syncthreads();
+    unsigned long long run = s_w[warp] + x - s;
+    for (int64_t t = b; t < e; ++t) {
+        offs[t] = run;
+        run += counts[t];
+    }
+}
+
+// The set bits of each tile, in order, as rows (first term, second term) at
+// the tile's offset.
+__global__ void __launch_bounds__(BM_THREADS) k_emit_pairs(const uint32_t *__restrict__ bits, int64_t nwords,
+                                                           const unsigned long long *__restrict__ offs,
+                                                           const int32_t *__restrict__ rankval, uint32_t vmin,
+                                                           uint64_t na, uint64_t w, int a_first,
+                                                           int32_t *__restrict__ out0, int32_t *__restrict__ out1) {
+    __shared__ uint32_t s_w[BM_THREADS / 32];
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t w0 = (int64_t)blockIdx.x * BM_TILE + (int64_t)threadIdx.x * BM_WORDS;
+    uint32_t v[BM_WORDS];
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < BM_WORDS; ++j) {
+        v[j] = w0 + j < nwords ? bits[w0 + j] : 0u;
+        c += __popc(v[j]);
+    }
+    uint32_t x = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if ((int)lane >= d) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (unsigned i = 0; i < warp; ++i) before += s_w[i];
+    uint64_t pos = offs[blockIdx.x] + before + x - c;
+    const uint64_t row_w = a_first ? w : na;  // bits per matrix row
+#pragma unroll
+    for (int j = 0; j < BM_WORDS; ++j) {
+        uint32_t m = v[j];
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const uint64_t g = (uint64_t)(w0 + j) * 32 + (uint64_t)b;
+            const uint64_t hi = g / row_w, lo = g - hi * row_w;
+            const uint64_t r = a_first ? hi : lo, d = a_first ? lo : hi;
+            const int32_t a = rankval[r], t = (int32_t)((vmin + (uint32_t)d) ^ 0x80000000u);
+            out0[pos] = a_first ? a : t;
+            out1[pos] = a_first ? t : a;
+            ++pos;
+        }
+    }
+}
+
+// *count = set bits of words[0, n) (one CTA)
+__global__ void __launch_bounds__(1024) k_count_bits(const uint32_t *__restrict__ words, int64_t n,
+                                                     unsigned long long *__restrict__ count) {
+    __shared__ unsigned long long s_w[32];
+    unsigned long long c = 0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) c += (unsigned)__popc(words[i]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        c = s_w[threadIdx.x];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+        if (threadIdx.x == 0) *count = c;
+    }
+}
+
+// mm[0] = min, mm[1] = max of col[0, n) in sort order (mm preset to ~0, 0)
+__global__ void k_col_range(const int32_t *__restrict__ col, int64_t n, uint32_t *__restrict__ mm) {
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = sort_order(col[i]);
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(mm, lo);
+        atomicMax(mm + 1, hi);
+    }
+}
+
 struct Sets {  // frees what it holds
     std::vector<tid_set *> v;
     ~Sets() {
@@ -70,6 +352,163 @@ struct Sets {  // frees what it holds
 };
 
 int rows_of(tid_set *s, int64_t *n) { return set_rows_host(s, n); }
+
+struct Buf {  // a device allocation freed on scope exit
+    tid_ctx *c;
+    void *p = nullptr;
+    ~Buf() {
+        if (p) dev_free(c, p);
+    }
+};
+
+constexpr int64_t PAIR_MAX_SCHEMA_ROWS = 1 << 22;  // schema rows ranked on the host
+constexpr uint64_t PAIR_MIN_BYTES = 64ull << 20;     // a matrix this small is always taken
+constexpr uint64_t PAIR_BYTES_PER_ROW = 32;          // else at most this per data-premise row
+constexpr uint64_t PAIR_MAX_BYTES = 4ull << 30;
+
+// The conclusion as the bit matrix of its distinct pairs (PairBits), when it
+// has two terms, A's non-join term and one of the data premise's, and the
+// matrix is small enough.  *out stays null when this form does not apply and
+// the join is taken instead.
+//   A: the schema premise's rows (join term and other term); B: the data
+//   premise's rows (nb), its column tcol the conclusion's term; table/d_table:
+//   the key table on the host and the device.
+int conclude_pairs(tid_ctx *ctx, const Rule &R, tid_set *A, tid_set *B, int64_t nb, const int8_t *bvars, int kb,
+                   const std::vector<int32_t> &table, const int32_t *d_table, int tbits, const int8_t *cvars,
+                   int kc, tid_set **out) {
+    *out = nullptr;
+    if (kc != 2 || nb == 0) return TID_OK;
+    const int8_t other = R.on == VA ? VB : VA;  // A's term that is not the join term
+    const int a_pos = cvars[0] == other ? 0 : (cvars[1] == other ? 1 : -1);
+    if (a_pos < 0) return TID_OK;
+    const int8_t tv = cvars[1 - a_pos];
+    int tcol = -1, kcol = -1;
+    for (int c = 0; c < kb; ++c) {
+        if (bvars[c] == tv && tv != R.on) tcol = c;
+        if (bvars[c] == R.on) kcol = c;
+    }
+    int ak = -1, ao = -1;
+    for (int c = 0; c < A->k; ++c) {
+        if (A->vars[c] == R.on) ak = c;
+        if (A->vars[c] == other) ao = c;
+    }
+    int64_t nA = 0;
+    TID_TRY(set_rows_host(A, &nA));
+    if (tcol < 0 || kcol < 0 || ak < 0 || ao < 0 || nA == 0 || nA > PAIR_MAX_SCHEMA_ROWS) return TID_OK;
+    cudaStream_t stream = ctx->stream;
+
+    // the range of the data premise's term, and A's rows on the host
+    Buf rb{ctx};
+    TID_TRY(dev_alloc(ctx, &rb.p, 2 * sizeof(uint32_t)));
+    uint32_t *mm = (uint32_t *)rb.p;
+    TID_TRY_CUDA(cudaMemsetAsync(mm, 0xFF, sizeof(uint32_t), stream), "range");
+    TID_TRY_CUDA(cudaMemsetAsync(mm + 1, 0, sizeof(uint32_t), stream), "range");
+    k_col_range<<<grid_for(nb, 256, 8), 256, 0, stream>>>(B->col[tcol], nb, mm);
+    TID_TRY(launch_check("k_col_range"));
+    uint32_t hmm[2] = {0, 0};
+    TID_TRY_CUDA(cudaMemcpyAsync(hmm, mm, sizeof hmm, cudaMemcpyDeviceToHost, stream), "range");
+    std::vector<int32_t> arows((size_t)nA * A->k);
+    int64_t got = 0;
+    TID_TRY(tid_set_to_host(A, arows.data(), nA, &got));  // synchronises
+    if (hmm[0] > hmm[1]) return TID_OK;
+
+    // A's other terms ranked; the matrix's size decides the form
+    std::vector<int32_t> vals((size_t)nA);
+    for (int64_t i = 0; i < nA; ++i) vals[(size_t)i] = arows[(size_t)i * A->k + ao];
+    std::sort(vals.begin(), vals.end());
+    vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+    const uint64_t na = vals.size(), w = (uint64_t)(hmm[1] - hmm[0]) + 1;
+    const uint64_t nwords = (na * w + 31) / 32, bytes = nwords * sizeof(uint32_t);
+    if (bytes > std::max(PAIR_MIN_BYTES, PAIR_BYTES_PER_ROW * (uint64_t)nb) || bytes > PAIR_MAX_BYTES) return TID_OK;
+
+    // per key slot, the ranks of its schema rows' other terms (ascending)
+    const uint32_t tsize = 1u << tbits;
+    std::vector<std::pair<uint32_t, uint32_t>> hr;
+    hr.reserve((size_t)nA);
+    for (int64_t i = 0; i < nA; ++i) {
+        const int32_t key = arows[(size_t)i * A->k + ak];
+        if (key == 0) continue;  // 0 never joins
+        uint32_t h = home_slot(key, tbits);
+        for (uint32_t probe = 0; probe < tsize && table[h] != key; ++probe) h = (h + 1) & (tsize - 1);
+        if (table[h] != key) continue;
+        const int32_t v = arows[(size_t)i * A->k + ao];
+        hr.emplace_back(h, (uint32_t)(std::lower_bound(vals.begin(), vals.end(), v) - vals.begin()));
+    }
+    std::sort(hr.begin(), hr.end());
+    hr.erase(std::unique(hr.begin(), hr.end()), hr.end());
+    const bool use_mask = a_pos == 1 && na <= 32;
+    // layout: rank values (na) | off (tsize + 1) | ranks | masks (tsize, when used)
+    std::vector<uint32_t> meta(na + tsize + 1 + hr.size() + (use_mask ? tsize : 0), 0u);
+    uint32_t *m_off = meta.data() + na, *m_rank = m_off + tsize + 1, *m_mask = m_rank + hr.size();
+    for (uint64_t r = 0; r < na; ++r) meta[r] = (uint32_t)vals[r];
+    for (size_t j = 0; j < hr.size(); ++j) {
+        m_off[hr[j].first + 1]++;
+        m_rank[j] = hr[j].second;
+        if (use_mask) m_mask[hr[j].first] |= 1u << hr[j].second;
+    }
+    for (uint32_t h = 0; h < tsize; ++h) m_off[h + 1] += m_off[h];
+    Buf mb{ctx};
+    TID_TRY(dev_alloc(ctx, &mb.p, meta.size() * sizeof(uint32_t)));
+    TID_TRY_CUDA(cudaMemcpyAsync(mb.p, meta.data(), meta.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, stream),
+                 "pair ranks");
+    const uint32_t *d_meta = (const uint32_t *)mb.p;
+
+    // the matrix's bits, then its set bits in order as rows
+    Buf bb{ctx};
+    TID_TRY(dev_alloc(ctx, &bb.p, bytes));
+    uint32_t *bits = (uint32_t *)bb.p;
+    TID_TRY_CUDA(cudaMemsetAsync(bits, 0, bytes, stream), "pair bits");
+    const PairBits P{B->col[kcol], B->col[tcol], nb, d_table, tbits,
+                     d_meta + na, d_meta + na + tsize + 1, use_mask ? d_meta + na + tsize + 1 + hr.size() : nullptr,
+                     hmm[0], na, w, a_pos == 0 ? 1 : 0, bits};
+    const unsigned grid = grid_for(ceil_div(nb, BM_RUN), BM_THREADS, 8);
+    if (use_mask) {
+        k_pair_bits_mask<<<grid, BM_THREADS, 0, stream>>>(P);
+        TID_TRY(launch_check("k_pair_bits_mask"));
+    } else {
+        k_pair_bits_list<<<grid, BM_THREADS, 0, stream>>>(P);
+        TID_TRY(launch_check("k_pair_bits_list"));
+    }
+    const int64_t tiles = ceil_div((int64_t)nwords, BM_TILE);
+    const int64_t cpad = (tiles + 1) & ~(int64_t)1;
+    Buf sb{ctx};
+    TID_TRY(dev_alloc(ctx, &sb.p, sizeof(uint32_t) * cpad + sizeof(unsigned long long) * (tiles + 1)));
+    uint32_t *counts = (uint32_t *)sb.p;
+    unsigned long long *offs = (unsigned long long *)(counts + cpad), *d_total = offs + tiles;
+    k_tile_bits<<<(unsigned)tiles, BM_THREADS, 0, stream>>>(bits, (int64_t)nwords, counts);
+    TID_TRY(launch_check("k_tile_bits"));
+    k_scan_tiles<<<1, 1024, 0, stream>>>(counts, tiles, offs, d_total);
+    TID_TRY(launch_check("k_scan_tiles"));
+    unsigned long long total = 0;
+    TID_TRY_CUDA(cudaMemcpyAsync(&total, d_total, sizeof total, cudaMemcpyDeviceToHost, stream), "pair rows");
+    TID_TRY_CUDA(cudaStreamSynchronize(stream), "pair rows");
+    tid_set *C = nullptr;
+    TID_TRY(set_alloc(ctx, 2, cvars, (int64_t)total, &C));
+    int rc = TID_OK;
+    if (total > 0) {
+        k_emit_pairs<<<(unsigned)tiles, BM_THREADS, 0, stream>>>(bits, (int64_t)nwords, offs,
+                                                                  (const int32_t *)d_meta, hmm[0], na, w,
+                                                                  a_pos == 0 ? 1 : 0, C->col[0], C->col[1]);
+        rc = launch_check("k_emit_pairs");
+    }
+    if (rc == TID_OK) rc = set_rows_const(C, (int64_t)total);
+    if (rc == TID_OK) {
+        // valid bounds (sort order) of each column
+        const uint32_t alo = (uint32_t)vals.front() ^ 0x80000000u, ahi = (uint32_t)vals.back() ^ 0x80000000u;
+        C->bounded = true;
+        C->lo[a_pos] = alo;
+        C->hi[a_pos] = ahi;
+        C->lo[1 - a_pos] = hmm[0];
+        C->hi[1 - a_pos] = hmm[1];
+        rc = set_ready(C);
+    }
+    if (rc != TID_OK) {
+        set_free(C);
+        return rc;
+    }
+    *out = C;
+    return TID_OK;
+}
 
 }  // namespace
 
@@ -121,7 +560,7 @@ extern "C" int tid_entail(tid_ctx *ctx, const tid_store *st, int rule, const tid
     std::vector<int32_t> table(tsize, 0);
     for (int32_t key : keys) {  // keys are distinct and positive (0 never joins)
         if (key == 0) continue;
-        uint32_t h = ((uint32_t)key * 0x9E3779B1u) >> (32 - tbits);
+        uint32_t h = home_slot(key, tbits);
         while (table[h] != 0) h = (h + 1) & (tsize - 1);
         table[h] = key;
     }
@@ -162,41 +601,72 @@ extern "C" int tid_entail(tid_ctx *ctx, const tid_store *st, int rule, const tid
     }
     TID_TRY(set_ready(Braw));
     TID_TRY(rows_of(Braw, &sx.res2));
-    // the distinct join terms among them (the paper's #Dist2)
+    // the distinct join terms among them (the paper's #Dist2): the rows mark
+    // their term's slot of the key table, and the marks are counted
     int kcol = 0;
     for (int c = 0; c < kb; ++c)
         if (bvars[c] == R.on) kcol = c;
-    tid_set *K2 = nullptr;
-    const int32_t *kcols[1] = {Braw->col[kcol]};
-    TID_TRY(canonicalize(ctx, kcols, 1, &R.on, sx.res2, true, nullptr, &K2));
-    hold.keep(K2);
-    TID_TRY(rows_of(K2, &sx.dist2));
-    B = Braw;  // rows in store order: the join below needs no order
+    {
+        const uint32_t fwords = (tsize + 31) / 32, fpad = (fwords + 1) & ~1u;
+        Buf fb{ctx};
+        TID_TRY(dev_alloc(ctx, &fb.p, sizeof(uint32_t) * fpad + sizeof(unsigned long long)));
+        uint32_t *flags = (uint32_t *)fb.p;
+        unsigned long long *d_cnt = (unsigned long long *)(flags + fpad);
+        TID_TRY_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t) * fwords, stream), "key marks");
+        if (sx.res2 > 0) {
+            const unsigned grid = grid_for(ceil_div(sx.res2, BM_RUN), BM_THREADS, 8);
+            const size_t fsmem = sizeof(uint32_t) * fwords;
+            if (fsmem <= 32 * 1024)
+                k_mark_keys<true><<<grid, BM_THREADS, fsmem, stream>>>(Braw->col[kcol], sx.res2,
+                                                                       (const int32_t *)d_table, tbits, flags);
+            else
+                k_mark_keys<false><<<grid, BM_THREADS, 0, stream>>>(Braw->col[kcol], sx.res2,
+                                                                    (const int32_t *)d_table, tbits, flags);
+            TID_TRY(launch_check("k_mark_keys"));
+        }
+        k_count_bits<<<1, 1024, 0, stream>>>(flags, fwords, d_cnt);
+        TID_TRY(launch_check("k_count_bits"));
+        unsigned long long cnt = 0;
+        TID_TRY_CUDA(cudaMemcpyAsync(&cnt, d_cnt, sizeof cnt, cudaMemcpyDeviceToHost, stream), "key count");
+        TID_TRY_CUDA(cudaStreamSynchronize(stream), "key count");
+        sx.dist2 = (int64_t)cnt;
+    }
+    B = Braw;  // rows in store order: neither form of step 4 needs an order
 
-    // 4) join on the shared term (the schema side is the small one: a hash join
-    //    with it as the table, rows left in the order written), then the
-    //    conclusion's variables put in canonical order with DISTINCT -- the one
-    //    sort of the rule
-    tid_set *J = nullptr, *C = nullptr;
-    TID_TRY(join_sets(ctx, A, B, TID_JOIN_HASH, &J, false));
-    hold.keep(J);
+    // 4) the join on the shared term, the conclusion's terms kept with
+    //    DISTINCT.  A two-term conclusion with one term from each premise is
+    //    the bit matrix of its distinct pairs, when that is small enough;
+    //    otherwise the join is a hash join with the schema side (the small one)
+    //    as the table, its rows left in the order written, and the conclusion's
+    //    terms are put in canonical order with DISTINCT -- the one sort of the
+    //    rule.
     int8_t cvars[3];
     int kc = 0;
-    const int32_t *ccols[3];
-    Bounds cb{};
     for (int slot = 0; slot < 3; ++slot)
-        if (R.then_var[slot] >= 0) {
+        if (R.then_var[slot] >= 0) cvars[kc++] = R.then_var[slot];
+    tid_set *C = nullptr;
+    TID_TRY(conclude_pairs(ctx, R, A, B, sx.res2, bvars, kb, table, (const int32_t *)d_table, tbits, cvars, kc,
+                           &C));
+    if (C) {
+        hold.keep(C);
+    } else {
+        tid_set *J = nullptr;
+        TID_TRY(join_sets(ctx, A, B, TID_JOIN_HASH, &J, false));
+        hold.keep(J);
+        const int32_t *ccols[3];
+        Bounds cb{};
+        for (int i = 0; i < kc; ++i) {
             int c = 0;
-            while (J->vars[c] != R.then_var[slot]) ++c;
-            ccols[kc] = J->col[c];
-            cb.lo[kc] = J->lo[c];
-            cb.hi[kc] = J->hi[c];
-            cvars[kc++] = R.then_var[slot];
+            while (J->vars[c] != cvars[i]) ++c;
+            ccols[i] = J->col[c];
+            cb.lo[i] = J->lo[c];
+            cb.hi[i] = J->hi[c];
         }
-    int64_t nj = 0;
-    TID_TRY(rows_of(J, &nj));
-    TID_TRY(canonicalize(ctx, ccols, kc, cvars, nj, true, J->bounded ? &cb : nullptr, &C));
-    hold.keep(C);
+        int64_t nj = 0;
+        TID_TRY(rows_of(J, &nj));
+        TID_TRY(canonicalize(ctx, ccols, kc, cvars, nj, true, J->bounded ? &cb : nullptr, &C));
+        hold.keep(C);
+    }
     int64_t rows = 0;
     TID_TRY(rows_of(C, &rows));
 

@@ -1,7 +1,9 @@
 """RDFS entailment (tid_entail) through the C ABI against the CPU oracle,
 bit-exact: the paper's Rule-11 walk-through, all six rules on a university
-store with its schema (conclusions and the paper's step counts), rules whose
-schema premise finds nothing, and bad arguments."""
+store with its schema (conclusions and the paper's step counts), the same
+store with its IDs spread over the int32 range (so two-term conclusions join
+and sort instead of using the pair bit matrix), rules whose schema premise
+finds nothing, and bad arguments."""
 import json
 import os
 
@@ -56,6 +58,30 @@ def test_all_rules_equal_oracle(ctx, orc, n):
         h, stats = tb.tid_entail(ctx, st, rule, vocab)
         got = _host(h)
         want, wstats = orc.entail(st_np.s, st_np.p, st_np.o, rule, vocab)
+        assert got.shape == want.rows.shape and np.array_equal(got, want.rows), rule
+        assert stats == wstats, (rule, stats, wstats)
+    tb.tid_store_free(st)
+
+
+def test_all_rules_sparse_ids_equal_oracle(ctx, orc):
+    """The same store with its IDs spread over the int32 range (order kept).  A
+    two-term conclusion's pair matrix is then far too large, so every rule
+    joins and sorts instead; the results are the oracle's all the same."""
+    base = synth.with_schema(synth.university_store(300_000))
+    vocab = synth.rdfs_vocab(base.meta["subjects"])
+    u = np.unique(np.concatenate([base.s, base.p, base.o]))
+    rng = np.random.default_rng(7)
+    gap = (2**31 - 2) // u.shape[0]
+    new = np.cumsum(rng.integers(1, gap + 1, size=u.shape[0])).astype(np.int64)
+    assert new[-1] < 2**31 - 1 and new[-1] - new[0] > 2**30
+    s, p, o = (new[np.searchsorted(u, c)].astype(np.int32) for c in (base.s, base.p, base.o))
+    assert all(np.isin(v, u) for v in vocab.values())
+    vocab = {k: int(new[np.searchsorted(u, v)]) for k, v in vocab.items()}
+    st = tb.tid_load(ctx, s, p, o)
+    for rule in tb.RULES:
+        h, stats = tb.tid_entail(ctx, st, rule, vocab)
+        got = _host(h)
+        want, wstats = orc.entail(s, p, o, rule, vocab)
         assert got.shape == want.rows.shape and np.array_equal(got, want.rows), rule
         assert stats == wstats, (rule, stats, wstats)
     tb.tid_store_free(st)
