@@ -401,6 +401,40 @@ extern "C" int tid_ctx_inject_alloc_failure(tid_ctx *ctx, int64_t after) {
     return TID_OK;
 }
 
+namespace {
+// *unsorted = 1 if some triple is smaller, in (s, p, o) order, than the one
+// before it
+__global__ void k_spo_unsorted(const int32_t *__restrict__ s, const int32_t *__restrict__ p,
+                               const int32_t *__restrict__ o, int64_t n, int32_t *__restrict__ unsorted) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s0 = s[i - 1], s1 = s[i];
+        if (s0 != s1) {
+            bad = bad || s0 > s1;
+            continue;
+        }
+        const int32_t p0 = p[i - 1], p1 = p[i];
+        bad = bad || p0 > p1 || (p0 == p1 && o[i - 1] > o[i]);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *unsorted = 1;
+}
+}  // namespace
+
+namespace tid {
+bool store_spo_sorted(const tid_store *st) {
+    if (st->spo_sorted < 0) {
+        int32_t h = 1;
+        DeviceGuard g(st->ctx->device);
+        cudaError_t e = cudaMemcpyAsync(&h, st->d_unsorted, sizeof h, cudaMemcpyDeviceToHost, st->ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st->ctx->stream);
+        if (e != cudaSuccess) return false;  // unknown: take the general path
+        st->spo_sorted = h == 0 ? 1 : 0;
+    }
+    return st->spo_sorted == 1;
+}
+}  // namespace tid
+
 extern "C" int tid_load(tid_ctx *ctx, const int32_t *s, const int32_t *p, const int32_t *o,
                         int64_t n, int where, int copy, tid_store **out) {
     clear_error();
@@ -446,6 +480,22 @@ extern "C" int tid_load(tid_ctx *ctx, const int32_t *s, const int32_t *p, const 
     }
     st->aligned16 = ((uintptr_t)st->s % 16 == 0) && ((uintptr_t)st->p % 16 == 0) &&
                     ((uintptr_t)st->o % 16 == 0);
+    // the order check: one read of the store, queued like the copies
+    int rc = dev_alloc(ctx, (void **)&st->d_unsorted, sizeof(int32_t));
+    if (rc == TID_OK) {
+        cudaError_t e = cudaMemsetAsync(st->d_unsorted, 0, sizeof(int32_t), ctx->stream);
+        if (e != cudaSuccess) rc = fail_cuda(e, "tid_load");
+    }
+    if (rc == TID_OK && n > 1) {
+        k_spo_unsorted<<<grid_for(n, 256, 8), 256, 0, ctx->stream>>>(st->s, st->p, st->o, n, st->d_unsorted);
+        rc = launch_check("k_spo_unsorted");
+    }
+    if (rc != TID_OK) {
+        if (st->d_unsorted) dev_free(ctx, st->d_unsorted);
+        if (st->owned) dev_free(ctx, st->owned);
+        delete st;
+        return rc;
+    }
     *out = st;
     return TID_OK;
 }
@@ -465,6 +515,7 @@ extern "C" int tid_store_free(tid_store *st) {
     clear_error();
     if (!st) return TID_OK;
     DeviceGuard g(st->ctx->device);
+    if (st->d_unsorted) dev_free(st->ctx, st->d_unsorted);
     if (st->owned) dev_free(st->ctx, st->owned);
     delete st;
     return TID_OK;

@@ -450,7 +450,7 @@ k_tile_write(Row row, int64_t n, int k_out, OutCols out, int64_t cap, const uint
 //
 // One cooperative launch.  Phase A: warps draw runs of BC_DRAW steps of 1024
 // rows from one counter; for step j a warp tests rows 1024 j + 32 w + lane
-// (w = 0..31, eight tests in flight per lane), keeps the 32 ballots as the
+// (w = 0..31, BC_INFLIGHT tests in flight per lane), keeps the 32 ballots as the
 // step's keep words and its count, and adds the count to the total of the CTA
 // whose fixed range of steps holds it.  Bounded grid barrier.  Phase C: CTA
 // c's offset is the sum of the earlier CTAs' totals; it block-scans its steps'
@@ -463,6 +463,7 @@ constexpr int BC_THREADS = 256;
 constexpr int BC_WARPS = BC_THREADS / 32;
 constexpr int BC_STEP = 1024;      // rows per warp step (32 keep words)
 constexpr int BC_DRAW = 8;         // steps per draw from the counter
+constexpr int BC_INFLIGHT = 16;    // rows a lane tests at once (their loads in flight together)
 constexpr int BC_CHUNK = BC_THREADS;  // steps scanned per round of phase C
 constexpr int BC_TICKET = 32;      // step counter's word in the control block
 constexpr size_t BC_CTL_BYTES = 256;
@@ -478,7 +479,7 @@ struct BcScratch {
 };
 
 template <class Row>
-__global__ void __launch_bounds__(BC_THREADS)
+__global__ void __launch_bounds__(BC_THREADS, 3)
 k_compact_bitmap(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_t *__restrict__ d_rows,
                  int64_t *__restrict__ h_rows, BcScratch sc, uint32_t *__restrict__ mm) {
     __shared__ uint16_t s_stage[BC_WARPS][BC_STEP];
@@ -504,15 +505,15 @@ k_compact_bitmap(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_
             uint32_t word = 0;
             unsigned c = 0;
 #pragma unroll 1
-            for (int w0 = 0; w0 < 32; w0 += 8) {
-                bool kp[8];
+            for (int w0 = 0; w0 < 32; w0 += BC_INFLIGHT) {
+                bool kp[BC_INFLIGHT];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {  // rows past n test row n - 1 (in bounds, no branch) and drop it
+                for (int u = 0; u < BC_INFLIGHT; ++u) {  // rows past n test row n - 1 (in bounds, no branch) and drop it
                     const int64_t r = base + (int64_t)(w0 + u) * 32;
                     kp[u] = row.keep(r < n ? r : n - 1) && r < n;
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
+                for (int u = 0; u < BC_INFLIGHT; ++u) {
                     const unsigned b = __ballot_sync(0xffffffffu, kp[u]);
                     if ((int)lane == w0 + u) word = b;
                     c += __popc(b);

@@ -63,8 +63,6 @@ __global__ void k_fill_i32(int32_t *__restrict__ out, int64_t n, int32_t v) {
 }
 
 constexpr int BM_THREADS = 256;
-constexpr int BM_WORDS = 8;                     // bit-matrix words per thread
-constexpr int BM_TILE = BM_THREADS * BM_WORDS;  // words per tile
 constexpr uint32_t KEY_HASH = 0x9E3779B1u;      // multiplicative (Knuth) hash of the key table
 
 __host__ __device__ __forceinline__ uint32_t home_slot(int32_t key, int tbits) {
@@ -88,14 +86,19 @@ __device__ __forceinline__ int find_slot(const int32_t *__restrict__ table, int 
 
 __device__ __forceinline__ uint32_t sort_order(int32_t x) { return (uint32_t)x ^ 0x80000000u; }
 
-constexpr int BM_RUN = 16;  // consecutive rows per thread in the marking kernels
+constexpr int BM_U = 4;  // rows per lane per step of the marking kernels (loads in flight)
+
+// A warp's step: rows i0 + 32 u + lane, u < BM_U, i0 warp-uniform (so every
+// lane takes part in the shuffles below).
+__device__ __forceinline__ int64_t bm_first() {
+    return (int64_t)blockIdx.x * (BM_THREADS * BM_U) + (int64_t)(threadIdx.x >> 5) * (32 * BM_U);
+}
+__device__ __forceinline__ int64_t bm_stride() { return (int64_t)gridDim.x * (BM_THREADS * BM_U); }
 
 // flags gets one bit per table slot whose key occurs in key[0, n): the distinct
-// join terms of the data premise's rows.  Each thread takes runs of BM_RUN
-// consecutive rows and sets a slot's bit only when the row's slot differs
-// from its previous row's and the bit is still clear, so rows of a repeated
-// term cost a read.  Bits collect in shared memory when SMEM, else in global
-// memory directly.
+// join terms of the data premise's rows.  A lane skips a row whose slot equals
+// the previous lane's, and sets a bit only while it is clear.  Bits collect in
+// shared memory when SMEM, else in global memory directly.
 template <bool SMEM>
 __global__ void __launch_bounds__(BM_THREADS) k_mark_keys(const int32_t *__restrict__ key, int64_t n,
                                                           const int32_t *__restrict__ table, int tbits,
@@ -107,16 +110,22 @@ __global__ void __launch_bounds__(BM_THREADS) k_mark_keys(const int32_t *__restr
         __syncthreads();
     }
     volatile uint32_t *f = SMEM ? s_f : flags;
-    const int64_t runs = (n + BM_RUN - 1) / BM_RUN;
-    for (int64_t q = (int64_t)blockIdx.x * BM_THREADS + threadIdx.x; q < runs; q += (int64_t)gridDim.x * BM_THREADS) {
-        int last = -1;
-        const int64_t e = min(n, (q + 1) * BM_RUN);
-        for (int64_t i = q * BM_RUN; i < e; ++i) {
-            const int h = find_slot(table, tbits, key[i]);
-            if (h < 0 || h == last) continue;
-            last = h;
-            const uint32_t b = 1u << (h & 31);
-            if (!(f[h >> 5] & b)) atomicOr((uint32_t *)f + (h >> 5), b);
+    const unsigned lane = threadIdx.x & 31;
+    for (int64_t i0 = bm_first(); i0 < n; i0 += bm_stride()) {
+        int32_t x[BM_U];
+#pragma unroll
+        for (int u = 0; u < BM_U; ++u) {
+            const int64_t i = i0 + 32 * u + lane;
+            x[u] = i < n ? key[i] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < BM_U; ++u) {
+            const int h = find_slot(table, tbits, x[u]);
+            const int hp = __shfl_up_sync(0xffffffffu, h, 1);
+            if (h >= 0 && (lane == 0 || hp != h)) {
+                const uint32_t b = 1u << (h & 31);
+                if (!(f[h >> 5] & b)) atomicOr((uint32_t *)f + (h >> 5), b);
+            }
         }
     }
     if (SMEM) {
@@ -129,10 +138,11 @@ __global__ void __launch_bounds__(BM_THREADS) k_mark_keys(const int32_t *__restr
 // The conclusion's distinct pairs as the set bits of a matrix.  A data-premise
 // row (join term, term t) joined with the schema rows of that join term gives
 // the pairs (r, t) for A's other terms r.  r is ranked among A's distinct
-// values of that term (ascending) and t is taken as d = order(t) - vmin.  The
-// pair is bit r * w + d when A's term comes first in the conclusion, d * na + r
-// when t does.  Matrix rows thus follow the first term, bits within a row the
-// second, and the set bits in ascending order are the canonical distinct rows.
+// values of that term (ascending) and t is taken as d = order(t) - vmin.  Rows
+// of the matrix follow the conclusion's first term and are 2^lg bits wide
+// (the second term's span rounded up to a power of two): the pair is bit
+// (r << lg) + d when A's term comes first, (d << lg) + r when t does.  The set
+// bits in ascending order are the canonical distinct rows.
 struct PairBits {
     const int32_t *key, *val;  // data-premise rows: join term, conclusion term
     int64_t n;
@@ -140,94 +150,107 @@ struct PairBits {
     int tbits;
     const uint32_t *off;    // slot h: A's ranks are rank[off[h] .. off[h + 1])
     const uint32_t *rank;
-    const uint32_t *kmask;  // slot h: the same ranks as a mask (t first, na <= 32)
+    const uint32_t *kmask;  // slot h: the same ranks as a mask (t first, 2^lg <= 32)
     uint32_t vmin;
-    uint64_t na, w;  // A's distinct terms; width of t's range
+    int lg;
     int a_first;
     uint32_t *bits;
 };
 
-// General form: one atomic OR per (row, rank).  A thread takes BM_RUN
-// consecutive rows and skips a row whose pairs repeat the previous row's.
+// General form: one atomic OR per (row, rank); a lane skips a row equal, in
+// slot and term, to the previous lane's.
 __global__ void __launch_bounds__(BM_THREADS) k_pair_bits_list(PairBits P) {
-    const int64_t runs = (P.n + BM_RUN - 1) / BM_RUN;
-    for (int64_t q = (int64_t)blockIdx.x * BM_THREADS + threadIdx.x; q < runs; q += (int64_t)gridDim.x * BM_THREADS) {
-        int last_h = -1;
-        uint64_t last_d = 0;
-        const int64_t e = min(P.n, (q + 1) * BM_RUN);
-        for (int64_t i = q * BM_RUN; i < e; ++i) {
-            const int h = find_slot(P.table, P.tbits, P.key[i]);
-            if (h < 0) continue;
-            const uint64_t d = sort_order(P.val[i]) - P.vmin;
-            if (h == last_h && d == last_d) continue;
-            last_h = h;
-            last_d = d;
+    const unsigned lane = threadIdx.x & 31;
+    for (int64_t i0 = bm_first(); i0 < P.n; i0 += bm_stride()) {
+        int32_t x[BM_U], t[BM_U];
+#pragma unroll
+        for (int u = 0; u < BM_U; ++u) {
+            const int64_t i = i0 + 32 * u + lane;
+            x[u] = i < P.n ? P.key[i] : 0;
+            t[u] = i < P.n ? P.val[i] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < BM_U; ++u) {
+            const int h = find_slot(P.table, P.tbits, x[u]);
+            const uint32_t d = sort_order(t[u]) - P.vmin;
+            const int hp = __shfl_up_sync(0xffffffffu, h, 1);
+            const uint32_t dp = __shfl_up_sync(0xffffffffu, d, 1);
+            if (h < 0 || (lane > 0 && hp == h && dp == d)) continue;
             for (uint32_t j = P.off[h]; j < P.off[h + 1]; ++j) {
                 const uint64_t r = P.rank[j];
-                const uint64_t g = P.a_first ? r * P.w + d : d * P.na + r;
+                const uint64_t g = P.a_first ? (r << P.lg) + d : ((uint64_t)d << P.lg) + r;
                 atomicOr(P.bits + (g >> 5), 1u << (g & 31));
             }
         }
     }
 }
 
-// t first and na <= 32: a row's ranks are one mask, shifted to bit d * na (at
-// most two words).  A thread ORs the masks of its run's consecutive rows that
-// fall in the same word pair and writes each pair once.
+// t first and rows of at most 32 bits: a row's ranks are one mask within one
+// word.  Lanes holding consecutive rows of the same word OR their masks (a
+// segmented scan across the warp) and the last lane of each run writes it.
 __global__ void __launch_bounds__(BM_THREADS) k_pair_bits_mask(PairBits P) {
-    const int64_t runs = (P.n + BM_RUN - 1) / BM_RUN;
-    for (int64_t q = (int64_t)blockIdx.x * BM_THREADS + threadIdx.x; q < runs; q += (int64_t)gridDim.x * BM_THREADS) {
-        uint64_t cur = ~0ull, acc = 0;  // word index and the bits of words cur, cur + 1
-        const int64_t e = min(P.n, (q + 1) * BM_RUN);
-        for (int64_t i = q * BM_RUN; i < e; ++i) {
-            const int h = find_slot(P.table, P.tbits, P.key[i]);
-            if (h < 0) continue;
-            const uint64_t g = (uint64_t)(sort_order(P.val[i]) - P.vmin) * P.na;
-            const uint64_t word = g >> 5;
-            const uint64_t m = (uint64_t)P.kmask[h] << (g & 31);
-            if (word != cur) {
-                if (acc & 0xFFFFFFFFull) atomicOr(P.bits + cur, (uint32_t)acc);
-                if (acc >> 32) atomicOr(P.bits + cur + 1, (uint32_t)(acc >> 32));
-                cur = word;
-                acc = 0;
-            }
-            acc |= m;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned le = lane == 31 ? 0xFFFFFFFFu : (2u << lane) - 1u;  // lanes <= this one
+    for (int64_t i0 = bm_first(); i0 < P.n; i0 += bm_stride()) {
+        int32_t x[BM_U], t[BM_U];
+#pragma unroll
+        for (int u = 0; u < BM_U; ++u) {
+            const int64_t i = i0 + 32 * u + lane;
+            x[u] = i < P.n ? P.key[i] : 0;
+            t[u] = i < P.n ? P.val[i] : 0;
         }
-        if (acc & 0xFFFFFFFFull) atomicOr(P.bits + cur, (uint32_t)acc);
-        if (acc >> 32) atomicOr(P.bits + cur + 1, (uint32_t)(acc >> 32));
+#pragma unroll
+        for (int u = 0; u < BM_U; ++u) {
+            const int h = find_slot(P.table, P.tbits, x[u]);
+            const uint64_t g = (uint64_t)(sort_order(t[u]) - P.vmin) << P.lg;
+            const uint64_t word = h >= 0 ? g >> 5 : ~0ull;
+            uint32_t acc = h >= 0 ? P.kmask[h] << (g & 31) : 0u;
+            const uint64_t wp = __shfl_up_sync(0xffffffffu, word, 1);
+            const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || wp != word);
+            const int start = 31 - __clz(heads & le);
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(0xffffffffu, acc, d);
+                if ((int)lane - d >= start) acc |= o;
+            }
+            const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+            if (h >= 0 && tail) atomicOr(P.bits + word, acc);
+        }
     }
 }
 
-// counts[t] = set bits of tile t (BM_TILE words; thread i owns words
-// [i * BM_WORDS, (i + 1) * BM_WORDS) of the tile)
-__global__ void __launch_bounds__(BM_THREADS) k_tile_bits(const uint32_t *__restrict__ bits, int64_t nwords,
-                                                          uint32_t *__restrict__ counts) {
-    __shared__ uint32_t s_w[BM_THREADS / 32];
-    const int64_t w0 = (int64_t)blockIdx.x * BM_TILE + (int64_t)threadIdx.x * BM_WORDS;
+// Reading the matrix out: segment s is words [s R 32, (s + 1) R 32), R rounds
+// of 32 words, one warp per segment (a round's words one per lane).
+__device__ __forceinline__ int64_t seg_of_warp() { return (int64_t)blockIdx.x * (BM_THREADS / 32) + (threadIdx.x >> 5); }
+
+// counts[s] = set bits of segment s
+__global__ void __launch_bounds__(BM_THREADS) k_seg_bits(const uint32_t *__restrict__ bits, int64_t nwords, int R,
+                                                         int64_t nseg, uint32_t *__restrict__ counts) {
+    const int64_t s = seg_of_warp();
+    if (s >= nseg) return;
+    const unsigned lane = threadIdx.x & 31;
+    const int64_t w0 = s * R * 32 + lane;
     uint32_t c = 0;
-#pragma unroll
-    for (int j = 0; j < BM_WORDS; ++j)
-        if (w0 + j < nwords) c += __popc(bits[w0 + j]);
+#pragma unroll 8
+    for (int r = 0; r < R; ++r) {
+        const int64_t w = w0 + (int64_t)r * 32;
+        c += w < nwords ? __popc(bits[w]) : 0u;
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < BM_THREADS / 32; ++w) t += s_w[w];
-        counts[blockIdx.x] = t;
-    }
+    if (lane == 0) counts[s] = c;
 }
 
-// offs[t] = sum of counts[0, t) (64-bit), *total = sum of all (one CTA: each
-// thread scans a contiguous share)
-__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *__restrict__ counts, int64_t tiles,
-                                                     unsigned long long *__restrict__ offs,
-                                                     unsigned long long *__restrict__ total) {
+// offs[s] = sum of counts[0, s) (64-bit), *total = sum of all (one CTA: each
+// thread sums a contiguous share, eight loads in flight)
+__global__ void __launch_bounds__(1024) k_scan_segs(const uint32_t *__restrict__ counts, int64_t nseg,
+                                                    unsigned long long *__restrict__ offs,
+                                                    unsigned long long *__restrict__ total) {
     __shared__ unsigned long long s_w[32];
-    const int64_t per = (tiles + 1023) / 1024;
-    const int64_t b = min(tiles, (int64_t)threadIdx.x * per), e = min(tiles, b + per);
+    const int64_t per = (nseg + 1023) / 1024;
+    const int64_t b = min(nseg, (int64_t)threadIdx.x * per), e = min(nseg, b + per);
     unsigned long long s = 0;
+#pragma unroll 8
     for (int64_t t = b; t < e; ++t) s += counts[t];
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long x = s;
@@ -251,55 +274,73 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t *__restrict_
     }
     __syncthreads();
     unsigned long long run = s_w[warp] + x - s;
+#pragma unroll 8
     for (int64_t t = b; t < e; ++t) {
+        const uint32_t c = counts[t];
         offs[t] = run;
-        run += counts[t];
+        run += c;
     }
 }
 
-// The set bits of each tile, in order, as rows (first term, second term) at
-// the tile's offset.
-__global__ void __launch_bounds__(BM_THREADS) k_emit_pairs(const uint32_t *__restrict__ bits, int64_t nwords,
-                                                           const unsigned long long *__restrict__ offs,
-                                                           const int32_t *__restrict__ rankval, uint32_t vmin,
-                                                           uint64_t na, uint64_t w, int a_first,
-                                                           int32_t *__restrict__ out0, int32_t *__restrict__ out1) {
-    __shared__ uint32_t s_w[BM_THREADS / 32];
-    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t w0 = (int64_t)blockIdx.x * BM_TILE + (int64_t)threadIdx.x * BM_WORDS;
-    uint32_t v[BM_WORDS];
-    uint32_t c = 0;
-#pragma unroll
-    for (int j = 0; j < BM_WORDS; ++j) {
-        v[j] = w0 + j < nwords ? bits[w0 + j] : 0u;
-        c += __popc(v[j]);
+struct PairOut {  // decoding a set bit into the conclusion's row
+    const int32_t *rankval;  // A's distinct terms, ascending
+    uint32_t vmin;
+    int lg;
+    int a_first;
+    int32_t *out0, *out1;
+    __device__ __forceinline__ void put(uint64_t g, uint64_t pos) const {
+        const uint64_t hi = g >> lg, lo = g & ((1ull << lg) - 1ull);
+        const uint64_t r = a_first ? hi : lo, d = a_first ? lo : hi;
+        const int32_t a = rankval[r], t = (int32_t)((vmin + (uint32_t)d) ^ 0x80000000u);
+        out0[pos] = a_first ? a : t;
+        out1[pos] = a_first ? t : a;
     }
-    uint32_t x = c;
+};
+
+// The set bits of each segment, in order, as rows at the segment's offset.  A
+// round whose words hold few bits (at most two each) is written lane by lane,
+// the lanes' rows being consecutive; a denser round word by word, the word's
+// bits one per lane, so the stores are coalesced either way.
+__global__ void __launch_bounds__(BM_THREADS) k_emit_pairs(const uint32_t *__restrict__ bits, int64_t nwords, int R,
+                                                           int64_t nseg, const unsigned long long *__restrict__ offs,
+                                                           PairOut O) {
+    const int64_t s = seg_of_warp();
+    if (s >= nseg) return;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t pos = offs[s];
+    for (int r = 0; r < R; ++r) {
+        const int64_t wb = (s * R + r) * 32;  // the round's first word
+        if (wb >= nwords) break;
+        const int64_t w = wb + lane;
+        uint32_t v = w < nwords ? bits[w] : 0u;
+        const uint32_t c = __popc(v);
+        uint32_t x = c;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if ((int)lane >= d) x += y;
-    }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    uint32_t before = 0;
-    for (unsigned i = 0; i < warp; ++i) before += s_w[i];
-    uint64_t pos = offs[blockIdx.x] + before + x - c;
-    const uint64_t row_w = a_first ? w : na;  // bits per matrix row
-#pragma unroll
-    for (int j = 0; j < BM_WORDS; ++j) {
-        uint32_t m = v[j];
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            const uint64_t g = (uint64_t)(w0 + j) * 32 + (uint64_t)b;
-            const uint64_t hi = g / row_w, lo = g - hi * row_w;
-            const uint64_t r = a_first ? hi : lo, d = a_first ? lo : hi;
-            const int32_t a = rankval[r], t = (int32_t)((vmin + (uint32_t)d) ^ 0x80000000u);
-            out0[pos] = a_first ? a : t;
-            out1[pos] = a_first ? t : a;
-            ++pos;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if ((int)lane >= d) x += y;
         }
+        const uint64_t mine = pos + x - c;
+        const uint32_t tot = __shfl_sync(0xffffffffu, x, 31);
+        if (__any_sync(0xffffffffu, c > 2)) {
+            unsigned nz = __ballot_sync(0xffffffffu, v != 0);
+            while (nz) {
+                const int L = __ffs(nz) - 1;
+                nz &= nz - 1;
+                const uint32_t wv = __shfl_sync(0xffffffffu, v, L);
+                const uint64_t b0 = __shfl_sync(0xffffffffu, mine, L);
+                if ((wv >> lane) & 1u) O.put((uint64_t)(wb + L) * 32 + lane, b0 + __popc(wv & lt));
+            }
+        } else {
+            uint64_t at = mine;
+            while (v) {
+                const int b = __ffs(v) - 1;
+                v &= v - 1;
+                O.put((uint64_t)w * 32 + b, at++);
+            }
+        }
+        pos += tot;
     }
 }
 
@@ -418,7 +459,13 @@ int conclude_pairs(tid_ctx *ctx, const Rule &R, tid_set *A, tid_set *B, int64_t 
     std::sort(vals.begin(), vals.end());
     vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
     const uint64_t na = vals.size(), w = (uint64_t)(hmm[1] - hmm[0]) + 1;
-    const uint64_t nwords = (na * w + 31) / 32, bytes = nwords * sizeof(uint32_t);
+    const uint64_t nrows = a_pos == 0 ? na : w, width = a_pos == 0 ? w : na;  // matrix rows, bits per row
+    int lg = 0;
+    while ((1ull << lg) < width) ++lg;
+    int lr = 0;
+    while ((1ull << lr) < nrows) ++lr;
+    if (lg + lr > 40) return TID_OK;  // far beyond the size limit below
+    const uint64_t nwords = ((nrows << lg) + 31) / 32, bytes = nwords * sizeof(uint32_t);
     if (bytes > std::max(PAIR_MIN_BYTES, PAIR_BYTES_PER_ROW * (uint64_t)nb) || bytes > PAIR_MAX_BYTES) return TID_OK;
 
     // per key slot, the ranks of its schema rows' other terms (ascending)
@@ -436,7 +483,7 @@ int conclude_pairs(tid_ctx *ctx, const Rule &R, tid_set *A, tid_set *B, int64_t 
     }
     std::sort(hr.begin(), hr.end());
     hr.erase(std::unique(hr.begin(), hr.end()), hr.end());
-    const bool use_mask = a_pos == 1 && na <= 32;
+    const bool use_mask = a_pos == 1 && lg <= 5;  // a row's ranks fit one word
     // layout: rank values (na) | off (tsize + 1) | ranks | masks (tsize, when used)
     std::vector<uint32_t> meta(na + tsize + 1 + hr.size() + (use_mask ? tsize : 0), 0u);
     uint32_t *m_off = meta.data() + na, *m_rank = m_off + tsize + 1, *m_mask = m_rank + hr.size();
@@ -460,8 +507,8 @@ int conclude_pairs(tid_ctx *ctx, const Rule &R, tid_set *A, tid_set *B, int64_t 
     TID_TRY_CUDA(cudaMemsetAsync(bits, 0, bytes, stream), "pair bits");
     const PairBits P{B->col[kcol], B->col[tcol], nb, d_table, tbits,
                      d_meta + na, d_meta + na + tsize + 1, use_mask ? d_meta + na + tsize + 1 + hr.size() : nullptr,
-                     hmm[0], na, w, a_pos == 0 ? 1 : 0, bits};
-    const unsigned grid = grid_for(ceil_div(nb, BM_RUN), BM_THREADS, 8);
+                     hmm[0], lg, a_pos == 0 ? 1 : 0, bits};
+    const unsigned grid = grid_for(nb, BM_THREADS * BM_U, 8);
     if (use_mask) {
         k_pair_bits_mask<<<grid, BM_THREADS, 0, stream>>>(P);
         TID_TRY(launch_check("k_pair_bits_mask"));
@@ -469,16 +516,19 @@ int conclude_pairs(tid_ctx *ctx, const Rule &R, tid_set *A, tid_set *B, int64_t 
         k_pair_bits_list<<<grid, BM_THREADS, 0, stream>>>(P);
         TID_TRY(launch_check("k_pair_bits_list"));
     }
-    const int64_t tiles = ceil_div((int64_t)nwords, BM_TILE);
-    const int64_t cpad = (tiles + 1) & ~(int64_t)1;
+    // segments of R rounds of 32 words, at most 2^16 of them (one warp each)
+    const int rounds = (int)std::max<int64_t>(8, ceil_div((int64_t)nwords, (int64_t)32 << 16));
+    const int64_t nseg = ceil_div((int64_t)nwords, (int64_t)rounds * 32);
+    const unsigned seg_ctas = (unsigned)ceil_div(nseg, BM_THREADS / 32);
+    const int64_t cpad = (nseg + 1) & ~(int64_t)1;
     Buf sb{ctx};
-    TID_TRY(dev_alloc(ctx, &sb.p, sizeof(uint32_t) * cpad + sizeof(unsigned long long) * (tiles + 1)));
+    TID_TRY(dev_alloc(ctx, &sb.p, sizeof(uint32_t) * cpad + sizeof(unsigned long long) * (nseg + 1)));
     uint32_t *counts = (uint32_t *)sb.p;
-    unsigned long long *offs = (unsigned long long *)(counts + cpad), *d_total = offs + tiles;
-    k_tile_bits<<<(unsigned)tiles, BM_THREADS, 0, stream>>>(bits, (int64_t)nwords, counts);
-    TID_TRY(launch_check("k_tile_bits"));
-    k_scan_tiles<<<1, 1024, 0, stream>>>(counts, tiles, offs, d_total);
-    TID_TRY(launch_check("k_scan_tiles"));
+    unsigned long long *offs = (unsigned long long *)(counts + cpad), *d_total = offs + nseg;
+    k_seg_bits<<<seg_ctas, BM_THREADS, 0, stream>>>(bits, (int64_t)nwords, rounds, nseg, counts);
+    TID_TRY(launch_check("k_seg_bits"));
+    k_scan_segs<<<1, 1024, 0, stream>>>(counts, nseg, offs, d_total);
+    TID_TRY(launch_check("k_scan_segs"));
     unsigned long long total = 0;
     TID_TRY_CUDA(cudaMemcpyAsync(&total, d_total, sizeof total, cudaMemcpyDeviceToHost, stream), "pair rows");
     TID_TRY_CUDA(cudaStreamSynchronize(stream), "pair rows");
@@ -486,9 +536,8 @@ int conclude_pairs(tid_ctx *ctx, const Rule &R, tid_set *A, tid_set *B, int64_t 
     TID_TRY(set_alloc(ctx, 2, cvars, (int64_t)total, &C));
     int rc = TID_OK;
     if (total > 0) {
-        k_emit_pairs<<<(unsigned)tiles, BM_THREADS, 0, stream>>>(bits, (int64_t)nwords, offs,
-                                                                  (const int32_t *)d_meta, hmm[0], na, w,
-                                                                  a_pos == 0 ? 1 : 0, C->col[0], C->col[1]);
+        const PairOut O{(const int32_t *)d_meta, hmm[0], lg, a_pos == 0 ? 1 : 0, C->col[0], C->col[1]};
+        k_emit_pairs<<<seg_ctas, BM_THREADS, 0, stream>>>(bits, (int64_t)nwords, rounds, nseg, offs, O);
         rc = launch_check("k_emit_pairs");
     }
     if (rc == TID_OK) rc = set_rows_const(C, (int64_t)total);
@@ -614,7 +663,7 @@ extern "C" int tid_entail(tid_ctx *ctx, const tid_store *st, int rule, const tid
         unsigned long long *d_cnt = (unsigned long long *)(flags + fpad);
         TID_TRY_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t) * fwords, stream), "key marks");
         if (sx.res2 > 0) {
-            const unsigned grid = grid_for(ceil_div(sx.res2, BM_RUN), BM_THREADS, 8);
+            const unsigned grid = grid_for(sx.res2, BM_THREADS * BM_U, 8);
             const size_t fsmem = sizeof(uint32_t) * fwords;
             if (fsmem <= 32 * 1024)
                 k_mark_keys<true><<<grid, BM_THREADS, fsmem, stream>>>(Braw->col[kcol], sx.res2,

@@ -104,14 +104,55 @@ int bind_set(tid_ctx *ctx, const tid_store *st, const tid_pattern &pat, const ti
     if (rc == TID_OK) rc = set_ready(tmp);
     int64_t m = 0;
     if (rc == TID_OK) rc = set_rows_host(tmp, &m);
-    if (rc == TID_OK) {
-        const int32_t *cols[TID_MAX_COLS];
-        Bounds b{};
-        for (int c = 0; c < k; ++c) {
-            cols[c] = tmp->col[c];
-            b.lo[c] = hb[c];
-            b.hi[c] = hb[TID_MAX_COLS + c];
+    const int32_t *cols[TID_MAX_COLS];
+    Bounds b{};
+    for (int c = 0; c < k; ++c) {
+        cols[c] = tmp->col[c];
+        b.lo[c] = hb[c];
+        b.hi[c] = hb[TID_MAX_COLS + c];
+    }
+    // In a store sorted by (s, p, o) the hits, in index order, are sorted by
+    // their variable slots in slot order (the bound slots are constant) when
+    // no anonymous slot comes before a variable -- the set's canonical order.
+    // The compaction keeps index order, so no sort is needed: the rows are
+    // the result, or (an anonymous slot last) one pass drops adjacent repeats.
+    bool in_order = rc == TID_OK;
+    {
+        const int32_t key[3] = {pat.s, pat.p, pat.o};
+        bool seen_anon = false;
+        for (int j = 0; j < 3; ++j) {
+            if (pat.var[j] >= 0) in_order = in_order && !seen_anon;
+            else if (key[j] == 0) seen_anon = true;
         }
+    }
+    if (in_order) in_order = store_spo_sorted(st);
+    if (in_order && !anon) {
+        tmp->bounded = m > 0;
+        for (int c = 0; c < k; ++c) {
+            tmp->lo[c] = b.lo[c];
+            tmp->hi[c] = b.hi[c];
+        }
+        if (mm) dev_free(ctx, mm);
+        *out = tmp;
+        return TID_OK;
+    }
+    if (in_order) {
+        tid_set *o = nullptr;
+        const int32_t *none[TID_MAX_COLS] = {nullptr};
+        rc = set_alloc(ctx, k, vars, m, &o);
+        if (rc == TID_OK) rc = merge_unique(ctx, cols, m, none, 0, k, o);
+        if (rc == TID_OK) rc = set_ready(o);
+        if (rc == TID_OK) {
+            o->bounded = m > 0;
+            for (int c = 0; c < k; ++c) {
+                o->lo[c] = b.lo[c];
+                o->hi[c] = b.hi[c];
+            }
+            *out = o;
+        } else if (o) {
+            set_free(o);
+        }
+    } else if (rc == TID_OK) {
         // distinct triples give distinct rows unless a "?" slot is anonymous
         rc = canonicalize(ctx, cols, k, vars, m, anon, &b, out);
     }

@@ -121,6 +121,12 @@ struct tid_store {
     const int32_t *s = nullptr, *p = nullptr, *o = nullptr;
     void *owned = nullptr;  // single allocation holding the three columns, or null
     bool aligned16 = false; // all three columns 16-byte aligned
+    // Whether the triples are in (s, p, o) order (int32 order, repeats
+    // allowed): *d_unsorted is set at load by a check kernel when some triple
+    // follows a larger one; `spo_sorted` caches it on the host once read
+    // (-1: not read yet).
+    int32_t *d_unsorted = nullptr;
+    mutable int spo_sorted = -1;
 };
 
 struct tid_set {
@@ -170,6 +176,7 @@ void set_free(tid_set *set);      // tid_set_free without clearing the error mes
 // *d_rows on the device) inside sb's allocations; takes one reference on sb.
 int set_view(tid_ctx *ctx, tid::SharedBlock *sb, int32_t *col, int64_t *d_rows, int64_t rows, tid_set **out);
 int check_ctx_error(tid_ctx *ctx); // reads and clears the kernel error word
+bool store_spo_sorted(const tid_store *st);  // triples in (s, p, o) order (waits for the load's check)
 int launch_check(const char *what);
 
 // kernels (match.cu)

@@ -107,6 +107,48 @@ def test_bind_with_fused_filters_tiny_store(ctx, orc):
     tb.tid_store_free(st)
 
 
+@pytest.mark.parametrize("order", ["spo", "shuffled", "one_swap"])
+def test_bind_store_order(ctx, orc, order):
+    """In a store sorted by (s, p, o), bind keeps index order (no sort) when no
+    anonymous slot precedes a variable, and drops adjacent repeats when one
+    follows them.  The same triples shuffled, or with one adjacent pair
+    swapped (the load's order check must see a single inversion), take the
+    sorting path.  Every pattern shape, with and without a fused filter, gives
+    the oracle's rows."""
+    rng = np.random.default_rng(11)
+    n = 200_000
+    keys = np.unique(np.stack([rng.integers(1, 3000, n), rng.integers(1, 9, n), rng.integers(1, 3000, n)], 1),
+                     axis=0)
+    if order == "shuffled":
+        keys = keys[rng.permutation(len(keys))]
+    elif order == "one_swap":
+        i = len(keys) // 2
+        keys[[i, i + 1]] = keys[[i + 1, i]]
+    S, P, O = (keys[:, j].astype(np.int32).copy() for j in range(3))
+    st = _store(ctx, S, P, O)
+    X, Y, Z = 0, 1, 2
+    cases = [((0, 3, 0), (X, -1, Y), []),
+             ((0, 3, 0), (X, -1, Y), [(Y, "lt", 1500)]),
+             ((0, 0, 0), (X, Y, Z), []),
+             ((0, 0, 0), (X, -1, Y), []),                    # anonymous between the variables
+             ((0, 0, 0), (X, Y, -1), []),                    # anonymous last: adjacent repeats
+             ((0, 0, 0), (X, Y, -1), [(X, "ge", 100)]),
+             ((0, 0, 0), (-1, X, Y), []),                    # anonymous first
+             ((0, 5, 0), (X, -1, X), []),                    # repeated variable
+             ((7, 0, 0), (-1, X, Y), []),
+             ((0, 0, 11), (X, Y, -1), []),
+             ((0, 4, 0), (Y, -1, X), [])]                    # column order follows the slots, not the ids
+    for key, var, preds in cases:
+        idx = tb.tid_match(ctx, st, key)
+        h = tb.tid_bind(ctx, st, (*key, var), idx, preds)
+        tb.tid_set_free(idx)
+        want = orc.bind(S, P, O, key, var, orc.match(S, P, O, key))
+        for v, op, *ab in preds:
+            want = orc.filter(want, v, op, *ab)
+        _same(_host(h), want)
+    tb.tid_store_free(st)
+
+
 @pytest.mark.parametrize("n", [0, 1, 2047, 2048, 2049, 30_001])
 def test_filter_all_ops(ctx, orc, n):
     rng = np.random.default_rng(n)
