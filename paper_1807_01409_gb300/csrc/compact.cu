@@ -174,8 +174,16 @@ struct SemiJoinRow {  // store triple r, kept when a slot holds a fixed term and
     __device__ __forceinline__ const int32_t *column(int slot) const { return slot == 0 ? S : (slot == 1 ? P : O); }
     // the fixed column first, the key column and a probe only for rows that pass
     __device__ __forceinline__ bool keep(int64_t r) const {
-        if (fixed_slot >= 0 && column(fixed_slot)[r] != fixed_val) return false;
-        const int32_t key = column(key_slot)[r];
+        return keep_given(r, first_column()[r]);
+    }
+    // the column tested first: the fixed one, else the key column
+    __device__ __forceinline__ const int32_t *first_column() const {
+        return column(fixed_slot >= 0 ? fixed_slot : key_slot);
+    }
+    // keep(r), given v = first_column()[r]
+    __device__ __forceinline__ bool keep_given(int64_t r, int32_t v) const {
+        if (fixed_slot >= 0 && v != fixed_val) return false;
+        const int32_t key = fixed_slot >= 0 ? column(key_slot)[r] : v;
         if (key == 0) return false;
         const uint32_t tmask = (1u << tbits) - 1u;
         uint32_t h = ((uint32_t)key * 0x9E3779B1u) >> (32 - tbits);  // top bits: all of the key counts
@@ -227,9 +235,12 @@ __device__ __forceinline__ void merge_bounds(uint32_t *mm, int k_out, const uint
                 a = min(a, __shfl_xor_sync(0xffffffffu, a, d));
                 b = max(b, __shfl_xor_sync(0xffffffffu, b, d));
             }
+            // the bounds only tighten, so a warp that cannot improve the
+            // current one (read from L2; a stale read only costs an atomic)
+            // skips its atomic: many warps otherwise queue on one address
             if (lane == 0 && a <= b) {
-                atomicMin(mm + c, a);
-                atomicMax(mm + TID_MAX_COLS + c, b);
+                if (a < __ldcg(mm + c)) atomicMin(mm + c, a);
+                if (b > __ldcg(mm + TID_MAX_COLS + c)) atomicMax(mm + TID_MAX_COLS + c, b);
             }
         }
     }
@@ -461,9 +472,36 @@ k_tile_write(Row row, int64_t n, int k_out, OutCols out, int64_t cap, const uint
 
 constexpr int BC_THREADS = 256;
 constexpr int BC_WARPS = BC_THREADS / 32;
+constexpr int BC_INFLIGHT = 16;    // rows a lane tests at once (their loads in flight together)
+
+// kp[u] = row.keep(row base + 32 u) for u < BC_INFLIGHT (false past n)
+template <class Row>
+__device__ __forceinline__ void keep_batch(const Row &row, int64_t base, int64_t n, bool *kp) {
+#pragma unroll
+    for (int u = 0; u < BC_INFLIGHT; ++u) {  // rows past n test row n - 1 (in bounds, no branch) and drop it
+        const int64_t r = base + (int64_t)u * 32;
+        kp[u] = row.keep(r < n ? r : n - 1) && r < n;
+    }
+}
+// The keyed pass: the first tested column of all BC_INFLIGHT rows is loaded
+// before any row is tested, since a test's early exit would otherwise keep
+// the next row's load from being issued ahead of it.
+__device__ __forceinline__ void keep_batch(const SemiJoinRow &row, int64_t base, int64_t n, bool *kp) {
+    const int32_t *first = row.first_column();
+    int32_t v[BC_INFLIGHT];
+#pragma unroll
+    for (int u = 0; u < BC_INFLIGHT; ++u) {
+        const int64_t r = base + (int64_t)u * 32;
+        v[u] = first[r < n ? r : n - 1];
+    }
+#pragma unroll
+    for (int u = 0; u < BC_INFLIGHT; ++u) {
+        const int64_t r = base + (int64_t)u * 32;
+        kp[u] = r < n && row.keep_given(r, v[u]);
+    }
+}
 constexpr int BC_STEP = 1024;      // rows per warp step (32 keep words)
 constexpr int BC_DRAW = 8;         // steps per draw from the counter
-constexpr int BC_INFLIGHT = 16;    // rows a lane tests at once (their loads in flight together)
 constexpr int BC_CHUNK = BC_THREADS;  // steps scanned per round of phase C
 constexpr int BC_TICKET = 32;      // step counter's word in the control block
 constexpr size_t BC_CTL_BYTES = 256;
@@ -507,11 +545,7 @@ k_compact_bitmap(Row row, int64_t n, int k_out, OutCols out, int64_t cap, int64_
 #pragma unroll 1
             for (int w0 = 0; w0 < 32; w0 += BC_INFLIGHT) {
                 bool kp[BC_INFLIGHT];
-#pragma unroll
-                for (int u = 0; u < BC_INFLIGHT; ++u) {  // rows past n test row n - 1 (in bounds, no branch) and drop it
-                    const int64_t r = base + (int64_t)(w0 + u) * 32;
-                    kp[u] = row.keep(r < n ? r : n - 1) && r < n;
-                }
+                keep_batch(row, base + (int64_t)w0 * 32, n, kp);
 #pragma unroll
                 for (int u = 0; u < BC_INFLIGHT; ++u) {
                     const unsigned b = __ballot_sync(0xffffffffu, kp[u]);
@@ -779,6 +813,7 @@ __global__ void __launch_bounds__(256) k_bind_gather(BindRow row, int64_t n, Out
 // ---- exclusive scan of uint32 (look-back) --------------------------------------
 
 constexpr int SC_THREADS = 256, SC_ITEMS = 16, SC_TILE = SC_THREADS * SC_ITEMS;
+static_assert(SC_ITEMS == 16, "k_scan_u32 splits tile positions as (e >> 4, e & 15)");
 
 // Exclusive scan of one 4096-item tile; the tile's first output is `prefix`
 // (from offs[tile] when offs is given, else by decoupled look-back -- used for a
@@ -789,18 +824,27 @@ k_scan_u32(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t 
     __shared__ unsigned s_tile;
     __shared__ uint32_t s_w[SC_THREADS / 32];
     __shared__ long long s_prefix;
+    // the tile, thread-blocked (thread t's items at t * 17 .. t * 17 + 15: the
+    // odd stride keeps a warp's blocked reads on distinct banks); global loads
+    // and stores go through it striped, so they are coalesced
+    __shared__ uint32_t s_t[SC_THREADS * (SC_ITEMS + 1)];
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_tile = offs ? blockIdx.x : lb_ticket(lb);
     __syncthreads();
     const unsigned tile = s_tile;
     if (!offs && tile >= lb.num_tiles) return;
-    // blocked: thread t owns items base + t*16 .. +15
-    const int64_t base = (int64_t)tile * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+    const int64_t base0 = (int64_t)tile * SC_TILE;
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; ++i) {
+        const int e = i * SC_THREADS + threadIdx.x;
+        s_t[(e >> 4) * (SC_ITEMS + 1) + (e & 15)] = base0 + e < n ? in[base0 + e] : 0u;
+    }
+    __syncthreads();
     uint32_t v[SC_ITEMS];
     uint32_t sum = 0;
 #pragma unroll
     for (int i = 0; i < SC_ITEMS; ++i) {
-        v[i] = base + i < n ? in[base + i] : 0u;
+        v[i] = s_t[threadIdx.x * (SC_ITEMS + 1) + i];
         sum += v[i];
     }
     uint32_t x = sum;
@@ -836,8 +880,14 @@ k_scan_u32(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t 
     uint32_t run = (uint32_t)s_prefix + s_w[warp] + (x - sum);
 #pragma unroll
     for (int i = 0; i < SC_ITEMS; ++i) {
-        if (base + i < n) out[base + i] = run;
+        s_t[threadIdx.x * (SC_ITEMS + 1) + i] = run;
         run += v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SC_ITEMS; ++i) {
+        const int e = i * SC_THREADS + threadIdx.x;
+        if (base0 + e < n) out[base0 + e] = s_t[(e >> 4) * (SC_ITEMS + 1) + (e & 15)];
     }
 }
 

@@ -157,8 +157,8 @@ struct PairBits {
     uint32_t *bits;
 };
 
-// General form: one atomic OR per (row, rank); a lane skips a row equal, in
-// slot and term, to the previous lane's.
+// General form: one atomic OR per (row, rank) whose bit is not yet set; a
+// lane skips a row equal, in slot and term, to the previous lane's.
 __global__ void __launch_bounds__(BM_THREADS) k_pair_bits_list(PairBits P) {
     const unsigned lane = threadIdx.x & 31;
     for (int64_t i0 = bm_first(); i0 < P.n; i0 += bm_stride()) {
@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(BM_THREADS) k_pair_bits_list(PairBits P) {
             for (uint32_t j = P.off[h]; j < P.off[h + 1]; ++j) {
                 const uint64_t r = P.rank[j];
                 const uint64_t g = P.a_first ? (r << P.lg) + d : ((uint64_t)d << P.lg) + r;
-                atomicOr(P.bits + (g >> 5), 1u << (g & 31));
+                const uint32_t b = 1u << (g & 31);
+                if (!(P.bits[g >> 5] & b)) atomicOr(P.bits + (g >> 5), b);  // read first, as above
             }
         }
     }
@@ -214,7 +215,9 @@ __global__ void __launch_bounds__(BM_THREADS) k_pair_bits_mask(PairBits P) {
                 if ((int)lane - d >= start) acc |= o;
             }
             const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-            if (h >= 0 && tail) atomicOr(P.bits + word, acc);
+            // most rows repeat a pair already set: read before the atomic (a
+            // stale read only costs the atomic)
+            if (h >= 0 && tail && (P.bits[word] & acc) != acc) atomicOr(P.bits + word, acc);
         }
     }
 }
@@ -241,45 +244,55 @@ __global__ void __launch_bounds__(BM_THREADS) k_seg_bits(const uint32_t *__restr
     if (lane == 0) counts[s] = c;
 }
 
-// offs[s] = sum of counts[0, s) (64-bit), *total = sum of all (one CTA: each
-// thread sums a contiguous share, eight loads in flight)
+// offs[s] = sum of counts[0, s) (64-bit), *total = sum of all.  One CTA steps
+// through the counts 8192 at a time (eight consecutive ones per thread) with a
+// carry.
 __global__ void __launch_bounds__(1024) k_scan_segs(const uint32_t *__restrict__ counts, int64_t nseg,
                                                     unsigned long long *__restrict__ offs,
                                                     unsigned long long *__restrict__ total) {
     __shared__ unsigned long long s_w[32];
-    const int64_t per = (nseg + 1023) / 1024;
-    const int64_t b = min(nseg, (int64_t)threadIdx.x * per), e = min(nseg, b + per);
-    unsigned long long s = 0;
-#pragma unroll 8
-    for (int64_t t = b; t < e; ++t) s += counts[t];
+    __shared__ unsigned long long s_chunk;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long x = s;
+    unsigned long long carry = 0;
+    for (int64_t base = 0; base < nseg; base += 1024 * 8) {
+        const int64_t e0 = base + (int64_t)threadIdx.x * 8;
+        uint32_t c[8];
+        unsigned long long s = 0;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
-        if ((int)lane >= d) x += y;
-    }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        const unsigned long long v = s_w[lane];
-        unsigned long long y = v;
+        for (int j = 0; j < 8; ++j) {
+            c[j] = e0 + j < nseg ? counts[e0 + j] : 0u;
+            s += c[j];
+        }
+        unsigned long long x = s;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long z = __shfl_up_sync(0xffffffffu, y, d);
-            if ((int)lane >= d) y += z;
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+            if ((int)lane >= d) x += y;
         }
-        s_w[lane] = y - v;
-        if (lane == 31) *total = y;
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long v = s_w[lane];
+            unsigned long long y = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long z = __shfl_up_sync(0xffffffffu, y, d);
+                if ((int)lane >= d) y += z;
+            }
+            s_w[lane] = y - v;
+            if (lane == 31) s_chunk = y;
+        }
+        __syncthreads();
+        unsigned long long run = carry + s_w[warp] + x - s;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (e0 + j < nseg) offs[e0 + j] = run;
+            run += c[j];
+        }
+        carry += s_chunk;
+        __syncthreads();  // s_w and s_chunk are rewritten by the next chunk
     }
-    __syncthreads();
-    unsigned long long run = s_w[warp] + x - s;
-#pragma unroll 8
-    for (int64_t t = b; t < e; ++t) {
-        const uint32_t c = counts[t];
-        offs[t] = run;
-        run += c;
-    }
+    if (threadIdx.x == 0) *total = carry;
 }
 
 struct PairOut {  // decoding a set bit into the conclusion's row
@@ -309,38 +322,48 @@ __global__ void __launch_bounds__(BM_THREADS) k_emit_pairs(const uint32_t *__res
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     uint64_t pos = offs[s];
-    for (int r = 0; r < R; ++r) {
-        const int64_t wb = (s * R + r) * 32;  // the round's first word
-        if (wb >= nwords) break;
-        const int64_t w = wb + lane;
-        uint32_t v = w < nwords ? bits[w] : 0u;
-        const uint32_t c = __popc(v);
-        uint32_t x = c;
+    constexpr int AHEAD = 8;  // rounds whose words are loaded together
+    for (int r0 = 0; r0 < R; r0 += AHEAD) {
+        uint32_t va[AHEAD];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-            if ((int)lane >= d) x += y;
+        for (int q = 0; q < AHEAD; ++q) {
+            const int64_t w = (s * R + r0 + q) * 32 + lane;
+            va[q] = r0 + q < R && w < nwords ? bits[w] : 0u;
         }
-        const uint64_t mine = pos + x - c;
-        const uint32_t tot = __shfl_sync(0xffffffffu, x, 31);
-        if (__any_sync(0xffffffffu, c > 2)) {
-            unsigned nz = __ballot_sync(0xffffffffu, v != 0);
-            while (nz) {
-                const int L = __ffs(nz) - 1;
-                nz &= nz - 1;
-                const uint32_t wv = __shfl_sync(0xffffffffu, v, L);
-                const uint64_t b0 = __shfl_sync(0xffffffffu, mine, L);
-                if ((wv >> lane) & 1u) O.put((uint64_t)(wb + L) * 32 + lane, b0 + __popc(wv & lt));
+#pragma unroll
+        for (int q = 0; q < AHEAD; ++q) {
+            const int64_t wb = (s * R + r0 + q) * 32;  // the round's first word
+            if (r0 + q >= R || wb >= nwords) break;
+            const int64_t w = wb + lane;
+            uint32_t v = va[q];
+            const uint32_t c = __popc(v);
+            uint32_t x = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+                if ((int)lane >= d) x += y;
             }
-        } else {
-            uint64_t at = mine;
-            while (v) {
-                const int b = __ffs(v) - 1;
-                v &= v - 1;
-                O.put((uint64_t)w * 32 + b, at++);
+            const uint64_t mine = pos + x - c;
+            const uint32_t tot = __shfl_sync(0xffffffffu, x, 31);
+            if (__any_sync(0xffffffffu, c > 2)) {
+                unsigned nz = __ballot_sync(0xffffffffu, v != 0);
+                while (nz) {
+                    const int L = __ffs(nz) - 1;
+                    nz &= nz - 1;
+                    const uint32_t wv = __shfl_sync(0xffffffffu, v, L);
+                    const uint64_t b0 = __shfl_sync(0xffffffffu, mine, L);
+                    if ((wv >> lane) & 1u) O.put((uint64_t)(wb + L) * 32 + lane, b0 + __popc(wv & lt));
+                }
+            } else {
+                uint64_t at = mine;
+                while (v) {
+                    const int b = __ffs(v) - 1;
+                    v &= v - 1;
+                    O.put((uint64_t)w * 32 + b, at++);
+                }
             }
+            pos += tot;
         }
-        pos += tot;
     }
 }
 
@@ -375,9 +398,9 @@ __global__ void k_col_range(const int32_t *__restrict__ col, int64_t n, uint32_t
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(mm, lo);
-        atomicMax(mm + 1, hi);
+    if ((threadIdx.x & 31) == 0) {  // skip an atomic that cannot tighten the bound
+        if (lo < __ldcg(mm)) atomicMin(mm, lo);
+        if (hi > __ldcg(mm + 1)) atomicMax(mm + 1, hi);
     }
 }
 
@@ -403,8 +426,12 @@ struct Buf {  // a device allocation freed on scope exit
 };
 
 constexpr int64_t PAIR_MAX_SCHEMA_ROWS = 1 << 22;  // schema rows ranked on the host
-constexpr uint64_t PAIR_MIN_BYTES = 64ull << 20;     // a matrix this small is always taken
-constexpr uint64_t PAIR_BYTES_PER_ROW = 32;          // else at most this per data-premise row
+// A matrix of up to 64 MiB stays mostly in L2 and is always taken; a larger
+// one only up to 4 bytes per data-premise row: beyond L2 every pair's bit is a
+// random DRAM read-modify-write, and joining and sorting the rows costs less
+// (R9 at 200M: a 1.28 GB matrix took 4.8 ms to fill and read out).
+constexpr uint64_t PAIR_MIN_BYTES = 64ull << 20;
+constexpr uint64_t PAIR_BYTES_PER_ROW = 4;
 constexpr uint64_t PAIR_MAX_BYTES = 4ull << 30;
 
 // The conclusion as the bit matrix of its distinct pairs (PairBits), when it

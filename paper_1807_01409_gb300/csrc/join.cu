@@ -160,40 +160,91 @@ __global__ void k_sm_count(Cols LK, int64_t nl, Cols RK, int64_t nr, int nk, boo
             lo_out[l] = lo;
             acc += c;
         }
-        block_add_u64(acc, total);
-        acc = 0;
     }
+    block_add_u64(acc, total);  // once per warp: one address takes these atomics one at a time
 }
 
-// one thread per output row
-__global__ void k_join_write(const uint32_t *__restrict__ off, int64_t nl, const uint32_t *__restrict__ lo,
-                             const int32_t *__restrict__ lperm, const int32_t *__restrict__ rmap,
-                             const int32_t *__restrict__ rperm, int64_t total, Cols L, int kl, Cols Rrest,
-                             int nrest, MCols outL, MCols outR, bool left_is_probe) {
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
-         o += (int64_t)gridDim.x * blockDim.x) {
-        int64_t a = 0, b = nl;  // first l with off[l] > o
-        while (a < b) {
-            const int64_t m = (a + b) >> 1;
-            if ((int64_t)off[m] <= o) a = m + 1;
+// Output rows of probe rows: probe row l's matches are written at off[l] ..
+// off[l + 1] - 1 (off the exclusive scan of the counts, total their sum).
+// Load-balanced search (the merge-path partition of Odeh et al. applied to
+// the sequences of row starts and output rows): CTA t takes items [t T, (t+1) T)
+// of their merged order (row l before output o when off[l] <= o), i.e. some
+// probe rows and the output rows next to them -- at most T items in all, so
+// neither a long run of rows without matches nor one row with millions of
+// matches makes a CTA's work unbounded.  The CTA stages its rows' offsets in
+// shared memory and each output row finds its probe row there by binary
+// search; consecutive output rows go to consecutive threads (coalesced
+// stores).
+constexpr int JW_THREADS = 256;
+constexpr int JW_ITEMS = 8;
+constexpr int JW_TILE = JW_THREADS * JW_ITEMS;
+
+// rows among the first d items of the merged order
+__device__ __forceinline__ int64_t jw_split(const uint32_t *__restrict__ off, int64_t nl, int64_t total, int64_t d) {
+    int64_t lo = max((int64_t)0, d - total), hi = min(d, nl);
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)off[mid] <= d - 1 - mid) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void join_row(const uint32_t *__restrict__ lo, const int32_t *__restrict__ lperm,
+                                         const int32_t *__restrict__ rmap, const int32_t *__restrict__ rperm,
+                                         const Cols &L, int kl, const Cols &Rrest, int nrest, const MCols &outL,
+                                         const MCols &outR, bool left_is_probe, int64_t l, uint32_t lol, int64_t k,
+                                         int64_t o) {
+    if (lol == NO_MATCH) {  // left outer join: the left row alone, right columns unbound
+        write_out(L, kl, Rrest, nrest, lperm ? lperm[l] : l, -1, outL, outR, o);
+        return;
+    }
+    const int64_t j = (int64_t)lol + k;
+    int64_t lr, rr;
+    if (left_is_probe) {
+        lr = lperm ? lperm[l] : l;
+        rr = rmap ? rmap[j] : j;
+        if (rperm) rr = rperm[rr];
+    } else {  // hash join built on the left: "l" walks right rows, j indexes grouped left rows
+        rr = l;
+        lr = rmap[j];
+    }
+    write_out(L, kl, Rrest, nrest, lr, rr, outL, outR, o);
+}
+
+__global__ void __launch_bounds__(JW_THREADS) k_join_write(const uint32_t *__restrict__ off, int64_t nl,
+                                                           const uint32_t *__restrict__ lo,
+                                                           const int32_t *__restrict__ lperm,
+                                                           const int32_t *__restrict__ rmap,
+                                                           const int32_t *__restrict__ rperm, int64_t total, Cols L,
+                                                           int kl, Cols Rrest, int nrest, MCols outL, MCols outR,
+                                                           bool left_is_probe) {
+    __shared__ uint32_t s_off[JW_TILE + 1];  // off[rb .. r1 - 1]
+    __shared__ int64_t s_r[2];
+    const int64_t d0 = (int64_t)blockIdx.x * JW_TILE, d1 = min(d0 + JW_TILE, nl + total);
+    if (threadIdx.x < 2) s_r[threadIdx.x] = jw_split(off, nl, total, threadIdx.x == 0 ? d0 : d1);
+    __syncthreads();
+    const int64_t r0 = s_r[0], r1 = s_r[1];
+    const int64_t o0 = d0 - r0, o1 = d1 - r1;
+    if (o0 >= o1) return;  // only rows here
+    // the output rows [o0, o1) belong to rows rb .. r1 - 1: row r0 - 1 precedes
+    // output o0 in the merged order (off[r0 - 1] <= o0), row r1 follows o1 - 1
+    const int64_t rb = r0 > 0 ? r0 - 1 : 0;
+    const int nr = (int)(r1 - rb);
+    for (int i = threadIdx.x; i < nr; i += JW_THREADS) s_off[i] = off[rb + i];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < JW_ITEMS; ++q) {
+        const int64_t o = o0 + q * JW_THREADS + threadIdx.x;
+        if (o >= o1) break;
+        int a = 0, b = nr;  // last i with s_off[i] <= o
+        while (b - a > 1) {
+            const int m = (a + b) >> 1;
+            if ((int64_t)s_off[m] <= o) a = m;
             else b = m;
         }
-        const int64_t l = a - 1;
-        if (lo[l] == NO_MATCH) {  // left outer join: the left row alone, right columns unbound
-            write_out(L, kl, Rrest, nrest, lperm ? lperm[l] : l, -1, outL, outR, o);
-            continue;
-        }
-        const int64_t j = (int64_t)lo[l] + (o - (int64_t)off[l]);
-        int64_t lr, rr;
-        if (left_is_probe) {
-            lr = lperm ? lperm[l] : l;
-            rr = rmap ? rmap[j] : j;
-            if (rperm) rr = rperm[rr];
-        } else {  // hash join built on the left: "l" walks right rows, j indexes grouped left rows
-            rr = l;
-            lr = rmap[j];
-        }
-        write_out(L, kl, Rrest, nrest, lr, rr, outL, outR, o);
+        const int64_t l = rb + a;
+        join_row(lo, lperm, rmap, rperm, L, kl, Rrest, nrest, outL, outR, left_is_probe, l, lo[l], o - s_off[a], o);
     }
 }
 
@@ -400,14 +451,27 @@ __global__ void k_hash_count(Cols QK, int64_t nq, Cols BK, int nk, const unsigne
         scnt = s_cnt;
         sstart = s_start;
     }
+    // HC_U probe rows per thread per step, hashed first so that their key
+    // loads are in flight together
+    constexpr int HC_U = 4;
     unsigned long long acc = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n_iter = ceil_div(nq, stride) * stride;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_iter; q += stride) {
-        if (q < nq) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * HC_U;
+    for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x * HC_U + threadIdx.x; q0 < nq; q0 += stride) {
+        unsigned long long h[HC_U];
+        bool z[HC_U];
+#pragma unroll
+        for (int u = 0; u < HC_U; ++u) {
+            const int64_t q = min(q0 + (int64_t)u * blockDim.x, nq - 1);
+            h[u] = hash_key(QK, q, nk);
+            z[u] = has_zero(QK, q, nk);
+        }
+#pragma unroll
+        for (int u = 0; u < HC_U; ++u) {
+            const int64_t q = q0 + (int64_t)u * blockDim.x;
+            if (q >= nq) break;
             uint32_t c = 0, st = 0;
-            if (!has_zero(QK, q, nk)) {
-                const int64_t s = find_slot(slots, mask, BK, QK, q, nk, hash_key(QK, q, nk));
+            if (!z[u]) {
+                const int64_t s = find_slot(slots, mask, BK, QK, q, nk, h[u]);
                 if (s >= 0) {
                     c = scnt[s];
                     st = sstart[s];
@@ -417,9 +481,8 @@ __global__ void k_hash_count(Cols QK, int64_t nq, Cols BK, int nk, const unsigne
             qstart[q] = st;
             acc += c;
         }
-        block_add_u64(acc, total);
-        acc = 0;
     }
+    block_add_u64(acc, total);  // once per warp: one address takes these atomics one at a time
 }
 
 struct Scratch {
@@ -675,9 +738,9 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         TID_TRY(s.get(&lo, nq));
         TID_TRY(s.get(&off, nq));
         if (T <= (uint32_t)SMEM_SLOTS)
-            k_hash_count<true><<<grid_for(nq, 256), 256, 0, st>>>(QK, nq, BK, nk, slots, scnt, sstart, mask, cnt, lo, d_total);
+            k_hash_count<true><<<grid_for(nq, 256 * 4), 256, 0, st>>>(QK, nq, BK, nk, slots, scnt, sstart, mask, cnt, lo, d_total);
         else
-            k_hash_count<false><<<grid_for(nq, 256), 256, 0, st>>>(QK, nq, BK, nk, slots, scnt, sstart, mask, cnt, lo, d_total);
+            k_hash_count<false><<<grid_for(nq, 256 * 4), 256, 0, st>>>(QK, nq, BK, nk, slots, scnt, sstart, mask, cnt, lo, d_total);
         TID_TRY(launch_check("k_hash_count"));
         TID_TRY(scan_exclusive_u32(ctx, cnt, off, nq, nullptr));
         rmap = grouped;
@@ -698,7 +761,7 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
         for (int c = 0; c < nrest; ++c) oR.c[c] = res->col[L->k + c];
         int rc = TID_OK;
         if (total > 0) {
-            k_join_write<<<grid_for((int64_t)total, 256), 256, 0, st>>>(
+            k_join_write<<<(unsigned)ceil_div(n_probe + (int64_t)total, JW_TILE), JW_THREADS, 0, st>>>(
                 off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, Lall, L->k, Rrest, nrest, oL, oR, left_is_probe);
             rc = launch_check("k_join_write");
         }
@@ -716,7 +779,7 @@ int join_sets(tid_ctx *ctx, const tid_set *L, const tid_set *R, int algo, tid_se
     for (int c = 0; c < L->k; ++c) oL.c[c] = oc.c[c];
     for (int c = 0; c < nrest; ++c) oR.c[c] = oc.c[L->k + c];
     if (total > 0) {
-        k_join_write<<<grid_for((int64_t)total, 256), 256, 0, st>>>(
+        k_join_write<<<(unsigned)ceil_div(n_probe + (int64_t)total, JW_TILE), JW_THREADS, 0, st>>>(
             off, n_probe, lo, lperm, rmap, rperm, (int64_t)total, Lall, L->k, Rrest, nrest, oL, oR, left_is_probe);
         TID_TRY(launch_check("k_join_write"));
     }

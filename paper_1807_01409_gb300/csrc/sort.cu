@@ -11,11 +11,14 @@
 // (key, row) pairs are radix sorted stably, so the final permutation orders
 // rows lexicographically; again only the bits that vary are sorted.
 //
-// One digit pass = per-tile histograms (k_tile_hist) + a scan of the (digit,
-// tile) counts + one ranking-and-scatter launch (k_onesweep): tiles of 4096
-// keys rank stably (warp match_any groups, the first lane of a group adding
-// its size to a shared counter) and scatter through shared memory so runs of
-// equal digits are written contiguously, at the scanned offsets.  No tile
+// One digit pass = per-tile histograms (k_tile_hist) + a scan of each digit's
+// tile counts (k_digit_scan, one CTA per digit) + one ranking-and-scatter
+// launch (k_onesweep): tiles of 4096
+// keys rank stably (the lanes of a warp with equal digits found by a match
+// instruction or by eight ballots, alternately, the first lane of each group
+// adding its size to a shared counter)
+// and scatter through shared memory so runs of equal digits are written
+// contiguously, at the scanned offsets.  No tile
 // waits for another: a one-launch form whose tiles took each bin's offset by a
 // decoupled look-back over earlier tiles (Adinets and Merrill, "Onesweep",
 // 2022) waited there longer than its tiles worked, every tile walking back
@@ -38,8 +41,11 @@ namespace {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 rows
+// Keys per thread of a digit pass (tiles of 4096 keys, three CTAs per SM).  A
+// template parameter of the pass kernels: 32 for keys-only 32-bit sorts (8192-
+// key tiles, two CTAs per SM) measured slower.
+template <typename K, bool HAS_VAL>
+constexpr int rs_items() { return 16; }
 constexpr int RS_BINS = 256;
 
 struct ColPtrs {
@@ -52,21 +58,40 @@ struct MutColPtrs {
 
 __device__ __forceinline__ uint32_t order_key(int32_t x) { return (uint32_t)x ^ 0x80000000u; }
 
+// The streaming kernels below (k_minmax, k_prep, k_pack, k_unpack, k_gather)
+// take EW_U elements per thread per step, a block's EW_U * blockDim.x
+// consecutive elements at a time, and issue all of a step's loads before using
+// them: one 4-byte load per thread in flight did not cover HBM latency.
+constexpr int EW_U = 4;
+constexpr int EW_THREADS = 256;
+
+__device__ __forceinline__ int64_t ew_first() { return (int64_t)blockIdx.x * (EW_THREADS * EW_U) + threadIdx.x; }
+__device__ __forceinline__ int64_t ew_stride() { return (int64_t)gridDim.x * (EW_THREADS * EW_U); }
+
 // per-column min and max in sort order (flipped sign bit)
-__global__ void k_minmax(ColPtrs cols, int k, int64_t n, uint32_t *__restrict__ mn, uint32_t *__restrict__ mx) {
+__global__ void __launch_bounds__(EW_THREADS) k_minmax(ColPtrs cols, int k, int64_t n, uint32_t *__restrict__ mn,
+                                                       uint32_t *__restrict__ mx) {
     uint32_t lo[TID_MAX_COLS], hi[TID_MAX_COLS];
 #pragma unroll
     for (int c = 0; c < TID_MAX_COLS; ++c) {
         lo[c] = 0xFFFFFFFFu;
         hi[c] = 0u;
     }
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i0 = ew_first(); i0 < n; i0 += ew_stride()) {
 #pragma unroll
         for (int c = 0; c < TID_MAX_COLS; ++c) {
             if (c >= k) continue;
-            const uint32_t v = order_key(cols.c[c][i]);
-            lo[c] = min(lo[c], v);
-            hi[c] = max(hi[c], v);
+            uint32_t v[EW_U];
+#pragma unroll
+            for (int u = 0; u < EW_U; ++u) {
+                const int64_t i = i0 + u * EW_THREADS;
+                v[u] = i < n ? order_key(cols.c[c][i]) : order_key(cols.c[c][i0]);
+            }
+#pragma unroll
+            for (int u = 0; u < EW_U; ++u) {
+                lo[c] = min(lo[c], v[u]);
+                hi[c] = max(hi[c], v[u]);
+            }
         }
     }
 #pragma unroll
@@ -78,21 +103,35 @@ __global__ void k_minmax(ColPtrs cols, int k, int64_t n, uint32_t *__restrict__ 
             a = min(a, __shfl_xor_sync(0xffffffffu, a, d));
             b = max(b, __shfl_xor_sync(0xffffffffu, b, d));
         }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(mn + c, a);
-            atomicMax(mx + c, b);
+        if ((threadIdx.x & 31) == 0) {  // skip an atomic that cannot tighten the bound
+            if (a < __ldcg(mn + c)) atomicMin(mn + c, a);
+            if (b > __ldcg(mx + c)) atomicMax(mx + c, b);
         }
     }
 }
 
 
 // keys[i] = order_key(col[src(i)]) - base, vals[i] = src(i), src = perm ? perm[i] : i
-__global__ void k_prep(const int32_t *__restrict__ col, const int32_t *__restrict__ perm, int64_t n, uint32_t base,
-                       uint32_t *__restrict__ keys, int32_t *__restrict__ vals) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s = perm ? perm[i] : (int32_t)i;
-        keys[i] = order_key(col[s]) - base;
-        vals[i] = s;
+__global__ void __launch_bounds__(EW_THREADS) k_prep(const int32_t *__restrict__ col, const int32_t *__restrict__ perm,
+                                                     int64_t n, uint32_t base, uint32_t *__restrict__ keys,
+                                                     int32_t *__restrict__ vals) {
+    for (int64_t i0 = ew_first(); i0 < n; i0 += ew_stride()) {
+        int32_t s[EW_U], x[EW_U];
+#pragma unroll
+        for (int u = 0; u < EW_U; ++u) {
+            const int64_t i = i0 + u * EW_THREADS;
+            s[u] = i < n ? (perm ? perm[i] : (int32_t)i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < EW_U; ++u) x[u] = i0 + u * EW_THREADS < n ? col[s[u]] : 0;
+#pragma unroll
+        for (int u = 0; u < EW_U; ++u) {
+            const int64_t i = i0 + u * EW_THREADS;
+            if (i < n) {
+                keys[i] = order_key(x[u]) - base;
+                vals[i] = s[u];
+            }
+        }
     }
 }
 
@@ -101,25 +140,25 @@ __global__ void k_iota32(int32_t *__restrict__ out, int64_t n) {
         out[i] = (int32_t)i;
 }
 
-// Per-tile histogram of one digit: hist[d * tiles + t] = keys of tile t (RS_TILE
+// Per-tile histogram of one digit: hist[d * tiles + t] = keys of tile t (ITEMS x 256
 // keys) whose digit at `shift` is d.  Per-warp counters in shared memory (a
 // whole warp on one digit is one add).
-template <typename K>
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(RS_THREADS) k_tile_hist(const K *__restrict__ keys, int64_t n, int shift,
                                                           uint32_t *__restrict__ hist, unsigned tiles) {
     __shared__ uint32_t s_h[RS_WARPS][RS_BINS];
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&s_h[0][0])[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    K k[RS_ITEMS];
+    const int64_t base = (int64_t)blockIdx.x * (RS_THREADS * ITEMS);
+    K k[ITEMS];
 #pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
         const int64_t i = base + j * RS_THREADS + threadIdx.x;
         k[j] = i < n ? keys[i] : (K)0;
     }
 #pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
         const int64_t i = base + j * RS_THREADS + threadIdx.x;
         const bool valid = i < n;
         const unsigned d = valid ? (unsigned)(k[j] >> shift) & 0xFFu : 0x100u;
@@ -137,31 +176,98 @@ __global__ void __launch_bounds__(RS_THREADS) k_tile_hist(const K *__restrict__ 
     hist[(size_t)threadIdx.x * tiles + blockIdx.x] = c;
 }
 
-// The offset of (digit d, tile t) is offs[d * tiles + t]: the scanned per-tile
-// histograms (k_tile_hist), so no tile waits for another.
-template <typename K, bool HAS_VAL>
-__global__ void __launch_bounds__(RS_THREADS, 3)
+// In place: row d of the per-tile histograms (hist[d * tiles + t]) becomes its
+// exclusive scan over the tiles, and tot[d] the row's total.  One CTA per
+// digit, stepping through its row 1024 tiles at a time with a carry.
+__global__ void __launch_bounds__(1024) k_digit_scan(uint32_t *__restrict__ hist, unsigned tiles,
+                                                     uint32_t *__restrict__ tot) {
+    __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_chunk;
+    uint32_t *row = hist + (size_t)blockIdx.x * tiles;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (unsigned b = 0; b < tiles; b += 1024) {
+        const unsigned t = b + threadIdx.x;
+        const uint32_t v = t < tiles ? row[t] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = s_w[lane];
+            uint32_t y = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+                if ((int)lane >= o) y += z;
+            }
+            s_w[lane] = y - w;
+            if (lane == 31) s_chunk = y;
+        }
+        __syncthreads();
+        if (t < tiles) row[t] = carry + s_w[warp] + x - v;
+        carry += s_chunk;
+        __syncthreads();  // s_w and s_chunk are rewritten by the next chunk
+    }
+    if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+}
+
+// The offset of (digit d, tile t) is the keys of smaller digits (the exclusive
+// scan of tot) plus offs[d * tiles + t], the row-scanned per-tile histograms
+// (k_tile_hist, k_digit_scan), so no tile waits for another.
+template <typename K, bool HAS_VAL, int ITEMS>
+__global__ void __launch_bounds__(RS_THREADS, ITEMS == 32 ? 2 : 3)
 k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__restrict__ kout, int32_t *__restrict__ vout,
-           int64_t n, int shift, const uint32_t *__restrict__ offs, unsigned tiles) {
+           int64_t n, int shift, const uint32_t *__restrict__ offs, const uint32_t *__restrict__ tot, unsigned tiles) {
     __shared__ uint32_t s_wcnt[RS_WARPS][RS_BINS];
-    __shared__ uint32_t s_tdig[RS_BINS];
     __shared__ uint32_t s_gbase[RS_BINS];
-    __shared__ uint32_t s_wsum[RS_WARPS];
-    __shared__ K s_k[RS_TILE];
-    __shared__ int32_t s_v[HAS_VAL ? RS_TILE : 1];
+    __shared__ uint32_t s_wsum[RS_WARPS], s_wtot[RS_WARPS];
+    __shared__ K s_k[(RS_THREADS * ITEMS)];
+    __shared__ int32_t s_v[HAS_VAL ? (RS_THREADS * ITEMS) : 1];
 
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&s_wcnt[0][0])[i] = 0;
-    __syncthreads();
     const unsigned tile = blockIdx.x;
-    const int64_t base = (int64_t)tile * RS_TILE;
-    const int64_t wbase = base + (int64_t)warp * (RS_ITEMS * 32);
-    K k[RS_ITEMS];
-    uint32_t r[RS_ITEMS];
-    int32_t v[HAS_VAL ? RS_ITEMS : 1];
+    {
+        // this tile's first output position per digit (one digit per thread):
+        // the keys of smaller digits (exclusive scan of tot) + this digit's
+        // keys in earlier tiles
+        const unsigned d = threadIdx.x;
+        const uint32_t t = tot[d];
+        uint32_t x = t;
 #pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) s_wtot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = lane < RS_WARPS ? s_wtot[lane] : 0u;
+            uint32_t y = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+                if ((int)lane >= o) y += z;
+            }
+            if (lane < RS_WARPS) s_wtot[lane] = y - w;
+        }
+        __syncthreads();
+        s_gbase[d] = x - t + s_wtot[warp] + offs[(size_t)d * tiles + tile];
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)tile * (RS_THREADS * ITEMS);
+    const int64_t wbase = base + (int64_t)warp * (ITEMS * 32);
+    K k[ITEMS];
+    uint32_t r[ITEMS / 2];  // ranks within the warp (< 32 ITEMS), two per register
+    int32_t v[HAS_VAL ? ITEMS : 1];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
         const int64_t i = wbase + j * 32 + lane;
         const bool valid = i < n;
         k[j] = valid ? kin[i] : (K)0;
@@ -173,16 +279,35 @@ k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__rest
     // the group reads that base from it -- no warp-wide wait between items,
     // so the items' counter updates overlap
 #pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
         const int64_t i = wbase + j * 32 + lane;
         const bool valid = i < n;
-        const unsigned d = valid ? (unsigned)(k[j] >> shift) & 0xFFu : 0x100u;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        // lanes with the same digit.  Two ways that load different pipes are
+        // alternated over the items: the warp-wide match instruction (its
+        // pipe alone held the kernel back when every item used it), and one
+        // ballot per digit bit (ALU work: alone, the ALU pipe bounded it).
+        unsigned peers;
+        if ((j & 1) == 0) {
+            peers = __match_any_sync(0xffffffffu, valid ? (unsigned)(k[j] >> shift) & 0xFFu : 0x100u);
+        } else {
+            const unsigned d = valid ? (unsigned)(k[j] >> shift) & 0xFFu : 0u;
+            peers = __ballot_sync(0xffffffffu, valid);  // separates the tail's invalid lanes
+            if (!valid) peers = ~peers;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const bool bit = (d >> b) & 1u;
+                const unsigned bb = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bb : ~bb;
+            }
+        }
+        const unsigned d = valid ? (unsigned)(k[j] >> shift) & 0xFFu : 0u;
         const int leader = __ffs(peers) - 1;
         uint32_t b = 0;
         if (valid && lane == (unsigned)leader) b = atomicAdd(&s_wcnt[warp][d], (uint32_t)__popc(peers));
         b = __shfl_sync(0xffffffffu, b, leader);
-        r[j] = b + __popc(peers & lt);
+        const uint32_t rank = b + __popc(peers & lt);
+        if (j & 1) r[j >> 1] |= rank << 16;
+        else r[j >> 1] = rank;
     }
     __syncthreads();
     {
@@ -213,26 +338,31 @@ k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__rest
             if (lane < RS_WARPS) s_wsum[lane] = y - w;
         }
         __syncthreads();
-        s_tdig[d] = x - run + s_wsum[warp];
-        s_gbase[d] = offs[(size_t)d * tiles + tile];
+        // digit d's first position in the tile, folded into each warp's
+        // counter (one shared load per key when scattering) and into the
+        // digit's tile-to-output shift (one per key when writing out)
+        const uint32_t tdig = x - run + s_wsum[warp];
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) s_wcnt[w][d] += tdig;
+        s_gbase[d] -= tdig;
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < RS_ITEMS; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
         const int64_t i = wbase + j * 32 + lane;
         if (i < n) {
             const unsigned d = (unsigned)(k[j] >> shift) & 0xFFu;
-            const uint32_t lp = s_tdig[d] + s_wcnt[warp][d] + r[j];
+            const uint32_t lp = s_wcnt[warp][d] + ((r[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
             s_k[lp] = k[j];
             if (HAS_VAL) s_v[lp] = v[j];
         }
     }
     __syncthreads();
-    const int cnt = (int)(n - base < RS_TILE ? n - base : RS_TILE);
+    const int cnt = (int)(n - base < (RS_THREADS * ITEMS) ? n - base : (RS_THREADS * ITEMS));
     for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
         const K kk = s_k[i];
         const unsigned d = (unsigned)(kk >> shift) & 0xFFu;
-        const uint32_t gp = s_gbase[d] + ((uint32_t)i - s_tdig[d]);
+        const uint32_t gp = s_gbase[d] + (uint32_t)i;  // wraps modulo 2^32 to the right position
         kout[gp] = kk;
         if (HAS_VAL) vout[gp] = s_v[i];
     }
@@ -241,26 +371,52 @@ k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__rest
 // packed key of a row: column 0 most significant; field c holds
 // order_key(col_c) - min_c in bits [shift_c, shift_c + bits_c)
 template <typename K>
-__global__ void k_pack(ColPtrs cols, int k, int64_t n, PackSpec ps, K *__restrict__ keys) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        K key = 0;
+__global__ void __launch_bounds__(EW_THREADS) k_pack(ColPtrs cols, int k, int64_t n, PackSpec ps,
+                                                     K *__restrict__ keys) {
+    for (int64_t i0 = ew_first(); i0 < n; i0 += ew_stride()) {
+        K key[EW_U];
 #pragma unroll
-        for (int c = 0; c < TID_MAX_COLS; ++c)  // a constant column (mask 0) has no field
-            if (c < k && ps.mask[c]) key |= (K)(order_key(cols.c[c][i]) - ps.min[c]) << ps.shift[c];
-        keys[i] = key;
+        for (int u = 0; u < EW_U; ++u) key[u] = 0;
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c) {  // a constant column (mask 0) has no field
+            if (c >= k || !ps.mask[c]) continue;
+            int32_t x[EW_U];
+#pragma unroll
+            for (int u = 0; u < EW_U; ++u) {
+                const int64_t i = i0 + u * EW_THREADS;
+                x[u] = i < n ? cols.c[c][i] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < EW_U; ++u) key[u] |= (K)(order_key(x[u]) - ps.min[c]) << ps.shift[c];
+        }
+#pragma unroll
+        for (int u = 0; u < EW_U; ++u) {
+            const int64_t i = i0 + u * EW_THREADS;
+            if (i < n) keys[i] = key[u];
+        }
     }
 }
 
 // sorted packed keys -> k columns (no duplicate removal)
 template <typename K>
-__global__ void k_unpack(const K *__restrict__ keys, int k, int64_t n, PackSpec ps, MutColPtrs out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const K key = keys[i];
+__global__ void __launch_bounds__(EW_THREADS) k_unpack(const K *__restrict__ keys, int k, int64_t n, PackSpec ps,
+                                                       MutColPtrs out) {
+    for (int64_t i0 = ew_first(); i0 < n; i0 += ew_stride()) {
+        K key[EW_U];
+#pragma unroll
+        for (int u = 0; u < EW_U; ++u) {
+            const int64_t i = i0 + u * EW_THREADS;
+            key[u] = i < n ? keys[i] : (K)0;
+        }
 #pragma unroll
         for (int c = 0; c < TID_MAX_COLS; ++c) {
             if (c >= k) continue;
-            const uint32_t f = ps.mask[c] ? (uint32_t)((key >> ps.shift[c]) & ps.mask[c]) : 0u;
-            out.c[c][i] = (int32_t)((f + ps.min[c]) ^ 0x80000000u);
+#pragma unroll
+            for (int u = 0; u < EW_U; ++u) {
+                const int64_t i = i0 + u * EW_THREADS;
+                const uint32_t f = ps.mask[c] ? (uint32_t)((key[u] >> ps.shift[c]) & ps.mask[c]) : 0u;
+                if (i < n) out.c[c][i] = (int32_t)((f + ps.min[c]) ^ 0x80000000u);
+            }
         }
     }
 }
@@ -348,12 +504,27 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_canonical(ColPtrs cols,
     }
 }
 
-__global__ void k_gather(ColPtrs in, int k, const int32_t *__restrict__ perm, int64_t n, MutColPtrs out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = perm[i];
+__global__ void __launch_bounds__(EW_THREADS) k_gather(ColPtrs in, int k, const int32_t *__restrict__ perm, int64_t n,
+                                                       MutColPtrs out) {
+    for (int64_t i0 = ew_first(); i0 < n; i0 += ew_stride()) {
+        int64_t s[EW_U];
 #pragma unroll
-        for (int c = 0; c < TID_MAX_COLS; ++c)
-            if (c < k) out.c[c][i] = in.c[c][s];
+        for (int u = 0; u < EW_U; ++u) {
+            const int64_t i = i0 + u * EW_THREADS;
+            s[u] = i < n ? perm[i] : 0;
+        }
+#pragma unroll
+        for (int c = 0; c < TID_MAX_COLS; ++c) {
+            if (c >= k) continue;
+            int32_t x[EW_U];
+#pragma unroll
+            for (int u = 0; u < EW_U; ++u) x[u] = i0 + u * EW_THREADS < n ? in.c[c][s[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < EW_U; ++u) {
+                const int64_t i = i0 + u * EW_THREADS;
+                if (i < n) out.c[c][i] = x[u];
+            }
+        }
     }
 }
 
@@ -397,7 +568,7 @@ static int column_ranges(tid_ctx *ctx, const int32_t *const *cols, int k, int64_
     for (int c = 0; c < k; ++c) cp.c[c] = cols[c];
     TID_TRY_CUDA(cudaMemsetAsync(mm, 0xFF, TID_MAX_COLS * 4, st), "memset");
     TID_TRY_CUDA(cudaMemsetAsync(mm + TID_MAX_COLS, 0, TID_MAX_COLS * 4, st), "memset");
-    k_minmax<<<grid_for(n, 256), 256, 0, st>>>(cp, k, n, mm, mm + TID_MAX_COLS);
+    k_minmax<<<grid_for(n, EW_THREADS * EW_U, 8), EW_THREADS, 0, st>>>(cp, k, n, mm, mm + TID_MAX_COLS);
     TID_TRY(launch_check("k_minmax"));
     uint32_t both[2 * TID_MAX_COLS];
     TID_TRY_CUDA(cudaMemcpyAsync(both, mm, sizeof both, cudaMemcpyDeviceToHost, st), "copy min/max");
@@ -416,17 +587,23 @@ static int range_bits(uint32_t lo, uint32_t hi) { return hi == lo ? 0 : 32 - __b
 template <typename K, bool HAS_VAL>
 static int radix_passes(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *&pb, int64_t n, int shift0,
                         int passes) {
-    const unsigned tiles = (unsigned)ceil_div(n, RS_TILE);
+    constexpr int ITEMS = rs_items<K, HAS_VAL>();
+    const unsigned tiles = (unsigned)ceil_div(n, RS_THREADS * ITEMS);
     uint32_t *offs = nullptr;
-    TID_TRY(dev_alloc(ctx, (void **)&offs, sizeof(uint32_t) * (size_t)RS_BINS * tiles + 256));
+    TID_TRY(dev_alloc(ctx, (void **)&offs, sizeof(uint32_t) * (size_t)RS_BINS * (tiles + 1)));
+    uint32_t *tot = offs + (size_t)RS_BINS * tiles;
     int rc = TID_OK;
     for (int p = 0; p < passes && rc == TID_OK; ++p) {
         const int shift = shift0 + 8 * p;
-        k_tile_hist<K><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, n, shift, offs, tiles);
+        k_tile_hist<K, ITEMS><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, n, shift, offs, tiles);
         rc = launch_check("k_tile_hist");
-        if (rc == TID_OK) rc = scan_exclusive_u32(ctx, offs, offs, (int64_t)RS_BINS * tiles, nullptr);
         if (rc == TID_OK) {
-            k_onesweep<K, HAS_VAL><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, pa, kb, pb, n, shift, offs, tiles);
+            k_digit_scan<<<RS_BINS, 1024, 0, ctx->stream>>>(offs, tiles, tot);
+            rc = launch_check("k_digit_scan");
+        }
+        if (rc == TID_OK) {
+            k_onesweep<K, HAS_VAL, ITEMS><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, pa, kb, pb, n, shift, offs, tot,
+                                                                          tiles);
             rc = launch_check("k_onesweep");
         }
         std::swap(ka, kb);
@@ -457,7 +634,7 @@ static int sort_perm_ranges(tid_ctx *ctx, const int32_t *const *keys, int nk, in
             TID_TRY(s.get(&pa, n));
             TID_TRY(s.get(&pb, n));
         }
-        k_prep<<<grid_for(n, 256), 256, 0, st>>>(keys[c], have_perm ? pa : nullptr, n, hmin[c], ka, pa);
+        k_prep<<<grid_for(n, EW_THREADS * EW_U, 8), EW_THREADS, 0, st>>>(keys[c], have_perm ? pa : nullptr, n, hmin[c], ka, pa);
         TID_TRY(launch_check("k_prep"));
         TID_TRY((radix_passes<uint32_t, true>(ctx, ka, kb, pa, pb, n, 0, passes)));
         have_perm = true;
@@ -509,13 +686,13 @@ static int canonical_packed(tid_ctx *ctx, const int32_t *const *cols, int k, int
     TID_TRY(s.get(&kb, n));
     ColPtrs cp{};
     for (int c = 0; c < k; ++c) cp.c[c] = cols[c];
-    k_pack<K><<<grid_for(n, 256), 256, 0, st>>>(cp, k, n, ps, ka);
+    k_pack<K><<<grid_for(n, EW_THREADS * EW_U, 8), EW_THREADS, 0, st>>>(cp, k, n, ps, ka);
     TID_TRY(launch_check("k_pack"));
     TID_TRY((radix_passes<K, false>(ctx, ka, kb, none_a, none_b, n, sorted_bits, passes)));
     if (dedupe) return compact_unique_packed(ctx, ka, sizeof(K) == 8, k, n, ps, set);
     MutColPtrs op{};
     for (int c = 0; c < k; ++c) op.c[c] = set->col[c];
-    k_unpack<K><<<grid_for(n, 256), 256, 0, st>>>(ka, k, n, ps, op);
+    k_unpack<K><<<grid_for(n, EW_THREADS * EW_U, 8), EW_THREADS, 0, st>>>(ka, k, n, ps, op);
     TID_TRY(launch_check("k_unpack"));
     return set_rows_const(set, n);
 }
@@ -529,7 +706,7 @@ int gather_cols(tid_ctx *ctx, const int32_t *const *in, int k, const int32_t *pe
         ip.c[c] = in[c];
         op.c[c] = out[c];
     }
-    k_gather<<<grid_for(n, 256), 256, 0, ctx->stream>>>(ip, k, perm, n, op);
+    k_gather<<<grid_for(n, EW_THREADS * EW_U, 8), EW_THREADS, 0, ctx->stream>>>(ip, k, perm, n, op);
     return launch_check("k_gather");
 }
 
