@@ -969,6 +969,49 @@ def run_rows_only(args, local):
     print(json.dumps({"rows": rows, "n_triples": st.n}), flush=True)
 
 
+def run_sort_only(args, local):
+    """The canonical sort alone, for profiling: a seeded three-column set of
+    n rows (a 20-bit leading column, then a 23-bit and a 12-bit one), made
+    canonical by tid_set_from_host, then projected onto its last two columns
+    (35-bit packed keys: pack, five digit passes, distinct rows kept), timed
+    with CUDA events on the context's stream.  The same again with a 3-bit last
+    column (26-bit keys, four passes)."""
+    import numpy as np
+    import torch
+
+    from paper_1807_01409_gb300 import binding as tb
+    from paper_1807_01409_gb300 import build as tbuild
+    torch.cuda.set_device(local)
+    tbuild.build()
+    n, reps = args.sort_only, max(1, args.rows_reps)
+    rng = np.random.default_rng(synth.QUERY_SEED)
+    stream = torch.cuda.Stream()
+    ctx = tb.tid_ctx_create(local, stream.cuda_stream)
+    res = {}
+    for name, c1, c2 in [("35bit", rng.integers(1, 5_000_000, n), 5_000_001 + 512 * rng.integers(0, 8, n)),
+                         ("26bit", rng.integers(1, 5_000_000, n), rng.integers(0, 8, n))]:
+        rows = np.stack([rng.integers(1, 1 << 20, n), c1, c2], 1).astype(np.int32)
+        S = tb.tid_set_from_host(ctx, rows, [0, 1, 2])
+        tb.tid_ctx_sync(ctx)
+        ts = []
+        for _ in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            P = tb.tid_project(ctx, S, [1, 2])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            out_rows = tb.tid_set_rows(P)
+            tb.tid_set_free(P)
+        tb.tid_set_free(S)
+        timed = sorted(ts[2:])
+        res[name] = {"rows_in": n, "rows_out": out_rows, "ms_median": round(timed[len(timed) // 2], 4),
+                     "ms_all": [round(t, 4) for t in ts]}
+    tb.tid_ctx_destroy(ctx)
+    print(json.dumps({"sort": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -990,12 +1033,16 @@ def main():
     ap.add_argument("--no-entail", action="store_true", help="skip the RDFS entailment row")
     ap.add_argument("--serve-only", action="store_true",
                     help="profiling aid: one served-versus-plain measurement only, printed as JSON")
+    ap.add_argument("--sort-only", type=int, default=0, metavar="N",
+                    help="time the canonical sort of N seeded rows alone (calls: --rows-reps) and exit")
     ap.add_argument("--triples", type=int, default=N_TRIPLES,
                     help="store size (default: the full 200M workload; smaller only for profiling)")
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.sort_only:
+        run_sort_only(args, local)
     elif args.rows_only:
         run_rows_only(args, local)
     elif args.batch_only:
