@@ -237,11 +237,17 @@ __global__ void __launch_bounds__(JW_THREADS) k_join_write(const uint32_t *__res
     for (int q = 0; q < JW_ITEMS; ++q) {
         const int64_t o = o0 + q * JW_THREADS + threadIdx.x;
         if (o >= o1) break;
-        int a = 0, b = nr;  // last i with s_off[i] <= o
-        while (b - a > 1) {
-            const int m = (a + b) >> 1;
-            if ((int64_t)s_off[m] <= o) a = m;
-            else b = m;
+        // last i with s_off[i] <= o.  First guess: rows of one match each
+        // (the common case) put output o at row o - s_off[0] of the tile.
+        int a = (int)min((int64_t)(nr - 1), o - (int64_t)s_off[0]);
+        if (!((int64_t)s_off[a] <= o && (a + 1 == nr || (int64_t)s_off[a + 1] > o))) {
+            a = 0;
+            int b = nr;
+            while (b - a > 1) {
+                const int m = (a + b) >> 1;
+                if ((int64_t)s_off[m] <= o) a = m;
+                else b = m;
+            }
         }
         const int64_t l = rb + a;
         join_row(lo, lperm, rmap, rperm, L, kl, Rrest, nrest, outL, outR, left_is_probe, l, lo[l], o - s_off[a], o);
