@@ -41,11 +41,18 @@ namespace {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-// Keys per thread of a digit pass (tiles of 4096 keys, three CTAs per SM).  A
-// template parameter of the pass kernels: 32 for keys-only 32-bit sorts (8192-
-// key tiles, two CTAs per SM) measured slower.
-template <typename K, bool HAS_VAL>
-constexpr int rs_items() { return 16; }
+// Shape of a digit pass: keys per thread (a tile is 256 threads' keys) and the
+// CTAs per SM the scatter pass is compiled for.  The scatter pass is
+// latency-bound (shared-memory round trips per key), so resident CTAs matter:
+//  - keys-only 32-bit sorts: 16 keys, four CTAs (64 registers; 26 % faster
+//    than three CTAs on 32M rows);
+//  - 64-bit keys, at most RS_SMALL keys: 12 keys, four CTAs (the 23.6M-row
+//    projection 14 % faster, the 12M-row bind sort faster too);
+//  - larger 64-bit sorts and the (key, row) pairs of the permutation sort:
+//    16 keys, three CTAs (12 keys at four CTAs measured 4-8 % slower on 32M
+//    to 60M keys).
+// 32 keys per thread at two CTAs measured slower for every size.
+constexpr int64_t RS_SMALL = 24ll << 20;
 constexpr int RS_BINS = 256;
 
 struct ColPtrs {
@@ -219,8 +226,8 @@ __global__ void __launch_bounds__(1024) k_digit_scan(uint32_t *__restrict__ hist
 // The offset of (digit d, tile t) is the keys of smaller digits (the exclusive
 // scan of tot) plus offs[d * tiles + t], the row-scanned per-tile histograms
 // (k_tile_hist, k_digit_scan), so no tile waits for another.
-template <typename K, bool HAS_VAL, int ITEMS>
-__global__ void __launch_bounds__(RS_THREADS, ITEMS == 32 ? 2 : 3)
+template <typename K, bool HAS_VAL, int ITEMS, int MINB>
+__global__ void __launch_bounds__(RS_THREADS, MINB)
 k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__restrict__ kout, int32_t *__restrict__ vout,
            int64_t n, int shift, const uint32_t *__restrict__ offs, const uint32_t *__restrict__ tot, unsigned tiles) {
     __shared__ uint32_t s_wcnt[RS_WARPS][RS_BINS];
@@ -586,8 +593,11 @@ static int range_bits(uint32_t lo, uint32_t hi) { return hi == lo ? 0 : 32 - __b
 // the ranking and scatter at the scanned offsets.
 template <typename K, bool HAS_VAL>
 static int radix_passes(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *&pb, int64_t n, int shift0,
-                        int passes) {
-    constexpr int ITEMS = rs_items<K, HAS_VAL>();
+                        int passes);
+
+template <typename K, bool HAS_VAL, int ITEMS, int MINB>
+static int radix_passes_shaped(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *&pb, int64_t n, int shift0,
+                               int passes) {
     const unsigned tiles = (unsigned)ceil_div(n, RS_THREADS * ITEMS);
     uint32_t *offs = nullptr;
     TID_TRY(dev_alloc(ctx, (void **)&offs, sizeof(uint32_t) * (size_t)RS_BINS * (tiles + 1)));
@@ -602,8 +612,8 @@ static int radix_passes(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *&pb
             rc = launch_check("k_digit_scan");
         }
         if (rc == TID_OK) {
-            k_onesweep<K, HAS_VAL, ITEMS><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, pa, kb, pb, n, shift, offs, tot,
-                                                                          tiles);
+            k_onesweep<K, HAS_VAL, ITEMS, MINB><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, pa, kb, pb, n, shift, offs,
+                                                                                tot, tiles);
             rc = launch_check("k_onesweep");
         }
         std::swap(ka, kb);
@@ -611,6 +621,19 @@ static int radix_passes(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *&pb
     }
     dev_free(ctx, offs);
     return rc;
+}
+
+template <typename K, bool HAS_VAL>
+static int radix_passes(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32_t *&pb, int64_t n, int shift0,
+                        int passes) {
+    if constexpr (sizeof(K) == 4 && !HAS_VAL) {
+        return radix_passes_shaped<K, HAS_VAL, 16, 4>(ctx, ka, kb, pa, pb, n, shift0, passes);
+    } else if constexpr (sizeof(K) == 8) {
+        if (n <= RS_SMALL) return radix_passes_shaped<K, HAS_VAL, 12, 4>(ctx, ka, kb, pa, pb, n, shift0, passes);
+        return radix_passes_shaped<K, HAS_VAL, 16, 3>(ctx, ka, kb, pa, pb, n, shift0, passes);
+    } else {
+        return radix_passes_shaped<K, HAS_VAL, 16, 3>(ctx, ka, kb, pa, pb, n, shift0, passes);
+    }
 }
 
 // Stable LSD sort of a row permutation by key columns, given their ranges.  The

@@ -262,6 +262,34 @@ def test_join_skewed_key(ctx, orc):
     tb.tid_set_free(hr)
 
 
+@pytest.mark.parametrize("kind", ["sparse", "fan_out"])
+def test_join_output_partition(ctx, orc, kind):
+    """The output rows are split over CTAs by probe rows and output rows
+    together: long runs of probe rows without a match (sparse), and one key
+    whose matches fill many CTAs' shares (fan-out), both against the oracle,
+    inner and left, both algorithms."""
+    rng = np.random.default_rng(17 if kind == "sparse" else 18)
+    if kind == "sparse":  # 200K left keys, 40 of them present on the right
+        lk = rng.choice(np.arange(1, 10_000_000), 200_000, replace=False)
+        rk = np.r_[rng.choice(lk, 40, replace=False), rng.integers(10_000_001, 20_000_000, 1000)]
+        L = orc.TupleSet((0, 1), orc.canonical(np.stack([lk, rng.integers(1, 9, lk.shape[0])], 1)))
+        R = orc.TupleSet((0, 2), orc.canonical(np.stack([rk, np.arange(1, rk.shape[0] + 1)], 1)))
+    else:  # key 5: 300 left rows x 2000 right rows = 600K output rows, among ordinary keys
+        L = orc.TupleSet((0, 1), orc.canonical(np.stack([np.r_[np.full(300, 5), rng.integers(6, 40_000, 20_000)],
+                                                         np.arange(1, 20_301)], 1)))
+        R = orc.TupleSet((0, 2), orc.canonical(np.stack([np.r_[np.full(2000, 5), rng.integers(6, 40_000, 30_000)],
+                                                         np.arange(1, 32_001)], 1)))
+    hl = tb.tid_set_from_host(ctx, L.rows, (0, 1))
+    hr = tb.tid_set_from_host(ctx, R.rows, (0, 2))
+    want = orc.join(L, R, method="sortmerge")
+    for algo in ("sort_merge", "hash"):
+        _same(_host(tb.tid_join(ctx, hl, hr, algo)), want)
+    want_left = orc.left_join(L, R)
+    _same(_host(tb.tid_join(ctx, hl, hr, "left")), want_left)
+    tb.tid_set_free(hl)
+    tb.tid_set_free(hr)
+
+
 def test_nine_relationship_types(ctx, orc):
     """Table 'Relationship between two triple patterns': OO, PP, SS, OP, OS, PS,
     PO, SP, SO -- the shared variable at each slot pairing -- on a small graph,
