@@ -122,8 +122,10 @@ int tid_ctx_test_bounded_wait(tid_ctx *ctx, int64_t polls);
  *                      while the store lives).
  * n may be 0.  IDs are not scanned for validity (an ID <= 0 in the store can
  * only ever be matched by "?").  The store must be a set (no repeated triple)
- * for the tuple-set calls to return sets.  Returns after the copies are
- * queued on the context stream. */
+ * for the tuple-set calls to return sets.  One read of the store checks
+ * whether its triples are in (s, p, o) order; tid_bind on such a store skips
+ * its sort when index order is already the result's order.  Returns after the
+ * copies and the check are queued on the context stream. */
 int tid_load(tid_ctx *ctx, const int32_t *s, const int32_t *p, const int32_t *o,
              int64_t n, int where, int copy, tid_store **out);
 

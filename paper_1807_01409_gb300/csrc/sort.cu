@@ -53,6 +53,9 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 //    to 60M keys).
 // 32 keys per thread at two CTAs measured slower for every size.
 constexpr int64_t RS_SMALL = 24ll << 20;
+// Sorts of at most this many tiles skip the digit-scan launch: each scatter
+// CTA sums its digit's row of tile counts (the many small sorts of a plan).
+constexpr unsigned RS_FEW_TILES = 32;
 constexpr int RS_BINS = 256;
 
 struct ColPtrs {
@@ -245,7 +248,19 @@ k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__rest
         // the keys of smaller digits (exclusive scan of tot) + this digit's
         // keys in earlier tiles
         const unsigned d = threadIdx.x;
-        const uint32_t t = tot[d];
+        // tot == nullptr: the histograms were not scanned (a sort of at most
+        // RS_FEW_TILES tiles); the digit's row is summed here instead
+        uint32_t t = 0, pre = 0;
+        if (tot) {
+            t = tot[d];
+            pre = offs[(size_t)d * tiles + tile];
+        } else {
+            for (unsigned u = 0; u < tiles; ++u) {
+                const uint32_t c = offs[(size_t)d * tiles + u];
+                t += c;
+                pre += u < tile ? c : 0u;
+            }
+        }
         uint32_t x = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -265,7 +280,7 @@ k_onesweep(const K *__restrict__ kin, const int32_t *__restrict__ vin, K *__rest
             if (lane < RS_WARPS) s_wtot[lane] = y - w;
         }
         __syncthreads();
-        s_gbase[d] = x - t + s_wtot[warp] + offs[(size_t)d * tiles + tile];
+        s_gbase[d] = x - t + s_wtot[warp] + pre;
     }
     __syncthreads();
     const int64_t base = (int64_t)tile * (RS_THREADS * ITEMS);
@@ -607,13 +622,14 @@ static int radix_passes_shaped(tid_ctx *ctx, K *&ka, K *&kb, int32_t *&pa, int32
         const int shift = shift0 + 8 * p;
         k_tile_hist<K, ITEMS><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, n, shift, offs, tiles);
         rc = launch_check("k_tile_hist");
-        if (rc == TID_OK) {
+        const bool scan = tiles > RS_FEW_TILES;  // else each scatter CTA sums its digits' rows itself
+        if (rc == TID_OK && scan) {
             k_digit_scan<<<RS_BINS, 1024, 0, ctx->stream>>>(offs, tiles, tot);
             rc = launch_check("k_digit_scan");
         }
         if (rc == TID_OK) {
             k_onesweep<K, HAS_VAL, ITEMS, MINB><<<tiles, RS_THREADS, 0, ctx->stream>>>(ka, pa, kb, pb, n, shift, offs,
-                                                                                tot, tiles);
+                                                                                scan ? tot : nullptr, tiles);
             rc = launch_check("k_onesweep");
         }
         std::swap(ka, kb);
